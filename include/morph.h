@@ -1,0 +1,196 @@
+/*
+ * morph.h -- C ABI of the GB300 (sm_103a) grayscale morphology library.
+ *
+ * Operation (paper, section 2, the erosion equation and the sentence after
+ * it): for a source image S of width x height pixels and a rectangular
+ * structuring element of wx x wy cells with anchor (anchor_x, anchor_y),
+ *
+ *   erosion   D(x,y) = min { S(x',y') : x' in [x-anchor_x, x-anchor_x+wx-1],
+ *                                       y' in [y-anchor_y, y-anchor_y+wy-1] }
+ *   dilation  D(x,y) = max { ... same window ... }
+ *
+ * where pixels outside the image are ignored (equivalently: padded with the
+ * maximum value for erosion and with 0 for dilation).  The anchor counts from
+ * the element's top-left cell; the conventional centre is floor(w/2).  The
+ * paper's literal formula S(x - n + wx/2, ...), n in [0, wx-1], is the anchor
+ * ceil(w/2)-1, which is the same cell for odd windows.
+ *
+ * The result is exact (integer min/max): every entry point gives the same
+ * bytes as the definition, whatever kernel, tile shape or method it picks.
+ * Computation is separable (section 5): a pass along x with a wx x 1 element
+ * and a pass along y with a 1 x wy element, each by the direct ("linear")
+ * method of sections 5.1.2/5.2.2 for small windows or by van Herk/Gil-Werman
+ * (sections 5.1.1/5.2.1) for large ones, switched at a crossover window
+ * (section 5.3) measured on this GPU.  Both passes run fused in one kernel.
+ *
+ * Conventions for every entry point below
+ *  - Image pointers are DEVICE pointers (cudaMalloc / torch CUDA memory)
+ *    unless the name ends in _host.  The caller owns all buffers.
+ *  - Pitches are in bytes; pitch >= width * element size.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) and return before the kernel finishes, except the
+ *    _host entry point, which synchronises its stream.
+ *  - Errors are returned as a negative morph_status; nothing is thrown
+ *    across the ABI and no output is written when a call is rejected.
+ *    A CUDA launch error maps to MORPH_ERR_CUDA.
+ *  - src and dst must not overlap (MORPH_ERR_ALIAS): every tile reads a halo
+ *    that neighbouring tiles write.
+ *  - wx, wy >= 1; 0 <= anchor < w.  A window may be larger than the image
+ *    (the window is clipped to the image).
+ *  - The fused single-image path allocates no device memory.
+ */
+#ifndef MORPH_H
+#define MORPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MORPH_OK = 0,
+    MORPH_ERR_NULL = -1,    /* a required pointer is NULL                     */
+    MORPH_ERR_SIZE = -2,    /* width/height < 1 or too large                   */
+    MORPH_ERR_WINDOW = -3,  /* wx or wy < 1, or beyond the supported maximum   */
+    MORPH_ERR_ANCHOR = -4,  /* anchor outside [0, w)                           */
+    MORPH_ERR_PITCH = -5,   /* pitch < width * element size, or a 16-bit image  
+                               not 2-byte aligned (pointer or pitch)          */
+    MORPH_ERR_ALIAS = -6,   /* source and destination buffers overlap          */
+    MORPH_ERR_CUDA = -7,    /* a CUDA call failed (launch, copy, attribute)    */
+    MORPH_ERR_NOMEM = -8,   /* a device/host allocation failed                 */
+    MORPH_ERR_DTYPE = -9,   /* unknown dtype or op code                        */
+    MORPH_ERR_ARG = -10,    /* any other invalid argument (count, plan, ...)   */
+    MORPH_ERR_DEVICE = -11  /* a kernel reported an error in the device word   */
+} morph_status;
+
+/* dtype and op codes used by morph_apply and morph_desc. */
+enum { MORPH_U8 = 0, MORPH_U16 = 1 };
+enum { MORPH_ERODE = 0, MORPH_DILATE = 1 };
+
+/* Largest window (after clipping to the image: a window never needs to be
+ * longer than 2*side-1) that one fused launch accepts, per axis. */
+#define MORPH_MAX_WINDOW 255
+
+/*
+ * Erosion / dilation of one 8-bit image (section 2; section 5 computes it on
+ * 8-bit pixels).  src and dst are device buffers of height rows of `pitch`
+ * bytes each (the same pitch for both).  Returns MORPH_OK or an error.
+ */
+int morph_erode(const uint8_t *src, int width, int height, size_t pitch,
+                int wx, int wy, int anchor_x, int anchor_y,
+                uint8_t *dst, void *stream);
+int morph_dilate(const uint8_t *src, int width, int height, size_t pitch,
+                 int wx, int wy, int anchor_x, int anchor_y,
+                 uint8_t *dst, void *stream);
+
+/* The same on 16-bit pixels (section 2 definition; identities 65535 / 0). */
+int morph_erode_u16(const uint16_t *src, int width, int height, size_t pitch,
+                    int wx, int wy, int anchor_x, int anchor_y,
+                    uint16_t *dst, void *stream);
+int morph_dilate_u16(const uint16_t *src, int width, int height, size_t pitch,
+                     int wx, int wy, int anchor_x, int anchor_y,
+                     uint16_t *dst, void *stream);
+
+/*
+ * General single-image form: separate source/destination pitches, dtype
+ * (MORPH_U8 / MORPH_U16) and op (MORPH_ERODE / MORPH_DILATE) as codes.
+ */
+int morph_apply(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
+                int width, int height, int dtype, int op,
+                int wx, int wy, int anchor_x, int anchor_y, void *stream);
+
+/*
+ * Host-buffer form: src and dst are HOST pointers (pinned memory gives full
+ * copy speed; pageable memory works).  The library copies the image to a
+ * device staging buffer that it owns and reuses (grown on demand, one pair per
+ * device, freed by morph_release_staging), filters it, copies the result
+ * back and synchronises `stream` before returning.  Not thread-safe: calls
+ * that share a device must not run concurrently.
+ */
+int morph_apply_host(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
+                     int width, int height, int dtype, int op,
+                     int wx, int wy, int anchor_x, int anchor_y, void *stream);
+int morph_release_staging(void);
+
+/*
+ * Batched form (one launch over many independent images of different sizes,
+ * windows and ops).  Each descriptor names one device image pair.
+ */
+typedef struct {
+    const void *src;     /* device, width x height pixels, src_pitch bytes/row */
+    void *dst;           /* device, same size, dst_pitch bytes per row         */
+    int32_t width, height;
+    int64_t src_pitch, dst_pitch;
+    int16_t wx, wy, anchor_x, anchor_y;
+    uint8_t op;          /* MORPH_ERODE or MORPH_DILATE */
+    uint8_t dtype;       /* MORPH_U8 or MORPH_U16 */
+    uint8_t pad[2];
+} morph_desc;
+
+/*
+ * Runs all n images in one persistent kernel launch on `stream`.  The
+ * descriptor array is on the host; the call copies it (and the derived tile
+ * list) to device memory owned by the library, so descs may be reused as soon
+ * as the call returns.  Asynchronous.
+ */
+int morph_batch(const morph_desc *descs_host, int n, void *stream);
+
+/*
+ * Graph form of morph_batch: plan_create validates the descriptors, builds the
+ * tile list in device memory at fixed addresses and captures the persistent
+ * launch in a CUDA graph; plan_launch replays it on `stream` (one
+ * cudaGraphLaunch).  The image buffers must stay alive and at the same
+ * addresses until plan_destroy.
+ */
+int morph_batch_plan_create(const morph_desc *descs_host, int n, void **plan);
+int morph_batch_plan_launch(void *plan, void *stream);
+int morph_batch_plan_destroy(void *plan);
+
+/*
+ * Transpose (section 4): dst[x][y] = src[y][x].  src is width x height pixels
+ * with src_pitch bytes per row; dst is height x width pixels (height pixels
+ * per row, dst_pitch >= height * element size).  Device pointers, async.
+ */
+int transpose_u8(const uint8_t *src, int width, int height, size_t src_pitch,
+                 uint8_t *dst, size_t dst_pitch, void *stream);
+int transpose_u16(const uint16_t *src, int width, int height, size_t src_pitch,
+                  uint16_t *dst, size_t dst_pitch, void *stream);
+
+/*
+ * Autotuner (section 5.3's crossover, measured here rather than taken from the
+ * paper's ARM figures): times the candidate methods and tile shapes on the
+ * current device, stores the chosen crossover windows and tiles, and writes
+ * them to cache_path as JSON when it is not NULL.  When cache_path names an
+ * existing, valid cache for this device it is loaded instead of re-measured.
+ * Without a call the library uses built-in defaults.  Synchronous.
+ */
+int morph_autotune(const char *cache_path);
+
+/*
+ * Manual tuning (what morph_autotune sets): for dtype (MORPH_U8/MORPH_U16),
+ * the pass along x uses the direct method of section 5.2.2 iff wx <=
+ * cross_row and van Herk/Gil-Werman otherwise; the pass along y likewise with
+ * wy and cross_col (section 5.3's w_x^0 and w_y^0).  tile_cfg (0: 128x64,
+ * 1: 64x64, 2: 64x32, 3: 32x32 output pixels per CTA) is tried first when it
+ * fits the window.  Pass -1 to keep a value.  The result never changes, only
+ * the speed.  morph_reset_tuning restores the built-in defaults.
+ */
+int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg);
+int morph_reset_tuning(void);
+
+/* Text for a morph_status value (static storage). */
+const char *morph_status_string(int status);
+
+/*
+ * Reads and clears the device error word that kernels set when a bounded wait
+ * gives up (0 = none).  Synchronises the device.
+ */
+int morph_device_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MORPH_H */

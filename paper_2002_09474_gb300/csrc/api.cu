@@ -1,0 +1,157 @@
+// C ABI (include/morph.h): argument checks, exact window clipping, method and
+// tile choice (section 5.3's crossover), launches, host staging.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/morph.h"
+#include "morph_internal.h"
+#include "plan.h"
+
+using namespace morph;
+
+namespace {
+
+int esz_of(int dtype) { return dtype == MORPH_U8 ? 1 : dtype == MORPH_U16 ? 2 : 0; }
+
+// Byte ranges [p, p + (H-1)*pitch + W*esz) of source and destination overlap?
+bool overlaps(const void* a, size_t ap, const void* b, size_t bp, int W, int H, int esz) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+  const uintptr_t a1 = a0 + static_cast<uintptr_t>(H - 1) * ap + static_cast<uintptr_t>(W) * esz;
+  const uintptr_t b1 = b0 + static_cast<uintptr_t>(H - 1) * bp + static_cast<uintptr_t>(W) * esz;
+  return a0 < b1 && b0 < a1;
+}
+
+}  // namespace
+
+namespace morph {
+
+int validate(const void* src, size_t sp, const void* dst, size_t dp, int W, int H, int dtype, int op, int wx,
+             int wy, int ax, int ay) {
+  if (!src || !dst) return MORPH_ERR_NULL;
+  const int esz = esz_of(dtype);
+  if (!esz || (op != MORPH_ERODE && op != MORPH_DILATE)) return MORPH_ERR_DTYPE;
+  if (W < 1 || H < 1 || W > (1 << 30) || H > (1 << 30)) return MORPH_ERR_SIZE;
+  if (wx < 1 || wy < 1) return MORPH_ERR_WINDOW;
+  if (ax < 0 || ax >= wx || ay < 0 || ay >= wy) return MORPH_ERR_ANCHOR;
+  if (sp < static_cast<size_t>(W) * esz || dp < static_cast<size_t>(W) * esz) return MORPH_ERR_PITCH;
+  // 16-bit pixels must be 2-byte aligned in every row.
+  if (esz == 2 && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | sp | dp) & 1))
+    return MORPH_ERR_PITCH;
+  if (overlaps(src, sp, dst, dp, W, H, esz)) return MORPH_ERR_ALIAS;
+  return MORPH_OK;
+}
+
+// A window never needs more than n-1 cells on either side of its anchor on an
+// axis of n pixels: every output pixel's clipped window is unchanged when the
+// part beyond n-1 cells is cut off.  So (w, a) -> (a' + e' + 1, a') with
+// a' = min(a, n-1), e' = min(w-1-a, n-1) gives identical results.
+void clip_window(int n, int w, int a, int* w_out, int* a_out) {
+  const int before = std::min(a, n - 1);
+  const int after = std::min(w - 1 - a, n - 1);
+  *a_out = before;
+  *w_out = before + after + 1;
+}
+
+int run_single(const void* src, size_t sp, void* dst, size_t dp, int W, int H, int dtype, int op, int wx,
+               int wy, int ax, int ay, cudaStream_t stream) {
+  int rc = validate(src, sp, dst, dp, W, H, dtype, op, wx, wy, ax, ay);
+  if (rc != MORPH_OK) return rc;
+  FusedLaunch L;
+  L.esz = esz_of(dtype);
+  L.op = op;
+  L.src = src;
+  L.dst = dst;
+  L.sp = static_cast<long long>(sp);
+  L.dp = static_cast<long long>(dp);
+  L.W = W;
+  L.H = H;
+  clip_window(W, wx, ax, &L.wx, &L.ax);
+  clip_window(H, wy, ay, &L.wy, &L.ay);
+  if (!plan_single(&L)) return MORPH_ERR_WINDOW;
+  return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+}
+
+}  // namespace morph
+
+// ---------------------------------------------------------------------------
+// Exported entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int morph_apply(const void* src, size_t src_pitch, void* dst, size_t dst_pitch, int width, int height,
+                int dtype, int op, int wx, int wy, int anchor_x, int anchor_y, void* stream) {
+  return run_single(src, src_pitch, dst, dst_pitch, width, height, dtype, op, wx, wy, anchor_x, anchor_y,
+                    static_cast<cudaStream_t>(stream));
+}
+
+int morph_erode(const uint8_t* src, int width, int height, size_t pitch, int wx, int wy, int anchor_x,
+                int anchor_y, uint8_t* dst, void* stream) {
+  return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U8, MORPH_ERODE, wx, wy, anchor_x, anchor_y,
+                     stream);
+}
+
+int morph_dilate(const uint8_t* src, int width, int height, size_t pitch, int wx, int wy, int anchor_x,
+                 int anchor_y, uint8_t* dst, void* stream) {
+  return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U8, MORPH_DILATE, wx, wy, anchor_x,
+                     anchor_y, stream);
+}
+
+int morph_erode_u16(const uint16_t* src, int width, int height, size_t pitch, int wx, int wy, int anchor_x,
+                    int anchor_y, uint16_t* dst, void* stream) {
+  return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U16, MORPH_ERODE, wx, wy, anchor_x,
+                     anchor_y, stream);
+}
+
+int morph_dilate_u16(const uint16_t* src, int width, int height, size_t pitch, int wx, int wy, int anchor_x,
+                     int anchor_y, uint16_t* dst, void* stream) {
+  return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U16, MORPH_DILATE, wx, wy, anchor_x,
+                     anchor_y, stream);
+}
+
+int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg) {
+  const int esz = esz_of(dtype);
+  if (!esz) return MORPH_ERR_DTYPE;
+  if (tile_cfg < -1 || tile_cfg >= kNumTileCfg) return MORPH_ERR_ARG;
+  Tuning& t = tuning();
+  if (cross_row >= 0) t.cross_row[esz - 1] = cross_row;
+  if (cross_col >= 0) t.cross_col[esz - 1] = cross_col;
+  if (tile_cfg >= 0) {
+    int* order = t.cfg_order[esz - 1];
+    int k = 0;
+    while (order[k] != tile_cfg) ++k;
+    for (; k > 0; --k) order[k] = order[k - 1];
+    order[0] = tile_cfg;
+  }
+  return MORPH_OK;
+}
+
+int morph_reset_tuning(void) {
+  reset_tuning_defaults();
+  return MORPH_OK;
+}
+
+const char* morph_status_string(int status) {
+  switch (status) {
+    case MORPH_OK: return "ok";
+    case MORPH_ERR_NULL: return "null pointer";
+    case MORPH_ERR_SIZE: return "invalid image size";
+    case MORPH_ERR_WINDOW: return "invalid or unsupported window size";
+    case MORPH_ERR_ANCHOR: return "anchor outside the window";
+    case MORPH_ERR_PITCH: return "pitch smaller than a row";
+    case MORPH_ERR_ALIAS: return "source and destination overlap";
+    case MORPH_ERR_CUDA: return "CUDA error";
+    case MORPH_ERR_NOMEM: return "out of memory";
+    case MORPH_ERR_DTYPE: return "unknown dtype or op";
+    case MORPH_ERR_ARG: return "invalid argument";
+    case MORPH_ERR_DEVICE: return "device-side error reported by a kernel";
+  }
+  return "unknown status";
+}
+
+int morph_device_error(void) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return MORPH_ERR_CUDA;
+  return fused_take_device_error();
+}
+
+}  // extern "C"

@@ -1,0 +1,146 @@
+// Device helpers shared by the morphology kernels (sm_103a).
+//
+// Pixels travel packed in 32-bit words: four 8-bit pixels or two 16-bit
+// pixels, lowest address in the lowest byte.  One packed min/max handles a
+// whole word, the GPU counterpart of the paper's 16-lane vminq_u8/vmaxq_u8
+// (section 3, section 5.1.1).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace morph {
+
+// Codes a kernel writes to its device error word.
+enum : int {
+  kDevErrNone = 0,
+  kDevErrTmaTimeout = 1,  // a TMA load did not complete within the wait limit
+  kDevErrBadTile = 2,     // a work item named a tile outside its image
+};
+
+// Wall-clock limit of every bounded wait (nanoseconds, %globaltimer).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+template <typename T> struct Pix;
+template <> struct Pix<uint8_t> {
+  static constexpr int PK = 4;          // pixels per 32-bit word
+  static constexpr uint32_t MAXV = 0xFFu;
+};
+template <> struct Pix<uint16_t> {
+  static constexpr int PK = 2;
+  static constexpr uint32_t MAXV = 0xFFFFu;
+};
+
+// Identity of the operation on a packed word: all ones never lowers a min
+// (erosion), zero never raises a max (dilation).
+template <int OP> __host__ __device__ constexpr uint32_t ident_word() {
+  return OP == 0 ? 0xFFFFFFFFu : 0u;
+}
+
+// Lane-wise min (OP 0, erosion) or max (OP 1, dilation) of two packed words.
+template <typename T, int OP> __device__ __forceinline__ uint32_t pop(uint32_t a, uint32_t b);
+template <> __device__ __forceinline__ uint32_t pop<uint8_t, 0>(uint32_t a, uint32_t b) { return __vminu4(a, b); }
+template <> __device__ __forceinline__ uint32_t pop<uint8_t, 1>(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
+template <> __device__ __forceinline__ uint32_t pop<uint16_t, 0>(uint32_t a, uint32_t b) { return __vminu2(a, b); }
+template <> __device__ __forceinline__ uint32_t pop<uint16_t, 1>(uint32_t a, uint32_t b) { return __vmaxu2(a, b); }
+
+// In-register transpose of a PK x PK block of pixels held as PK words.
+// On entry v[i] holds row i (pixel j in lane j); on exit v[j] holds column j
+// (row i in lane i).  4x4 bytes: two butterfly rounds of byte permutes, first
+// interleaving bytes of row pairs, then 16-bit halves of those pairs -- the
+// same two-level 2x2 block transpose as the paper's vtrn-based 8x8.16 and
+// 16x16.8 transposes (section 4), on 4-byte registers.
+__device__ __forceinline__ void transpose_block(uint32_t (&v)[4]) {
+  const uint32_t a0 = __byte_perm(v[0], v[1], 0x5140);  // r0.b0 r1.b0 r0.b1 r1.b1
+  const uint32_t a1 = __byte_perm(v[0], v[1], 0x7362);  // r0.b2 r1.b2 r0.b3 r1.b3
+  const uint32_t b0 = __byte_perm(v[2], v[3], 0x5140);  // r2.b0 r3.b0 r2.b1 r3.b1
+  const uint32_t b1 = __byte_perm(v[2], v[3], 0x7362);  // r2.b2 r3.b2 r2.b3 r3.b3
+  v[0] = __byte_perm(a0, b0, 0x5410);                   // column 0
+  v[1] = __byte_perm(a0, b0, 0x7632);                   // column 1
+  v[2] = __byte_perm(a1, b1, 0x5410);                   // column 2
+  v[3] = __byte_perm(a1, b1, 0x7632);                   // column 3
+}
+// 2x2 block of 16-bit pixels.
+__device__ __forceinline__ void transpose_block(uint32_t (&v)[2]) {
+  const uint32_t c0 = __byte_perm(v[0], v[1], 0x5410);  // r0.p0 r1.p0
+  const uint32_t c1 = __byte_perm(v[0], v[1], 0x7632);  // r0.p1 r1.p1
+  v[0] = c0;
+  v[1] = c1;
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory / TMA / mbarrier wrappers (inline PTX).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes the barrier initialisation visible to the TMA unit (async proxy).
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the barrier phase with the given parity to complete; gives up
+// after kWaitLimitNs and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  unsigned ns = 32;
+  while (!mbar_test_wait(bar, parity)) {
+    if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+  return true;
+}
+
+// 2-D tiled TMA load of one box into shared memory, completing on `bar`.
+// x must be a multiple of 16 bytes / element size (caller's contract).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (TMA) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+}  // namespace morph

@@ -1,0 +1,46 @@
+// Host-side interfaces between the C-ABI layer and the kernel translation
+// units (not part of the public ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace morph {
+
+// Output tile shapes the fused kernel is built for (TX x TY pixels).
+enum TileCfg : int { kTile128x64 = 0, kTile64x64 = 1, kTile64x32 = 2, kTile32x32 = 3, kNumTileCfg = 4 };
+inline int tile_tx(int cfg) { return cfg == kTile128x64 ? 128 : cfg == kTile32x32 ? 32 : 64; }
+inline int tile_ty(int cfg) { return cfg == kTile128x64 || cfg == kTile64x64 ? 64 : 32; }
+
+// Largest dynamic shared memory a CTA may use on sm_103a (bytes).
+constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // leave room for static smem
+
+// One single-image launch of the fused kernel, fully resolved.
+struct FusedLaunch {
+  int esz;             // 1 or 2
+  int op;              // 0 erode, 1 dilate
+  int cfg;             // TileCfg
+  const void* src;
+  void* dst;
+  long long sp, dp;
+  int W, H;
+  int wx, wy, ax, ay;  // clipped window
+  bool vhgw_col, vhgw_row;
+};
+
+// Shared-memory bytes the fused kernel needs for this launch (0 if the
+// configuration is invalid).
+int fused_smem_bytes(const FusedLaunch& L);
+// Enqueues the fused kernel; returns a cudaError_t.
+cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream);
+// Reads and clears the fused kernels' device error word.
+int fused_take_device_error();
+
+// Encodes a 2-D tiled tensor map over a pitched image (driver entry point
+// resolved through the runtime).  Returns false if TMA cannot describe it.
+bool encode_tensor_map_2d(CUtensorMap* map, const void* base, int esz, int W, int H, long long pitch,
+                          int box_w, int box_h);
+
+}  // namespace morph

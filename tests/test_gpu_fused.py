@@ -1,0 +1,149 @@
+"""GPU parity of the fused single-image path against the CPU oracle.
+
+Bit-exact (integer min/max): every case compares all pixels with the
+oracle's brute-force definition (section 2), with both pass methods forced in
+turn (direct, section 5.1.2/5.2.2; van Herk/Gil-Werman, 5.1.1/5.2.1), every
+tile shape, ragged image edges, pitched and unaligned buffers, and guard
+bytes around the destination.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_09474_gb300 import synth
+
+from gpu_util import DeviceImage, need_cuda
+
+pytestmark = pytest.mark.gpu
+
+OPS = {"erode": 0, "dilate": 1}
+DIRECT, VHGW = 10**6, 0  # crossover values that force one method on both passes
+
+
+@pytest.fixture(scope="module")
+def lib():
+    need_cuda()
+    from paper_2002_09474_gb300 import morph
+    yield morph
+    morph.morph_reset_tuning()
+
+
+def run(lib, torch, img, wx, wy, ax, ay, op, pad=0, offset=0, dst_pad=None, dst_offset=0):
+    h, w = img.shape
+    src = DeviceImage(torch, h, w, img.dtype, pad=pad, offset=offset, fill=img)
+    dst = DeviceImage(torch, h, w, img.dtype, pad=pad if dst_pad is None else dst_pad,
+                      offset=dst_offset)
+    dtype = lib.MORPH_U8 if img.dtype == np.uint8 else lib.MORPH_U16
+    rc = lib.morph_apply(src.ptr, src.pitch, dst.ptr, dst.pitch, w, h, dtype, OPS[op],
+                         wx, wy, ax, ay, 0)
+    assert rc == 0, lib.status_string(rc)
+    torch.cuda.synchronize()
+    assert dst.untouched_outside(), "kernel wrote outside the destination image"
+    assert src.untouched_outside()
+    return dst.read()
+
+
+def set_methods(lib, dtype, col, row, cfg=-1):
+    code = lib.MORPH_U8 if dtype == np.uint8 else lib.MORPH_U16
+    assert lib.morph_set_tuning(code, row, col, cfg) == 0
+
+
+SHAPES = [(1, 1), (2, 3), (5, 17), (33, 7), (67, 130), (129, 257), (200, 300)]
+WINDOWS = [(1, 1), (3, 3), (2, 5), (7, 1), (1, 9), (4, 4), (15, 15), (31, 7), (61, 61)]
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("method", ["direct", "vhgw", "mixed"])
+def test_shapes_windows_methods(lib, dtype, method):
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    col, row = {"direct": (DIRECT, DIRECT), "vhgw": (VHGW, VHGW), "mixed": (DIRECT, VHGW)}[method]
+    set_methods(lib, dtype, col, row)
+    g = synth.rng(100 + (dtype == np.uint16))
+    for (h, w) in SHAPES:
+        img = synth.uniform_image(w, h, dtype, gen=g)
+        for (wx, wy) in WINDOWS:
+            ax, ay = wx // 2, wy // 2
+            for op in ("erode", "dilate"):
+                got = run(lib, torch, img, wx, wy, ax, ay, op)
+                want = oracle.morph(img, wx, wy, ax, ay, op)
+                assert np.array_equal(got, want), (h, w, wx, wy, op, method)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+def test_every_tile_shape(lib, dtype, cfg):
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    g = synth.rng(110 + cfg)
+    img = synth.uniform_image(301, 177, dtype, gen=g)
+    for method in ("direct", "vhgw"):
+        c = DIRECT if method == "direct" else VHGW
+        set_methods(lib, dtype, c, c, cfg)
+        for (wx, wy, ax, ay) in ((3, 5, 1, 2), (8, 2, 7, 0), (21, 51, 10, 25), (101, 1, 50, 0)):
+            for op in ("erode", "dilate"):
+                got = run(lib, torch, img, wx, wy, ax, ay, op)
+                want = oracle.morph(img, wx, wy, ax, ay, op)
+                assert np.array_equal(got, want), (cfg, method, wx, wy, op)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_all_anchors_even_and_odd(lib, dtype):
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    g = synth.rng(120)
+    img = synth.uniform_image(70, 45, dtype, gen=g)
+    for method in ("direct", "vhgw"):
+        c = DIRECT if method == "direct" else VHGW
+        set_methods(lib, dtype, c, c)
+        for (wx, wy) in ((4, 3), (6, 6), (5, 2)):
+            for ax, ay in itertools.product(range(wx), range(wy)):
+                got = run(lib, torch, img, wx, wy, ax, ay, "erode")
+                want = oracle.morph(img, wx, wy, ax, ay, "erode")
+                assert np.array_equal(got, want), (method, wx, wy, ax, ay)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_pitched_and_unaligned_buffers(lib, dtype):
+    """16-byte-aligned pitches take the TMA path; others the plain-load path;
+    odd byte offsets force per-pixel loads and stores."""
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    g = synth.rng(130)
+    img = synth.uniform_image(150, 90, dtype, gen=g)
+    esz = np.dtype(dtype).itemsize
+    cases = [(0, 0, 0, 0), (16 - (150 * esz) % 16, 0, 32, 0), (13 * esz, 0, 13 * esz, 0),
+             (6, 4, 2, 8), (esz, esz, 3 * esz, esz)]
+    for pad, off, dpad, doff in cases:
+        for (wx, wy) in ((3, 3), (17, 9), (40, 40)):
+            for op in ("erode", "dilate"):
+                got = run(lib, torch, img, wx, wy, wx // 2, wy // 2, op, pad=pad, offset=off,
+                          dst_pad=dpad, dst_offset=doff)
+                want = oracle.morph(img, wx, wy, wx // 2, wy // 2, op)
+                assert np.array_equal(got, want), (pad, off, dpad, doff, wx, wy, op)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_windows_larger_than_image(lib, dtype):
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    g = synth.rng(140)
+    img = synth.uniform_image(37, 23, dtype, gen=g)
+    for (wx, wy, ax, ay) in ((75, 47, 37, 23), (200, 3, 0, 1), (3, 500, 2, 499), (1000, 1000, 1, 998)):
+        for op in ("erode", "dilate"):
+            got = run(lib, torch, img, wx, wy, ax, ay, op)
+            want = oracle.morph(img, wx, wy, ax, ay, op)
+            assert np.array_equal(got, want), (wx, wy, ax, ay, op)
+
+
+def test_constant_and_extreme_values(lib):
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    for dtype in (np.uint8, np.uint16):
+        mx = np.iinfo(dtype).max
+        for v in (0, 1, mx - 1, mx):
+            img = np.full((40, 50), v, dtype)
+            for op in ("erode", "dilate"):
+                assert np.array_equal(run(lib, torch, img, 5, 7, 2, 3, op), img)
