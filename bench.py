@@ -1,0 +1,403 @@
+"""Benchmark: erosion/dilation throughput (Gpixel/s) and fraction of the HBM
+roofline on the 4096x4096 workload, through the C ABI.
+
+Workload (one step): 4096x4096 images in uint8 and uint16, each a uniform
+random image and a smooth gradient with noise (synthetic, seeded); windows
+1x101, 101x1, 21x51 and 127x127 (wx x wy, anchor at the centre); erosion and
+dilation of each -- 32 single-image calls.  Every call reads a different copy
+of its input (8 rotating copies per image), so inputs come from HBM, not L2
+(129 MB).  Inputs are resident in device memory when timing starts.
+
+Reported (one JSON line on rank 0):
+  value        whole-job Gpixel/s (output pixels of all ranks / max time)
+  roofline     the dominant kernel class: algorithmic bytes (read + write one
+               image) / its mean CUDA-event launch time, against the measured
+               HBM copy bandwidth
+  e2e          the same step through morph_apply_host with pinned host buffers
+               (host->device and device->host copies inside the timed region)
+  cpu_baseline the brute-force CPU oracle on a bounded sample of the step
+  breakdown    per (dtype, window) class: mean us per call, Gpixel/s, GB/s
+``--impl reference`` times the CPU oracle alone (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2002_09474_gb300 import synth  # noqa: E402
+
+SIDE = 4096
+WINDOWS = synth.C3_WINDOWS  # (wx, wy)
+OPS = (0, 1)                # erode, dilate
+DTYPES = (np.uint8, np.uint16)
+IMAGES = ("uniform", "gradient")
+ROTATE = 8                  # input copies per image (defeats L2 reuse)
+METRIC = "erosion/dilation Gpixel/s (4096x4096 u8+u16, 4 windows, erode+dilate)"
+UNIT = "Gpixel/s"
+KERNEL_SOURCES = ("morph_tile.cuh", "morph_common.cuh", "morph_fused.cu")
+
+
+def workload_config():
+    return {"workload": "4096x4096 u8+u16 (uniform, gradient+noise), windows 1x101 101x1 21x51 "
+                        "127x127, erode+dilate: 32 calls per step",
+            "image": [SIDE, SIDE], "windows_wx_wy": [list(w) for w in WINDOWS],
+            "dtypes": ["u8", "u16"], "ops": ["erode", "dilate"], "calls_per_step": 32,
+            "l2": "inputs rotate over %d copies per image (>1 GB between reuses of a copy)" % ROTATE}
+
+
+def step_runs():
+    """The 32 calls of one step: (dtype, image kind, (wx, wy), op)."""
+    return [(dt, kind, w, op) for dt in DTYPES for kind in IMAGES for w in WINDOWS for op in OPS]
+
+
+def make_image(dtype, kind):
+    seed = 3 if dtype == np.uint8 else 4
+    if kind == "uniform":
+        return synth.uniform_image(SIDE, SIDE, dtype, seed=seed)
+    return synth.gradient_image(SIDE, SIDE, dtype, seed=seed + 100)
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2002_09474_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def load_traffic(kernel_class: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_hash") != kernel_hash():
+        return None
+    v = t.get("classes", {}).get(kernel_class)
+    return None if v is None else float(v)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", self.gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for_smi(torch) -> str:
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[0] if vis else "0"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_sample(images, target_ops: float = 1.5e9, seed: int = 7):
+    """Times the brute-force oracle on sampled output pixels of every call of
+    the step and extrapolates the step's CPU time.  Returns (Gpixel/s,
+    threads, seconds spent, description)."""
+    import oracle
+    g = synth.rng(seed)
+    est_step_s = 0.0
+    spent = 0.0
+    npts_total = 0
+    for (dt, kind, (wx, wy), op) in step_runs():
+        img = images[(dt, kind)]
+        n = int(max(256, min(SIDE * SIDE, target_ops / (wx * wy))))
+        xs = g.integers(0, SIDE, size=n)
+        ys = g.integers(0, SIDE, size=n)
+        t0 = time.perf_counter()
+        oracle.morph_points(img, wx, wy, wx // 2, wy // 2, op, xs, ys)
+        dt_s = time.perf_counter() - t0
+        spent += dt_s
+        npts_total += n
+        est_step_s += dt_s * (SIDE * SIDE) / n
+    step_px = len(step_runs()) * SIDE * SIDE
+    desc = ("brute-force oracle (section 2 definition) at %d random output pixels of the "
+            "step's 32 calls (about %.1e window cells per call), step time extrapolated by "
+            "pixel count" % (npts_total, target_ops))
+    return step_px / est_step_s / 1e9, oracle.num_threads(), spent, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    images = {(dt, k): make_image(dt, k) for dt in DTYPES for k in IMAGES}
+    for _ in range(args.warmup):
+        oracle_sample(images, target_ops=5e7)
+    vals, spent_total, desc, cores = [], 0.0, "", 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, spent, desc = oracle_sample(images, target_ops=5e7)
+        vals.append(v)
+        spent_total += spent
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    step_px = len(step_runs()) * SIDE * SIDE
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_px / (value * 1e9) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def reduce_over_ranks(torch, dist, value: float, op: str) -> float:
+    """max or sum of a float over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized():
+        return value
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+
+    from paper_2002_09474_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2002_09474_gb300 import morph
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    host_imgs = {(dt, k): make_image(dt, k) for dt in DTYPES for k in IMAGES}
+    tdt = {np.uint8: torch.uint8, np.uint16: torch.uint16}
+    srcs = {}
+    for key, im in host_imgs.items():
+        base = torch.from_numpy(im).to(dev)
+        srcs[key] = [base] + [base.clone() for _ in range(ROTATE - 1)]
+    dsts = {dt: [torch.empty((SIDE, SIDE), dtype=tdt[dt], device=dev) for _ in range(ROTATE)]
+            for dt in DTYPES}
+    runs = step_runs()
+    ctr = {"src": {k: 0 for k in srcs}, "dst": {dt: 0 for dt in DTYPES}}
+
+    def launch(run):
+        dt, kind, (wx, wy), op = run
+        key = (dt, kind)
+        i = ctr["src"][key]
+        ctr["src"][key] = (i + 1) % ROTATE
+        j = ctr["dst"][dt]
+        ctr["dst"][dt] = (j + 1) % ROTATE
+        s, d = srcs[key][i], dsts[dt][j]
+        code = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
+        pitch = SIDE * np.dtype(dt).itemsize
+        rc = morph.morph_apply(s.data_ptr(), pitch, d.data_ptr(), pitch, SIDE, SIDE, code, op,
+                               wx, wy, wx // 2, wy // 2, sh)
+        if rc != 0:
+            raise morph.MorphError("morph_apply", rc)
+
+    for _ in range(args.warmup):
+        for r in runs:
+            launch(r)
+    torch.cuda.synchronize()
+
+    # timed region: per-launch events on the launching stream
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in runs] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_id_for_smi(torch))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record(stream)
+    for k in range(args.steps):
+        for r, (e0, e1) in zip(runs, ev[k]):
+            e0.record(stream)
+            launch(r)
+            e1.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    max_ms = reduce_over_ranks(torch, dist, elapsed_ms, "max")
+    step_px = len(runs) * SIDE * SIDE
+    total_px = reduce_over_ranks(torch, dist, float(step_px * args.steps), "sum")
+    value = total_px / (max_ms * 1e-3) / 1e9
+
+    # per-class launch times
+    per = {}
+    for k in range(args.steps):
+        for r, (e0, e1) in zip(runs, ev[k]):
+            dt, _, (wx, wy), _ = r
+            per.setdefault((dt, wx, wy), []).append(e0.elapsed_time(e1))
+    peak, peak_kind = load_peaks()
+    breakdown = {}
+    dom, dom_total = None, -1.0
+    for (dt, wx, wy), ts in per.items():
+        esz = np.dtype(dt).itemsize
+        mean_ms = statistics.mean(ts)
+        name = "%s_%dx%d" % ("u8" if dt == np.uint8 else "u16", wx, wy)
+        gbs = 2 * esz * SIDE * SIDE / (mean_ms * 1e-3) / 1e9
+        breakdown[name] = {"us_per_call": round(mean_ms * 1e3, 2),
+                           "gpix_s": round(SIDE * SIDE / (mean_ms * 1e-3) / 1e9, 1),
+                           "gb_s": round(gbs, 1), "frac_of_%s_hbm" % peak_kind: round(gbs / peak, 3)}
+        if sum(ts) > dom_total:
+            dom_total, dom = sum(ts), (name, gbs)
+
+    # end to end through the host-buffer entry point
+    pinned_in = {k: torch.from_numpy(v).pin_memory() for k, v in host_imgs.items()}
+    pinned_out = {dt: torch.empty((SIDE, SIDE), dtype=tdt[dt]).pin_memory() for dt in DTYPES}
+    e2e_steps = max(3, args.steps // 10)
+
+    def e2e_step():
+        for dt, kind, (wx, wy), op in runs:
+            s, d = pinned_in[(dt, kind)], pinned_out[dt]
+            code = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
+            pitch = SIDE * np.dtype(dt).itemsize
+            rc = morph.morph_apply_host(s.data_ptr(), pitch, d.data_ptr(), pitch, SIDE, SIDE,
+                                        code, op, wx, wy, wx // 2, wy // 2, sh)
+            if rc != 0:
+                raise morph.MorphError("morph_apply_host", rc)
+    e2e_step()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = reduce_over_ranks(torch, dist, time.perf_counter() - t0, "max")
+    e2e_px = reduce_over_ranks(torch, dist, float(step_px * e2e_steps), "sum")
+    io_bytes = sum(SIDE * SIDE * np.dtype(dt).itemsize for dt, _, _, _ in runs)
+    morph.morph_release_staging()
+    morph.check_device_error()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8+u16 (integer min/max)",
+                "data": "synthetic (seeded uniform and gradient+noise images)",
+                "config": dict(workload_config(), parallelism="replicas" if world > 1 else "single"),
+                "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": round(dom[1], 1),
+                             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                             "frac": round(dom[1] / peak, 4),
+                             "traffic": load_traffic(dom[0])},
+                "e2e": {"value": round(e2e_px / e2e_s / 1e9, 3), "unit": UNIT,
+                        "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+                        "api": "morph_apply_host, pinned host buffers"},
+                "gpu_launches": len(runs) * args.steps,
+                "clocks": clk,
+                "breakdown": breakdown}
+        if not args.no_cpu_baseline:
+            v, cores, spent, desc = oracle_sample(host_imgs)
+            line["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": cores,
+                                    "kind": "oracle", "sample": desc, "seconds": round(spent, 1)}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the CPU oracle sample (for profiler runs)")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -172,10 +172,12 @@ int morph_autotune(const char *cache_path);
  * Manual tuning (what morph_autotune sets): for dtype (MORPH_U8/MORPH_U16),
  * the pass along x uses the direct method of section 5.2.2 iff wx <=
  * cross_row and van Herk/Gil-Werman otherwise; the pass along y likewise with
- * wy and cross_col (section 5.3's w_x^0 and w_y^0).  tile_cfg (0: 128x64,
- * 1: 64x64, 2: 64x32, 3: 32x32 output pixels per CTA) is tried first when it
- * fits the window.  Pass -1 to keep a value.  The result never changes, only
- * the speed.  morph_reset_tuning restores the built-in defaults.
+ * wy and cross_col (section 5.3's w_x^0 and w_y^0); a negative crossover
+ * keeps the current value.  tile_cfg selects the output tile per CTA when it
+ * fits the window in shared memory (0: 128x64, 1: 64x64, 2: 64x128,
+ * 3: 256x32, 4: 32x32, 5: 32x128 pixels); -1 lets a built-in cost model pick
+ * per call.  The result never changes, only the speed.  morph_reset_tuning
+ * restores the built-in defaults.
  */
 int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg);
 int morph_reset_tuning(void);

@@ -72,6 +72,39 @@ int run_single(const void* src, size_t sp, void* dst, size_t dp, int W, int H, i
   return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
 }
 
+// Device staging buffers of morph_apply_host: one input/output pair per
+// device, grown on demand and kept until morph_release_staging.
+struct Staging {
+  void* in = nullptr;
+  void* out = nullptr;
+  size_t bytes = 0;
+};
+constexpr int kMaxDevices = 64;
+Staging g_staging[kMaxDevices];
+std::mutex g_staging_mu;
+
+int stage_buffers(size_t bytes, void** in, void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MORPH_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_staging_mu);
+  Staging& s = g_staging[dev];
+  if (s.bytes < bytes) {
+    if (s.in) cudaFree(s.in);
+    if (s.out) cudaFree(s.out);
+    s = Staging();
+    if (cudaMalloc(&s.in, bytes) != cudaSuccess) return MORPH_ERR_NOMEM;
+    if (cudaMalloc(&s.out, bytes) != cudaSuccess) {
+      cudaFree(s.in);
+      s.in = nullptr;
+      return MORPH_ERR_NOMEM;
+    }
+    s.bytes = bytes;
+  }
+  *in = s.in;
+  *out = s.out;
+  return MORPH_OK;
+}
+
 }  // namespace morph
 
 // ---------------------------------------------------------------------------
@@ -116,18 +149,49 @@ int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg) {
   Tuning& t = tuning();
   if (cross_row >= 0) t.cross_row[esz - 1] = cross_row;
   if (cross_col >= 0) t.cross_col[esz - 1] = cross_col;
-  if (tile_cfg >= 0) {
-    int* order = t.cfg_order[esz - 1];
-    int k = 0;
-    while (order[k] != tile_cfg) ++k;
-    for (; k > 0; --k) order[k] = order[k - 1];
-    order[0] = tile_cfg;
-  }
+  if (tile_cfg >= -1) t.forced_cfg[esz - 1] = tile_cfg;
   return MORPH_OK;
 }
 
 int morph_reset_tuning(void) {
   reset_tuning_defaults();
+  return MORPH_OK;
+}
+
+int morph_apply_host(const void* src, size_t src_pitch, void* dst, size_t dst_pitch, int width, int height,
+                     int dtype, int op, int wx, int wy, int anchor_x, int anchor_y, void* stream) {
+  // Host buffers may overlap-check like device ones; the staging copies do not.
+  int rc = validate(src, src_pitch, dst, dst_pitch, width, height, dtype, op, wx, wy, anchor_x, anchor_y);
+  if (rc != MORPH_OK) return rc;
+  const int esz = esz_of(dtype);
+  const size_t row = static_cast<size_t>(width) * esz;
+  const size_t pitch = (row + 15) / 16 * 16;  // 16-byte rows: the TMA path
+  void *din = nullptr, *dout = nullptr;
+  rc = stage_buffers(pitch * static_cast<size_t>(height), &din, &dout);
+  if (rc != MORPH_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpy2DAsync(din, pitch, src, src_pitch, row, height, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return MORPH_ERR_CUDA;
+  rc = run_single(din, pitch, dout, pitch, width, height, dtype, op, wx, wy, anchor_x, anchor_y, st);
+  if (rc != MORPH_OK) return rc;
+  if (cudaMemcpy2DAsync(dst, dst_pitch, dout, pitch, row, height, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return MORPH_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+}
+
+int morph_release_staging(void) {
+  std::lock_guard<std::mutex> lock(g_staging_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < kMaxDevices; ++d) {
+    Staging& s = g_staging[d];
+    if (!s.in && !s.out) continue;
+    cudaSetDevice(d);
+    if (s.in) cudaFree(s.in);
+    if (s.out) cudaFree(s.out);
+    s = Staging();
+  }
+  cudaSetDevice(cur);
   return MORPH_OK;
 }
 

@@ -1,4 +1,5 @@
 // Single-image fused erosion/dilation kernel: one CTA per output tile.
+#include <cstring>
 #include <mutex>
 
 #include <cudaTypedefs.h>
@@ -11,30 +12,34 @@ namespace morph {
 __device__ int g_fused_err;
 
 template <typename T, int OP, int TX, int TY>
-__global__ void __launch_bounds__(kThreads) fused_kernel(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(kThreads, 2) fused_kernel(const __grid_constant__ CUtensorMap tin,
+                                                         const __grid_constant__ CUtensorMap tout,
                                                          const ImgArgs a, const Geom g) {
   __shared__ __align__(8) uint64_t bar;
-  extern __shared__ __align__(128) uint32_t smem[];
-  if (a.tma && threadIdx.x == 0) {
+  extern __shared__ __align__(128) uint4 smem[];
+  if (a.tma_ld && threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
   }
   __syncthreads();
   uint32_t phase = 0;
-  run_tile<T, OP, TX, TY>(a, &tin, blockIdx.x * TX, blockIdx.y * TY, g, smem, &bar, phase, &g_fused_err);
+  run_tile<T, OP, TX, TY>(a, &tin, &tout, blockIdx.x * TX, blockIdx.y * TY, g, smem, &bar, phase,
+                          &g_fused_err);
 }
 
 namespace {
 
-using KernelFn = void (*)(const CUtensorMap, const ImgArgs, const Geom);
+using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const ImgArgs, const Geom);
 
 template <typename T, int OP>
 KernelFn pick_kernel(int cfg) {
   switch (cfg) {
     case kTile128x64: return fused_kernel<T, OP, 128, 64>;
     case kTile64x64: return fused_kernel<T, OP, 64, 64>;
-    case kTile64x32: return fused_kernel<T, OP, 64, 32>;
+    case kTile64x128: return fused_kernel<T, OP, 64, 128>;
+    case kTile256x32: return fused_kernel<T, OP, 256, 32>;
     case kTile32x32: return fused_kernel<T, OP, 32, 32>;
+    case kTile32x128: return fused_kernel<T, OP, 32, 128>;
   }
   return nullptr;
 }
@@ -79,17 +84,15 @@ bool encode_tensor_map_2d(CUtensorMap* map, const void* base, int esz, int W, in
 
 int fused_smem_bytes(const FusedLaunch& L) {
   if (L.cfg < 0 || L.cfg >= kNumTileCfg) return 0;
-  Geom g = make_geom(L.esz, tile_tx(L.cfg), tile_ty(L.cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
-  return g.smem_bytes;
+  return make_geom(L.esz, tile_tx(L.cfg), tile_ty(L.cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row).smem_bytes;
 }
 
 cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int TX = tile_tx(L.cfg), TY = tile_ty(L.cfg);
-  Geom g = make_geom(L.esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
+  const Geom g = make_geom(L.esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
   if (g.smem_bytes > kMaxSmemBytes) return cudaErrorInvalidConfiguration;
   KernelFn k = kernel_for(L.esz, L.op, L.cfg);
   if (!k) return cudaErrorInvalidValue;
-  // Opt in to large dynamic shared memory once per kernel.
   static bool opted[2][2][kNumTileCfg] = {};
   bool& done = opted[L.esz - 1][L.op][L.cfg];
   if (!done) {
@@ -108,15 +111,18 @@ cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
   a.wy = L.wy;
   a.ax = L.ax;
   a.ay = L.ay;
-  a.vhgw_col = L.vhgw_col;
-  a.vhgw_row = L.vhgw_row;
+  a.blk_y = L.vhgw_col && L.wy > 1;
+  a.blk_x = L.vhgw_row && L.wx > 1;
   a.ld_vec = (reinterpret_cast<uintptr_t>(L.src) % 4 == 0) && (L.sp % 4 == 0);
   a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % 4 == 0) && (L.dp % 4 == 0);
-  CUtensorMap tin;
+  CUtensorMap tin, tout;
   memset(&tin, 0, sizeof(tin));
-  a.tma = encode_tensor_map_2d(&tin, L.src, L.esz, L.W, L.H, L.sp, 128 / L.esz, g.bh) ? 1 : 0;
+  memset(&tout, 0, sizeof(tout));
+  a.tma_ld = encode_tensor_map_2d(&tin, L.src, L.esz, L.W, L.H, L.sp, 128 / L.esz, g.bh) ? 1 : 0;
+  const int sbox = TX * L.esz < 128 ? TX * L.esz : 128;
+  a.tma_st = encode_tensor_map_2d(&tout, L.dst, L.esz, L.W, L.H, L.dp, sbox / L.esz, TY) ? 1 : 0;
   dim3 grid(cdiv(L.W, TX), cdiv(L.H, TY));
-  k<<<grid, kThreads, g.smem_bytes, stream>>>(tin, a, g);
+  k<<<grid, kThreads, g.smem_bytes, stream>>>(tin, tout, a, g);
   return cudaGetLastError();
 }
 

@@ -9,10 +9,25 @@
 
 namespace morph {
 
-// Output tile shapes the fused kernel is built for (TX x TY pixels).
-enum TileCfg : int { kTile128x64 = 0, kTile64x64 = 1, kTile64x32 = 2, kTile32x32 = 3, kNumTileCfg = 4 };
-inline int tile_tx(int cfg) { return cfg == kTile128x64 ? 128 : cfg == kTile32x32 ? 32 : 64; }
-inline int tile_ty(int cfg) { return cfg == kTile128x64 || cfg == kTile64x64 ? 64 : 32; }
+// Output tile shapes the fused kernel is built for (TX x TY pixels): square,
+// tall (for long windows along y) and wide (for long windows along x).
+enum TileCfg : int {
+  kTile128x64 = 0,
+  kTile64x64 = 1,
+  kTile64x128 = 2,
+  kTile256x32 = 3,
+  kTile32x32 = 4,
+  kTile32x128 = 5,
+  kNumTileCfg = 6
+};
+inline int tile_tx(int cfg) {
+  static const int tx[kNumTileCfg] = {128, 64, 64, 256, 32, 32};
+  return tx[cfg];
+}
+inline int tile_ty(int cfg) {
+  static const int ty[kNumTileCfg] = {64, 64, 128, 32, 32, 128};
+  return ty[cfg];
+}
 
 // Largest dynamic shared memory a CTA may use on sm_103a (bytes).
 constexpr int kMaxSmemBytes = 227 * 1024 - 1024;  // leave room for static smem

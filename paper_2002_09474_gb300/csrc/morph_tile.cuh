@@ -1,41 +1,74 @@
 // Fused two-pass erosion/dilation of one output tile (sm_103a).
 //
-// A CTA computes a TX x TY tile of D (paper section 2) in shared memory:
+// A CTA computes a TX x TY tile of D (paper section 2) in shared memory.
+// Work units are "octets": 8 consecutive pixels of one row, held in registers
+// as four 32-bit words of two 16-bit lanes, so one min.u16x2 / max.u16x2
+// handles two pixels (on sm_103a the byte-wise __vminu4 costs several
+// instructions, the 16x2 form one).  8-bit pixels are widened on the fly when
+// read from shared memory and narrowed again before the final store.
 //
-//   1. TMA load of the input window of the tile (TX+wx-1 columns, TY+wy-1
-//      rows, column start rounded down to 16 bytes) into S0 -- or plain
-//      loads when the image is not TMA-aligned.  Pixels outside the image
-//      become the operation's identity (section 2's window ignores them).
-//   2. Working copy in 16-bit lanes: every word holds two pixels, so one
-//      min.u16x2 / max.u16x2 handles two pixels (8-bit pixels are widened
-//      once; on sm_103a the byte-wise __vminu4 costs several instructions,
-//      the 16x2 form one).
-//   3. Pass along y (1 x wy element, the paper's "horizontal pass" of
-//      section 5.1): each thread scans one word column downwards, either
-//      directly with outputs sharing the common rows (the paired-row idea of
-//      section 5.1.2, generalised to G outputs) or by van Herk/Gil-Werman
-//      (section 5.1.1).  Results leave through 2x2 register transposes into
-//      S1T, where a row is one pixel column x and a word holds two image rows.
-//   4. Pass along x (wx x 1 element, section 5.2) on S1T: the same vertical
-//      scan, now along x -- the paper's "transpose, vertical pass,
-//      transpose" (sections 1 and 5.2.1) done in registers and shared memory.
-//      Results transpose back into row-major S2.
-//   5. Coalesced 32-bit stores of S2, clipped to the image.
-//
-// Each image pixel crosses HBM once in and once out; the halos of
-// neighbouring tiles are re-read from L2.
+//   1. TMA 2-D load of the tile's input window -- TX+wx-1 columns (start
+//      rounded down to 16 bytes) by TY+wy-1 rows -- into S0, or plain loads
+//      when the image is not TMA-aligned.  Pixels outside the image become the
+//      operation's identity (the section 2 window ignores them).
+//   2. Pass along y (1 x wy element; the paper's "horizontal pass" of
+//      section 5.1) on octet columns of S0, by one of two methods:
+//        direct  -- each thread makes 8 consecutive outputs, which share the
+//                   rows common to their windows (the paired-row loop of
+//                   section 5.1.2, generalised from 2 to 8 outputs);
+//        blocked -- van Herk/Gil-Werman's decomposition (section 5.1.1): a
+//                   window is a suffix of the block it starts in plus a
+//                   prefix of the block it ends in.  Blocks here are 8 rows
+//                   held in registers rather than w rows; the whole blocks
+//                   that lie inside a window are folded from per-block
+//                   totals (w/64 extra operations per output), and both scan
+//                   phases run fully in parallel.  With 8-row blocks and
+//                   w = 8 this is exactly the paper's method.
+//      Each thread's 8x8-pixel result block is transposed in registers
+//      (2x2 byte-permute butterflies, the GPU form of the vtrn transposes of
+//      section 4) into S1T, where a row is one pixel column.
+//   3. Pass along x (wx x 1 element, section 5.2) on S1T with the same two
+//      methods -- the paper's "transpose, vertical pass, transpose" (sections
+//      1 and 5.2.1) -- and the 8x8 results transposed back into row-major S2.
+//   4. S2 leaves by a TMA 2-D store (clipped to the image by the hardware) or
+//      by plain stores.
+// A window of width 1 skips its pass and the transposes around it.
+// Each image pixel crosses HBM once in and once out; tile halos are re-read
+// from L2.
 #pragma once
 
 #include "morph_common.cuh"
+#include "morph_geom.h"
 
 namespace morph {
 
 constexpr int kThreads = 256;  // threads per CTA of every tile kernel
-constexpr int kGroup = 4;      // outputs per thread along the scan direction
 
-// 16-bit-lane min/max (both pixel types run in this form).
+// ---------------------------------------------------------------------------
+// Packed helpers on octets (uint4 = 8 pixels in 16-bit lanes)
+// ---------------------------------------------------------------------------
 template <int OP> __device__ __forceinline__ uint32_t op2(uint32_t a, uint32_t b) {
   return OP == 0 ? __vminu2(a, b) : __vmaxu2(a, b);
+}
+template <int OP> __device__ __forceinline__ uint4 op4(uint4 a, uint4 b) {
+  return make_uint4(op2<OP>(a.x, b.x), op2<OP>(a.y, b.y), op2<OP>(a.z, b.z), op2<OP>(a.w, b.w));
+}
+// 8 bytes -> 8 pixels in 16-bit lanes, and back.
+__device__ __forceinline__ uint4 widen8(uint2 b) {
+  return make_uint4(__byte_perm(b.x, 0u, 0x4140), __byte_perm(b.x, 0u, 0x4342),
+                    __byte_perm(b.y, 0u, 0x4140), __byte_perm(b.y, 0u, 0x4342));
+}
+__device__ __forceinline__ uint2 narrow8(uint4 w) {
+  return make_uint2(__byte_perm(w.x, w.y, 0x6420), __byte_perm(w.z, w.w, 0x6420));
+}
+__device__ __forceinline__ uint32_t word_of(const uint4& v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set_word(uint4& v, int j, uint32_t w) {
+  if (j == 0) v.x = w;
+  else if (j == 1) v.y = w;
+  else if (j == 2) v.z = w;
+  else v.w = w;
 }
 
 // Walks a row-major n0 x n1 index space with a fixed stride without a
@@ -58,78 +91,6 @@ struct Strided2D {
   }
 };
 
-// ---------------------------------------------------------------------------
-// Tile geometry, computed identically on the host (shared-memory size) and on
-// the device (addressing).  Sizes in 32-bit words unless named otherwise.
-// ---------------------------------------------------------------------------
-struct Geom {
-  int esz;       // bytes per pixel
-  int ox;        // first needed pixel, counted from the 16-byte-aligned load start
-  int lead;      // pixels between the load start and x0 (ox + anchor_x)
-  int iw_pix;    // pixels needed per input row, from the load start
-  int nw;        // 16-bit-lane words per working row (2 pixels each)
-  int c0;        // first working word the passes need (words left of it hold only padding)
-  int nbx;       // 128-byte TMA boxes across a row
-  int ih;        // input rows: TY + wy - 1
-  int nby, bh;   // TMA boxes down the tile and their height
-  int ihp;       // rows allocated per box column (nby * bh)
-  int p1;        // S1T row pitch (words): TY/2 row pairs + 1
-  int off_s0, off_w, off_s1t, off_h, off_s2;  // word offsets in dynamic smem
-  int smem_bytes;
-};
-
-__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
-__host__ __device__ inline int round_up(int a, int b) { return cdiv(a, b) * b; }
-
-// vhgw_any: either pass uses van Herk/Gil-Werman (needs the H scratch).
-__host__ __device__ inline Geom make_geom(int esz, int TX, int TY, int wx, int wy, int ax,
-                                          bool vhgw_col, bool vhgw_row) {
-  Geom g;
-  g.esz = esz;
-  const int al = 16 / esz;                   // pixels per 16 bytes
-  g.lead = round_up(ax, al);                 // load start = x0 - lead, 16-byte aligned
-  g.ox = g.lead - ax;
-  g.iw_pix = g.ox + TX + wx - 1;
-  g.nw = (esz == 1) ? 2 * cdiv(g.iw_pix, 4) : cdiv(g.iw_pix, 2);
-  g.c0 = (esz == 1) ? 2 * (g.ox / 4) : g.ox / 2;
-  g.nbx = cdiv(g.iw_pix * esz, 128);
-  g.ih = TY + wy - 1;
-  g.nby = cdiv(g.ih, 256);
-  g.bh = cdiv(g.ih, g.nby);
-  g.ihp = g.nby * g.bh;
-  g.p1 = TY / 2 + 1;
-  const int s0 = g.nbx * g.ihp * 32;         // TMA landing buffer (box layout)
-  const int w = (esz == 1) ? g.ih * g.nw : 0; // widened copy (8-bit only)
-  const int s1t = 2 * g.nw * g.p1;           // one row per pixel column
-  int h = 0;
-  if (vhgw_col) h = TY * g.nw;
-  if (vhgw_row && TX * g.p1 > h) h = TX * g.p1;
-  const int s2 = TY * (TX * esz / 4);
-  // Regions (each 32-word = 128-byte aligned):
-  //  8-bit : A = S0 then S1T, B = widened copy then S2, C = H
-  //  16-bit: A = S0 (working copy) then S2, B = S1T, C = H
-  int a, b;
-  if (esz == 1) {
-    a = s0 > s1t ? s0 : s1t;
-    b = w > s2 ? w : s2;
-    g.off_s0 = 0;
-    g.off_s1t = 0;
-    g.off_w = round_up(a, 32);
-    g.off_s2 = g.off_w;
-    g.off_h = g.off_w + round_up(b, 32);
-  } else {
-    a = s0 > s2 ? s0 : s2;
-    b = s1t;
-    g.off_s0 = 0;
-    g.off_w = 0;
-    g.off_s2 = 0;
-    g.off_s1t = round_up(a, 32);
-    g.off_h = g.off_s1t + round_up(b, 32);
-  }
-  g.smem_bytes = 4 * (g.off_h + round_up(h, 32));
-  return g;
-}
-
 // Per-launch description of one image.
 struct ImgArgs {
   const uint8_t* src;
@@ -137,114 +98,240 @@ struct ImgArgs {
   long long sp, dp;    // pitches in bytes
   int W, H;            // pixels
   int wx, wy, ax, ay;  // window and anchor (already clipped to the image)
-  int vhgw_col, vhgw_row;
-  int tma;             // 1: S0 arrives by TMA through the tensor map
+  int blk_y, blk_x;    // 1: the pass uses the blocked method (window >= 8)
+  int tma_ld;          // 1: S0 arrives by TMA through the input tensor map
+  int tma_st;          // 1: S2 leaves by TMA through the output tensor map
   int ld_vec;          // 1: src rows allow aligned 32-bit loads
   int st_vec;          // 1: dst rows allow aligned 32-bit stores
 };
 
-// out[j] = op over rows j .. j+w-1 of the column at p (row stride `stride`),
-// j = 0..G-1.  For w >= G the G windows share rows G-1 .. w-1 (the "core"),
-// which is scanned once; each output adds a suffix of the rows before the
-// core and a prefix of the rows after it.  With G = 2 this is exactly the
-// paper's paired-row loop (section 5.1.2): w-1 shared rows, one extra row per
-// output.
-template <int OP, int G>
-__device__ __forceinline__ void direct_group(const uint32_t* __restrict__ p, int stride, int w,
-                                             uint32_t (&out)[G]) {
+// ---------------------------------------------------------------------------
+// Direct method: out[j] = op over rows r0+j .. r0+j+w-1, j = 0..G-1.  For
+// w >= G the G windows share rows r0+G-1 .. r0+w-1 (scanned once); each adds
+// a suffix of the rows before and a prefix of the rows after.  With G = 2 this
+// is the paper's paired-row loop (section 5.1.2).
+// ---------------------------------------------------------------------------
+template <int OP, int G, class In>
+__device__ __forceinline__ void direct_group(const In& in, int r0, int w, uint4 (&out)[G]) {
   if (w >= G) {
-    uint32_t core = p[(G - 1) * stride];
-    const uint32_t* q = p + G * stride;
-#pragma unroll 4
-    for (int k = G; k < w; ++k, q += stride) core = op2<OP>(core, *q);
-    uint32_t left[G];  // left[j] = op(rows j .. G-2), j <= G-2
-    left[G - 2] = p[(G - 2) * stride];
+    uint4 core = in(r0 + G - 1);
+#pragma unroll 2
+    for (int k = G; k < w; ++k) core = op4<OP>(core, in(r0 + k));
+    // out[j] = core + suffix(rows r0+j .. r0+G-2) + prefix(rows r0+w .. r0+w+j-1)
+    uint4 acc = in(r0 + G - 2);
+    out[G - 2] = op4<OP>(core, acc);
 #pragma unroll
-    for (int j = G - 3; j >= 0; --j) left[j] = op2<OP>(left[j + 1], p[j * stride]);
-    uint32_t right = p[w * stride];  // op(rows w .. w+j-1), j >= 1
-    out[0] = op2<OP>(core, left[0]);
+    for (int j = G - 3; j >= 0; --j) {
+      acc = op4<OP>(acc, in(r0 + j));
+      out[j] = op4<OP>(core, acc);
+    }
+    acc = in(r0 + w);
+    out[G - 1] = op4<OP>(core, acc);
 #pragma unroll
     for (int j = 1; j < G - 1; ++j) {
-      out[j] = op2<OP>(op2<OP>(core, left[j]), right);
-      right = op2<OP>(right, p[(w + j) * stride]);
+      out[j] = op4<OP>(out[j], acc);
+      acc = op4<OP>(acc, in(r0 + w + j));
+      if (j == G - 2) out[G - 1] = op4<OP>(out[G - 1], acc);
     }
-    out[G - 1] = op2<OP>(core, right);
   } else {
-    // w < G: load the G+w-1 <= 2G-2 rows once, then combine.
-    uint32_t r[2 * G - 2];
+    // w < G: read the G+w-1 rows once; r[j] becomes op(r[j] .. r[j+w-1]) in
+    // place (later j only read rows above j, still unmodified).
+    uint4 r[2 * G - 2];
 #pragma unroll
-    for (int k = 0; k < 2 * G - 2; ++k) r[k] = (k < G + w - 1) ? p[k * stride] : 0u;
+    for (int k = 0; k < 2 * G - 2; ++k)
+      if (k < G + w - 1) r[k] = in(r0 + k);
 #pragma unroll
     for (int j = 0; j < G; ++j) {
-      uint32_t v = r[j];
 #pragma unroll
       for (int k = 1; k < G; ++k)
-        if (k < w) v = op2<OP>(v, r[j + k]);
-      out[j] = v;
+        if (k < w) r[j] = op4<OP>(r[j], r[j + k]);
+      out[j] = r[j];
     }
   }
 }
 
-// van Herk/Gil-Werman on one block [lo, hi) of a column (rows relative to
-// the pass's first input row): h, the running op from the block's last row
-// upwards, goes to hcol for rows < nout; g, the running op from the block's
-// first row downwards, replaces the column in place.  A window starting at
-// row s then is op(h[s], g[s+w-1]) (section 5.1.1).
-template <int OP>
-__device__ __forceinline__ void vhgw_block(uint32_t* __restrict__ col, int stride, int lo, int hi,
-                                           uint32_t* __restrict__ hcol, int hstride, int nout) {
-  uint32_t h = col[(hi - 1) * stride];
-  if (hi - 1 < nout) hcol[(hi - 1) * hstride] = h;
-#pragma unroll 4
-  for (int r = hi - 2; r >= lo; --r) {
-    h = op2<OP>(h, col[r * stride]);
-    if (r < nout) hcol[r * hstride] = h;
+// ---------------------------------------------------------------------------
+// Shared-memory views.  Each gives row r of one 16-byte column as 8 pixels in
+// 16-bit lanes.
+// ---------------------------------------------------------------------------
+// Octet k of the TMA landing buffer (128-byte boxes, `ihp` rows per box column).
+template <typename T>
+struct S0Col {
+  const uint8_t* base;
+  __device__ __forceinline__ S0Col(const uint8_t* s0, int k, int ihp) {
+    const int byte = k * 8 * static_cast<int>(sizeof(T));
+    base = s0 + (byte >> 7) * (ihp * 128) + (byte & 127);
   }
-  uint32_t g = col[lo * stride];
-#pragma unroll 4
-  for (int r = lo + 1; r < hi; ++r) {
-    g = op2<OP>(g, col[r * stride]);
-    col[r * stride] = g;
+  __device__ __forceinline__ uint4 operator()(int r) const {
+    if (sizeof(T) == 1) return widen8(*reinterpret_cast<const uint2*>(base + r * 128));
+    return *reinterpret_cast<const uint4*>(base + r * 128);
+  }
+};
+
+// S1T row ox + xr (xr counted from the first needed pixel column), chunk c of
+// 8 image rows; the chunk index is XOR-swizzled by xr/8 so that the
+// 8-row-strided writes of the transposes hit distinct banks.
+template <int MT>
+struct TCol {
+  const uint4* base;  // S1T + ox * ntc
+  int ntc, c;
+  __device__ __forceinline__ uint4 operator()(int xr) const {
+    return base[xr * ntc + (c ^ ((xr >> 3) & MT))];
+  }
+};
+
+// S2 (output tile, original pixel type), octet k: rows of `SBOX`-byte boxes.
+template <typename T, int TX, int TY>
+struct S2Col {
+  uint8_t* base;
+  static constexpr int SBOX = (TX * sizeof(T) < 128) ? TX * sizeof(T) : 128;
+  __device__ __forceinline__ S2Col(uint8_t* s2, int k) {
+    const int byte = k * 8 * static_cast<int>(sizeof(T));
+    base = s2 + (byte / SBOX) * (TY * SBOX) + (byte % SBOX);
+  }
+  __device__ __forceinline__ void store(int r, uint4 v) const {
+    if (sizeof(T) == 1)
+      *reinterpret_cast<uint2*>(base + r * SBOX) = narrow8(v);
+    else
+      *reinterpret_cast<uint4*>(base + r * SBOX) = v;
+  }
+};
+
+// In-register transpose of an 8x8-pixel block: v[i] holds row i (word j =
+// pixels 2j, 2j+1); on exit t[p] holds pixel column p (word q = rows 2q, 2q+1).
+__device__ __forceinline__ void transpose8(const uint4 (&v)[8], uint4 (&t)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t p[2] = {word_of(v[2 * q], j), word_of(v[2 * q + 1], j)};
+      transpose_block(p);
+      set_word(t[2 * j], q, p[0]);
+      set_word(t[2 * j + 1], q, p[1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Blocked large-window method, phase 1: block j (rows 8j .. 8j+7 of the
+// column, rows >= nrows read as the identity) -> suffix S (stored for rows
+// < nout), prefix P (stored at row - (w-1) for rows w-1 .. w-2+nout) and the
+// block total T[j].  Phase 2 then gives out[s] = op(S[s], P[s], totals of the
+// blocks strictly between the blocks of s and s+w-1).
+// ---------------------------------------------------------------------------
+template <int OP, class In, class St>
+__device__ __forceinline__ void blocked_scan(const In& in, int j, int nrows, int w, int nout, const St& st) {
+  const uint32_t id = ident_word<OP>();
+  uint4 v[kBlk];
+  const int r0 = j * kBlk;
+#pragma unroll
+  for (int i = 0; i < kBlk; ++i) v[i] = (r0 + i < nrows) ? in(r0 + i) : make_uint4(id, id, id, id);
+  uint4 p = v[0];
+#pragma unroll
+  for (int i = 0; i < kBlk; ++i) {
+    if (i) p = op4<OP>(p, v[i]);
+    const int e = r0 + i - (w - 1);
+    if (e >= 0 && e < nout) st.p(e, p);
+  }
+  uint4 sfx = v[kBlk - 1];
+#pragma unroll
+  for (int i = kBlk - 1; i >= 0; --i) {
+    if (i < kBlk - 1) sfx = op4<OP>(sfx, v[i]);
+    if (r0 + i < nout) st.s(r0 + i, sfx);
+  }
+  st.t(j, sfx);
+}
+
+// Phase 2 for outputs s = 8k .. 8k+7 (all < nout).
+template <int OP, class Ld>
+__device__ __forceinline__ void blocked_combine(const Ld& ld, int k, int w, uint4 (&out)[kBlk]) {
+  const uint32_t id = ident_word<OP>();
+  const int ce0 = (k * kBlk + w - 1) / kBlk;  // block of the first window's end
+  uint4 ma = make_uint4(id, id, id, id);      // totals of blocks k+1 .. ce0-1
+  for (int j = k + 1; j < ce0; ++j) ma = op4<OP>(ma, ld.t(j));
+  const uint4 mb = (ce0 > k) ? op4<OP>(ma, ld.t(ce0)) : ma;  // ... k+1 .. ce0
+#pragma unroll
+  for (int i = 0; i < kBlk; ++i) {
+    const int s = k * kBlk + i;
+    const uint4 m = ((s + w - 1) / kBlk == ce0) ? ma : mb;
+    out[i] = op4<OP>(op4<OP>(ld.s(s), ld.p(s)), m);
   }
 }
 
-// Address of 32-bit word c of row r in a TMA box-layout buffer (128-byte
-// boxes stacked per box column, `ihp` rows each).
-__device__ __forceinline__ int box_word(int r, int c, int ihp) {
-  return (c >> 5) * (ihp * 32) + r * 32 + (c & 31);
-}
+// Scratch of the blocked method on a plain row-major buffer (pass along y:
+// lanes of a warp take consecutive columns, so no swizzle is needed).
+struct YScratch {
+  uint4 *sb, *pb, *tb;
+  int pitch, c;
+  __device__ __forceinline__ void s(int r, uint4 v) const { sb[r * pitch + c] = v; }
+  __device__ __forceinline__ void p(int r, uint4 v) const { pb[r * pitch + c] = v; }
+  __device__ __forceinline__ void t(int j, uint4 v) const { tb[j * pitch + c] = v; }
+  __device__ __forceinline__ uint4 s(int r) const { return sb[r * pitch + c]; }
+  __device__ __forceinline__ uint4 p(int r) const { return pb[r * pitch + c]; }
+  __device__ __forceinline__ uint4 t(int j) const { return tb[j * pitch + c]; }
+};
+
+// Scratch of the blocked method for the pass along x: phase 2 gives lanes
+// consecutive 8-row groups, so chunk indices are XOR-swizzled by row/8.
+template <int MT>
+struct XScratch {
+  uint4 *sb, *pb, *tb;
+  int ntc, c;
+  __device__ __forceinline__ int at(int r) const { return r * ntc + (c ^ ((r >> 3) & MT)); }
+  __device__ __forceinline__ int att(int j) const { return j * ntc + (c ^ (j & MT)); }
+  __device__ __forceinline__ void s(int r, uint4 v) const { sb[at(r)] = v; }
+  __device__ __forceinline__ void p(int r, uint4 v) const { pb[at(r)] = v; }
+  __device__ __forceinline__ void t(int j, uint4 v) const { tb[att(j)] = v; }
+  __device__ __forceinline__ uint4 s(int r) const { return sb[at(r)]; }
+  __device__ __forceinline__ uint4 p(int r) const { return pb[at(r)]; }
+  __device__ __forceinline__ uint4 t(int j) const { return tb[att(j)]; }
+};
 
 template <typename T> __device__ __forceinline__ uint32_t load_px(const uint8_t* row, int x) {
   return reinterpret_cast<const T*>(row)[x];
 }
 
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_addr(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // One tile.  `bar`/`phase` track the TMA barrier across tiles of a CTA.
 // Returns false when a bounded wait gave up (the error word is set).
+// ---------------------------------------------------------------------------
 template <typename T, int OP, int TX, int TY>
-__device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* tin, int x0, int y0,
-                                         const Geom& g, uint32_t* smem, uint64_t* bar,
+__device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* tin, const CUtensorMap* tout,
+                                         int x0, int y0, const Geom& g, uint4* smem, uint64_t* bar,
                                          uint32_t& phase, int* err) {
   constexpr int E = sizeof(T);
-  constexpr int PPW = 4 / E;  // pixels per 32-bit word in S0/S2
-  constexpr int G = kGroup;
+  constexpr int PPW = 4 / E;   // pixels per 32-bit word of S0/S2
+  constexpr int NTC = TY / 8;  // 8-row chunks per S1T row
+  constexpr int NXO = TX / 8;  // output octets per row
+  constexpr int MT = (NTC < 8 ? NTC : 8) - 1;
+  constexpr int SBOX = S2Col<T, TX, TY>::SBOX;
   constexpr uint32_t PXMASK = (E == 1) ? 0xFFu : 0xFFFFu;
   const int tid = threadIdx.x;
   const int xs = x0 - g.lead;  // first loaded pixel column (16-byte aligned)
   const int ys = y0 - a.ay;    // first loaded row
-  uint32_t* s0 = smem + g.off_s0;
+  uint8_t* s0 = reinterpret_cast<uint8_t*>(smem + g.off_s0);
   const uint32_t IDW = ident_word<OP>();
-  const int nwi = cdiv(g.iw_pix * E, 4);  // S0 words per row that matter
-  const int wi0 = (E == 1) ? g.c0 / 2 : g.c0;  // first S0 word that matters
 
-  // ---- 1. load ----------------------------------------------------------------
-  const bool border = xs < 0 || ys < 0 || xs + g.iw_pix > a.W || ys + g.ih > a.H;
-  if (a.tma) {
+  // ---- 1. load ---------------------------------------------------------------
+  const int w_lo = g.k0 * 2 * E, w_hi = g.noct * 2 * E;  // S0 words the passes read
+  const bool border = xs < 0 || ys < 0 || xs + g.noct * 8 > a.W || ys + g.ih > a.H;
+  if (a.tma_ld) {
     if (tid == 0) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(bar, static_cast<uint32_t>(g.nbx * g.nby * 128 * g.bh));
       for (int bx = 0; bx < g.nbx; ++bx)
         for (int by = 0; by < g.nby; ++by)
-          tma_load_2d(s0 + (bx * g.ihp + by * g.bh) * 32, tin, bar, xs + bx * (128 / E), ys + by * g.bh);
+          tma_load_2d(s0 + (bx * g.ihp + by * g.bh) * 128, tin, bar, xs + bx * (128 / E), ys + by * g.bh);
     }
     const bool ok = mbar_wait_bounded(bar, phase);
     phase ^= 1u;
@@ -254,10 +341,11 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     }
     // TMA fills out-of-image pixels with 0: the identity of max, not of min.
     if (OP == 0 && border) {
-      for (Strided2D i(nwi - wi0, tid, kThreads); i.r < g.ih; i.next()) {
-        const int c = wi0 + i.c, r = i.r;
+      uint32_t* s0w = reinterpret_cast<uint32_t*>(s0);
+      for (Strided2D i(w_hi - w_lo, tid, kThreads); i.r < g.ih; i.next()) {
+        const int c = w_lo + i.c, r = i.r;
         const int y = ys + r;
-        uint32_t* pw = s0 + box_word(r, c, g.ihp);
+        uint32_t* pw = s0w + (c >> 5) * (g.ihp * 32) + r * 32 + (c & 31);
         if (y < 0 || y >= a.H) {
           *pw = IDW;
         } else {
@@ -273,8 +361,9 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
       __syncthreads();
     }
   } else {
-    for (Strided2D i(nwi - wi0, tid, kThreads); i.r < g.ih; i.next()) {
-      const int c = wi0 + i.c, r = i.r;
+    uint32_t* s0w = reinterpret_cast<uint32_t*>(s0);
+    for (Strided2D i(w_hi - w_lo, tid, kThreads); i.r < g.ih; i.next()) {
+      const int c = w_lo + i.c, r = i.r;
       const int y = ys + r;
       uint32_t v = IDW;
       if (y >= 0 && y < a.H) {
@@ -293,143 +382,138 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
           }
         }
       }
-      s0[box_word(r, c, g.ihp)] = v;
+      s0w[(c >> 5) * (g.ihp * 32) + r * 32 + (c & 31)] = v;
     }
     __syncthreads();
   }
 
-  // ---- 2. working copy in 16-bit lanes ----------------------------------------
-  // Column c of the working buffer starts at wcol(c); rows are wstride apart.
-  uint32_t* wbuf;
-  int wstride;
-  if (E == 1) {
-    wbuf = smem + g.off_w;
-    wstride = g.nw;
-    for (Strided2D i(g.nw / 2 - wi0, tid, kThreads); i.r < g.ih; i.next()) {
-      const int q = wi0 + i.c, r = i.r;
-      const uint32_t v = s0[box_word(r, q, g.ihp)];
-      uint2 pr;
-      pr.x = __byte_perm(v, 0u, 0x4140);  // pixels 0,1 -> 16-bit lanes
-      pr.y = __byte_perm(v, 0u, 0x4342);  // pixels 2,3
-      *reinterpret_cast<uint2*>(wbuf + r * g.nw + 2 * q) = pr;
+  uint8_t* s2 = reinterpret_cast<uint8_t*>(smem + g.off_s2);
+  uint4* s1t = smem + g.off_s1t;
+  const int nk = g.noct - g.k0;  // octet columns of S0 the pass along y covers
+  const YScratch ysc0{smem + g.off_sy, smem + g.off_py, smem + g.off_ty, g.noct, 0};
+
+  // Emits the 8 y-pass outputs rows 8k..8k+7 of octet column c.
+  auto emit_y = [&](int c, int k, const uint4 (&o)[kBlk]) {
+    if (a.wx == 1) {
+      const S2Col<T, TX, TY> out(s2, c);
+#pragma unroll
+      for (int i = 0; i < kBlk; ++i) out.store(kBlk * k + i, o[i]);
+    } else {
+      uint4 t[kBlk];
+      transpose8(o, t);
+#pragma unroll
+      for (int px = 0; px < kBlk; ++px) {
+        const int xr = 8 * c + px - g.ox;  // pixel column relative to the first needed one
+        if (xr >= 0) s1t[(g.ox + xr) * NTC + (k ^ ((xr >> 3) & MT))] = t[px];
+      }
     }
-    __syncthreads();
-  } else {
-    wbuf = s0;
-    wstride = 32;
-  }
-  auto wcol = [&](int c) -> uint32_t* {
-    return E == 1 ? wbuf + c : wbuf + (c >> 5) * (g.ihp * 32) + (c & 31);
   };
 
-  // ---- 3. pass along y (window wy), results transposed into S1T -----------------
-  uint32_t* s1t = smem + g.off_s1t;
-  uint32_t* hb = smem + g.off_h;
-  constexpr int NSG = TY / G;  // row groups per column
-  const int ncw = g.nw - g.c0;  // working columns the passes need
-  if (a.vhgw_col) {
-    const int nblk = cdiv(g.ih, a.wy);
-    for (Strided2D i(ncw, tid, kThreads); i.r < nblk; i.next()) {
-      const int c = g.c0 + i.c;
-      const int lo = i.r * a.wy;
-      const int hi = min(lo + a.wy, g.ih);
-      vhgw_block<OP>(wcol(c), wstride, lo, hi, hb + c, g.nw, TY);
+  // ---- 2. pass along y --------------------------------------------------------
+  if (a.wy == 1 && a.wx > 1) {
+    for (Strided2D i(nk, tid, kThreads); i.r < NTC; i.next()) {  // transpose only
+      const int c = g.k0 + i.c, k = i.r;
+      const S0Col<T> col(s0, c, g.ihp);
+      uint4 o[kBlk];
+#pragma unroll
+      for (int q = 0; q < kBlk; ++q) o[q] = col(kBlk * k + q);
+      emit_y(c, k, o);
+    }
+  } else if (a.blk_y) {
+    for (Strided2D i(nk, tid, kThreads); i.r < g.nchy; i.next()) {
+      const int c = g.k0 + i.c;
+      YScratch st = ysc0;
+      st.c = c;
+      blocked_scan<OP>(S0Col<T>(s0, c, g.ihp), i.r, g.ih, a.wy, TY, st);
     }
     __syncthreads();
-  }
-  for (Strided2D i(ncw, tid, kThreads); i.r < NSG; i.next()) {
-    const int c = g.c0 + i.c;
-    const int r0 = i.r * G;
-    uint32_t o[G];
-    const uint32_t* col = wcol(c);
-    if (a.vhgw_col) {
-#pragma unroll
-      for (int j = 0; j < G; ++j)
-        o[j] = op2<OP>(hb[(r0 + j) * g.nw + c], col[(r0 + j + a.wy - 1) * wstride]);
-    } else {
-      direct_group<OP, G>(col + r0 * wstride, wstride, a.wy, o);
+    for (Strided2D i(nk, tid, kThreads); i.r < NTC; i.next()) {
+      const int c = g.k0 + i.c;
+      YScratch ld = ysc0;
+      ld.c = c;
+      uint4 o[kBlk];
+      blocked_combine<OP>(ld, i.r, a.wy, o);
+      emit_y(c, i.r, o);
     }
-#pragma unroll
-    for (int pr = 0; pr < G / 2; ++pr) {
-      uint32_t v[2] = {o[2 * pr], o[2 * pr + 1]};
-      transpose_block(v);  // v[t] = pixel 2c+t of rows r0+2pr, r0+2pr+1
-      const int sp = r0 / 2 + pr;
-      s1t[(2 * c) * g.p1 + sp] = v[0];
-      s1t[(2 * c + 1) * g.p1 + sp] = v[1];
+  } else {
+    for (Strided2D i(nk, tid, kThreads); i.r < NTC; i.next()) {
+      const int c = g.k0 + i.c;
+      uint4 o[kBlk];
+      direct_group<OP, kBlk>(S0Col<T>(s0, c, g.ihp), kBlk * i.r, a.wy, o);
+      emit_y(c, i.r, o);
     }
   }
   __syncthreads();
 
-  // ---- 4. pass along x (window wx) on S1T, results back to row-major S2 ---------
-  uint32_t* s2 = smem + g.off_s2;
-  constexpr int NSP = TY / 2;                // row pairs
-  constexpr int NXQ = TX / G;                // output pixel groups
-  constexpr int P2 = TX * E / 4;             // S2 row pitch (words)
-  constexpr int SWM = (P2 < 32 ? P2 : 32) - 1;  // S2 bank swizzle mask
-  uint32_t* s1x = s1t + g.ox * g.p1;         // row 0 = first needed pixel column
-  if (a.vhgw_row) {
-    const int nx = TX + a.wx - 1;
-    const int nblk = cdiv(nx, a.wx);
-    for (int it = tid; it < NSP * nblk; it += kThreads) {
-      const int sp = it % NSP, k = it / NSP;
-      const int lo = k * a.wx;
-      const int hi = min(lo + a.wx, nx);
-      vhgw_block<OP>(s1x + sp, g.p1, lo, hi, hb + sp, g.p1, TX);
-    }
-    __syncthreads();
-  }
-  for (int it = tid; it < NSP * NXQ; it += kThreads) {
-    const int sp = it % NSP, xq = it / NSP;
-    const int xo = xq * G;
-    uint32_t o[G];
-    if (a.vhgw_row) {
+  // ---- 3. pass along x on S1T, results transposed back into S2 -------------------
+  if (a.wx > 1) {
+    const uint4* s1x = s1t + g.ox * NTC;
+    auto emit_x = [&](int c, int k, const uint4 (&o)[kBlk]) {
+      uint4 rw[kBlk];
+      transpose8(o, rw);  // o[pixel] (rows in words) -> rw[row] (pixels in words)
+      const S2Col<T, TX, TY> out(s2, k);
 #pragma unroll
-      for (int j = 0; j < G; ++j)
-        o[j] = op2<OP>(hb[(xo + j) * g.p1 + sp], s1x[(xo + j + a.wx - 1) * g.p1 + sp]);
+      for (int r = 0; r < kBlk; ++r) out.store(kBlk * c + r, rw[r]);
+    };
+    if (a.blk_x) {
+      const XScratch<MT> xsc0{smem + g.off_sx, smem + g.off_px, smem + g.off_tx, NTC, 0};
+      for (int it = tid; it < NTC * g.nchx; it += kThreads) {
+        const int c = it % NTC, j = it / NTC;
+        XScratch<MT> st = xsc0;
+        st.c = c;
+        blocked_scan<OP>(TCol<MT>{s1x, NTC, c}, j, g.nrx, a.wx, TX, st);
+      }
+      __syncthreads();
+      for (int it = tid; it < NXO * NTC; it += kThreads) {
+        const int k = it % NXO, c = it / NXO;
+        XScratch<MT> ld = xsc0;
+        ld.c = c;
+        uint4 o[kBlk];
+        blocked_combine<OP>(ld, k, a.wx, o);
+        emit_x(c, k, o);
+      }
     } else {
-      direct_group<OP, G>(s1x + xo * g.p1 + sp, g.p1, a.wx, o);
-    }
-    // o[j] = pixel xo+j of rows 2sp, 2sp+1 -> row-major pixel pairs
-    uint32_t rw[2][G / 2];
-#pragma unroll
-    for (int pr = 0; pr < G / 2; ++pr) {
-      uint32_t v[2] = {o[2 * pr], o[2 * pr + 1]};
-      transpose_block(v);  // v[i] = pixels xo+2pr, xo+2pr+1 of row 2sp+i
-      rw[0][pr] = v[0];
-      rw[1][pr] = v[1];
-    }
-    const int sw = sp & SWM;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int s = 2 * sp + i;
-      if (E == 1) {
-        // narrow the 4 pixels held in two 16-bit-lane words to one byte word
-        s2[s * P2 + (xq ^ sw)] = __byte_perm(rw[i][0], rw[i][1], 0x6420);
-      } else {
-#pragma unroll
-        for (int pr = 0; pr < G / 2; ++pr) s2[s * P2 + ((xq * (G / 2) + pr) ^ sw)] = rw[i][pr];
+      for (int it = tid; it < NXO * NTC; it += kThreads) {
+        const int k = it % NXO, c = it / NXO;
+        uint4 o[kBlk];
+        direct_group<OP, kBlk>(TCol<MT>{s1x, NTC, c}, kBlk * k, a.wx, o);
+        emit_x(c, k, o);
       }
     }
   }
-  __syncthreads();
 
-  // ---- 5. store S2, clipped to the image -----------------------------------------
-  for (int it = tid; it < TY * P2; it += kThreads) {
-    const int xw = it % P2, s = it / P2;
-    const int y = y0 + s;
-    const int x = x0 + xw * PPW;
-    if (y >= a.H || x >= a.W) continue;
-    const uint32_t v = s2[s * P2 + (xw ^ ((s >> 1) & SWM))];
-    uint8_t* row = a.dst + static_cast<long long>(y) * a.dp;
-    if (a.st_vec && x + PPW <= a.W) {
-      *reinterpret_cast<uint32_t*>(row + static_cast<long long>(x) * E) = v;
-    } else {
-#pragma unroll
-      for (int t = 0; t < PPW; ++t)
-        if (x + t < a.W) reinterpret_cast<T*>(row)[x + t] = static_cast<T>(v >> (8 * E * t));
+  // ---- 4. store S2 ---------------------------------------------------------------
+  if (a.tma_st) {
+    fence_proxy_async_smem();  // make this thread's S2 writes visible to the TMA unit
+    __syncthreads();
+    if (tid == 0) {
+      for (int bx = 0; bx < TX * E / SBOX; ++bx) tma_store_2d(tout, s2 + bx * TY * SBOX, x0 + bx * (SBOX / E), y0);
+      bulk_commit();
+      bulk_wait_read_all();
     }
+    __syncthreads();
+  } else {
+    __syncthreads();
+    constexpr int NW = TX * E / 4;  // 32-bit words per output row
+    for (int it = tid; it < TY * NW; it += kThreads) {
+      const int xw = it % NW, s = it / NW;
+      const int y = y0 + s;
+      const int x = x0 + xw * PPW;
+      if (y >= a.H || x >= a.W) continue;
+      const int byte = xw * 4;
+      const uint32_t v =
+          *reinterpret_cast<const uint32_t*>(s2 + (byte / SBOX) * (TY * SBOX) + s * SBOX + byte % SBOX);
+      uint8_t* row = a.dst + static_cast<long long>(y) * a.dp;
+      if (a.st_vec && x + PPW <= a.W) {
+        *reinterpret_cast<uint32_t*>(row + static_cast<long long>(x) * E) = v;
+      } else {
+#pragma unroll
+        for (int t = 0; t < PPW; ++t)
+          if (x + t < a.W) reinterpret_cast<T*>(row)[x + t] = static_cast<T>(v >> (8 * E * t));
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   return true;
 }
 

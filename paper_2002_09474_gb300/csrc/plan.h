@@ -11,7 +11,7 @@ namespace morph {
 struct Tuning {
   int cross_col[2];  // [esz-1]: pass along y uses the direct method iff wy <= cross_col
   int cross_row[2];  // [esz-1]: pass along x uses the direct method iff wx <= cross_row
-  int cfg_order[2][kNumTileCfg];  // [esz-1]: tile configurations to try, best first
+  int forced_cfg[2];              // [esz-1]: tile configuration to use when it fits (-1: cost model)
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 

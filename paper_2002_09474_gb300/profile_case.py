@@ -1,0 +1,64 @@
+"""Runs one erosion/dilation class a few times through the C ABI, for
+profiler captures of a single kernel (e.g. under ``ncu -k regex:fused -c 1``).
+
+  python -m paper_2002_09474_gb300.profile_case --dtype u8 --wx 127 --wy 127 --op erode --reps 3
+
+Inputs are seeded uniform images; nothing is checked or printed except a
+one-line summary (launch count, mean event time of the launches).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dtype", choices=("u8", "u16"), default="u8")
+    ap.add_argument("--width", type=int, default=4096)
+    ap.add_argument("--height", type=int, default=4096)
+    ap.add_argument("--wx", type=int, default=3)
+    ap.add_argument("--wy", type=int, default=3)
+    ap.add_argument("--op", choices=("erode", "dilate"), default="erode")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--cross-row", type=int, default=-1, help="force the x-pass crossover")
+    ap.add_argument("--cross-col", type=int, default=-1, help="force the y-pass crossover")
+    ap.add_argument("--tile", type=int, default=-1, help="force a tile configuration first")
+    args = ap.parse_args(argv)
+
+    import torch
+    from paper_2002_09474_gb300 import build as libbuild, synth
+    libbuild.build()
+    from paper_2002_09474_gb300 import morph
+
+    dt = np.uint8 if args.dtype == "u8" else np.uint16
+    code = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
+    morph.morph_set_tuning(code, args.cross_row, args.cross_col, args.tile)
+    img = synth.uniform_image(args.width, args.height, dt, seed=1)
+    src = torch.from_numpy(img).cuda()
+    dst = torch.empty_like(src)
+    op = morph.MORPH_ERODE if args.op == "erode" else morph.MORPH_DILATE
+    times = []
+    for _ in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        morph.apply(src, dst, args.wx, args.wy, op=op)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    morph.check_device_error()
+    print("profile_case %s %dx%d %dx%d %s: %d launches, last %.1f us" % (
+        args.dtype, args.width, args.height, args.wx, args.wy, args.op, args.reps,
+        times[-1] * 1e3))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

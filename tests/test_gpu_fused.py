@@ -51,7 +51,8 @@ def set_methods(lib, dtype, col, row, cfg=-1):
 
 
 SHAPES = [(1, 1), (2, 3), (5, 17), (33, 7), (67, 130), (129, 257), (200, 300)]
-WINDOWS = [(1, 1), (3, 3), (2, 5), (7, 1), (1, 9), (4, 4), (15, 15), (31, 7), (61, 61)]
+WINDOWS = [(1, 1), (3, 3), (2, 5), (7, 1), (1, 9), (4, 4), (8, 8), (9, 16), (17, 8), (15, 15), (31, 7),
+           (64, 65), (61, 61)]
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
@@ -73,7 +74,7 @@ def test_shapes_windows_methods(lib, dtype, method):
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5])
 def test_every_tile_shape(lib, dtype, cfg):
     torch = need_cuda()
     lib.morph_reset_tuning()
