@@ -175,7 +175,8 @@ int morph_autotune(const char *cache_path);
  * wy and cross_col (section 5.3's w_x^0 and w_y^0); a negative crossover
  * keeps the current value.  tile_cfg selects the output tile per CTA when it
  * fits the window in shared memory (0: 128x64, 1: 64x64, 2: 64x128,
- * 3: 256x32, 4: 32x32, 5: 32x128 pixels); -1 lets a built-in cost model pick
+ * 3: 256x32, 4: 32x32, 5: 128x128, 6: 256x64, 7: 32x128 pixels); -1 lets a
+ * built-in cost model pick
  * per call.  The result never changes, only the speed.  morph_reset_tuning
  * restores the built-in defaults.
  */

@@ -3,8 +3,10 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/morph.h"
+#include "batch.h"
 #include "morph_internal.h"
 #include "plan.h"
 
@@ -105,6 +107,76 @@ int stage_buffers(size_t bytes, void** in, void** out) {
   return MORPH_OK;
 }
 
+// Validates and plans every descriptor of a batch.  Besides the single-image
+// checks, no destination may overlap any other image's source or
+// destination (images of one launch run concurrently).
+int plan_batch(const morph_desc* d, int n, std::vector<BatchImageIn>* out) {
+  if (!d) return MORPH_ERR_NULL;
+  if (n < 1) return MORPH_ERR_ARG;
+  out->resize(n);
+  struct Range {
+    uintptr_t lo, hi;
+    int img, is_dst;
+  };
+  std::vector<Range> ranges;
+  ranges.reserve(2 * static_cast<size_t>(n));
+  for (int i = 0; i < n; ++i) {
+    const morph_desc& e = d[i];
+    if (e.src_pitch < 0 || e.dst_pitch < 0) return MORPH_ERR_PITCH;
+    const int rc = validate(e.src, static_cast<size_t>(e.src_pitch), e.dst, static_cast<size_t>(e.dst_pitch),
+                            e.width, e.height, e.dtype, e.op, e.wx, e.wy, e.anchor_x, e.anchor_y);
+    if (rc != MORPH_OK) return rc;
+    FusedLaunch& L = (*out)[i].L;
+    L = FusedLaunch();
+    L.esz = esz_of(e.dtype);
+    L.op = e.op;
+    L.src = e.src;
+    L.dst = e.dst;
+    L.sp = e.src_pitch;
+    L.dp = e.dst_pitch;
+    L.W = e.width;
+    L.H = e.height;
+    clip_window(e.width, e.wx, e.anchor_x, &L.wx, &L.ax);
+    clip_window(e.height, e.wy, e.anchor_y, &L.wy, &L.ay);
+    if (!plan_single(&L)) return MORPH_ERR_WINDOW;
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(e.src), d0 = reinterpret_cast<uintptr_t>(e.dst);
+    const uintptr_t row = static_cast<uintptr_t>(e.width) * L.esz;
+    ranges.push_back({s0, s0 + static_cast<uintptr_t>(e.height - 1) * e.src_pitch + row, i, 0});
+    ranges.push_back({d0, d0 + static_cast<uintptr_t>(e.height - 1) * e.dst_pitch + row, i, 1});
+  }
+  std::sort(ranges.begin(), ranges.end(), [](const Range& a, const Range& b) { return a.lo < b.lo; });
+  // sweep: a destination may not overlap any range that starts before it ends
+  uintptr_t reach_any = 0, reach_dst = 0;
+  for (const Range& r : ranges) {
+    if (r.lo < reach_dst) return MORPH_ERR_ALIAS;            // overlaps an earlier destination
+    if (r.is_dst && r.lo < reach_any) return MORPH_ERR_ALIAS;  // a destination overlaps anything earlier
+    reach_any = std::max(reach_any, r.hi);
+    if (r.is_dst) reach_dst = std::max(reach_dst, r.hi);
+  }
+  return MORPH_OK;
+}
+
+// Device layout of a batch: tensor maps (64-byte aligned), image records.
+struct BatchDev {
+  size_t maps_off, imgs_off, counter_off, bytes;
+};
+BatchDev batch_dev_layout(const BatchHost& h) {
+  BatchDev L;
+  L.maps_off = 0;
+  L.imgs_off = (h.maps.size() * sizeof(CUtensorMap) + 255) / 256 * 256;
+  L.counter_off = (L.imgs_off + h.imgs.size() * sizeof(BatchImage) + 255) / 256 * 256;
+  L.bytes = L.counter_off + 256;
+  return L;
+}
+
+struct BatchPlan {
+  int device = 0;
+  BatchHost host;
+  void* dmem = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
 }  // namespace morph
 
 // ---------------------------------------------------------------------------
@@ -140,6 +212,131 @@ int morph_dilate_u16(const uint16_t* src, int width, int height, size_t pitch, i
                      int anchor_y, uint16_t* dst, void* stream) {
   return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U16, MORPH_DILATE, wx, wy, anchor_x,
                      anchor_y, stream);
+}
+
+static int transpose_any(const void* src, int width, int height, size_t src_pitch, void* dst, size_t dst_pitch,
+                         int esz, void* stream) {
+  if (!src || !dst) return MORPH_ERR_NULL;
+  if (width < 1 || height < 1 || width > (1 << 30) || height > (1 << 30)) return MORPH_ERR_SIZE;
+  if (src_pitch < static_cast<size_t>(width) * esz || dst_pitch < static_cast<size_t>(height) * esz)
+    return MORPH_ERR_PITCH;
+  if (esz == 2 &&
+      ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst) | src_pitch | dst_pitch) & 1))
+    return MORPH_ERR_PITCH;
+  // source: height rows; destination: width rows of height pixels
+  const uintptr_t s0 = reinterpret_cast<uintptr_t>(src), d0 = reinterpret_cast<uintptr_t>(dst);
+  const uintptr_t s1 = s0 + static_cast<uintptr_t>(height - 1) * src_pitch + static_cast<uintptr_t>(width) * esz;
+  const uintptr_t d1 = d0 + static_cast<uintptr_t>(width - 1) * dst_pitch + static_cast<uintptr_t>(height) * esz;
+  if (s0 < d1 && d0 < s1) return MORPH_ERR_ALIAS;
+  return transpose_launch(src, static_cast<long long>(src_pitch), dst, static_cast<long long>(dst_pitch), width,
+                          height, esz, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? MORPH_OK
+             : MORPH_ERR_CUDA;
+}
+
+int transpose_u8(const uint8_t* src, int width, int height, size_t src_pitch, uint8_t* dst, size_t dst_pitch,
+                 void* stream) {
+  return transpose_any(src, width, height, src_pitch, dst, dst_pitch, 1, stream);
+}
+
+int transpose_u16(const uint16_t* src, int width, int height, size_t src_pitch, uint16_t* dst, size_t dst_pitch,
+                  void* stream) {
+  return transpose_any(src, width, height, src_pitch, dst, dst_pitch, 2, stream);
+}
+
+int morph_batch(const morph_desc* descs_host, int n, void* stream) {
+  std::vector<BatchImageIn> in;
+  int rc = plan_batch(descs_host, n, &in);
+  if (rc != MORPH_OK) return rc;
+  BatchHost h;
+  if (batch_prepare(in.data(), n, &h) != 0) return MORPH_ERR_WINDOW;
+  if (batch_configure(&h) != cudaSuccess) return MORPH_ERR_CUDA;
+  const BatchDev L = batch_dev_layout(h);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Stream-ordered scratch: allocated and freed in the stream's order, so
+  // concurrent batches on different streams never share it.
+  void* dmem = nullptr;
+  if (cudaMallocAsync(&dmem, L.bytes, st) != cudaSuccess) return MORPH_ERR_NOMEM;
+  uint8_t* base = static_cast<uint8_t*>(dmem);
+  cudaError_t e = cudaMemcpyAsync(base + L.maps_off, h.maps.data(), h.maps.size() * sizeof(CUtensorMap),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + L.imgs_off, h.imgs.data(), h.imgs.size() * sizeof(BatchImage),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = batch_enqueue(h, reinterpret_cast<const BatchImage*>(base + L.imgs_off),
+                      reinterpret_cast<const CUtensorMap*>(base + L.maps_off),
+                      reinterpret_cast<int*>(base + L.counter_off), st);
+  cudaFreeAsync(dmem, st);
+  return e == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+}
+
+int morph_batch_plan_create(const morph_desc* descs_host, int n, void** plan) {
+  if (!plan) return MORPH_ERR_NULL;
+  *plan = nullptr;
+  std::vector<BatchImageIn> in;
+  int rc = plan_batch(descs_host, n, &in);
+  if (rc != MORPH_OK) return rc;
+  BatchPlan* p = new BatchPlan();
+  cudaGetDevice(&p->device);
+  if (batch_prepare(in.data(), n, &p->host) != 0) {
+    delete p;
+    return MORPH_ERR_WINDOW;
+  }
+  if (batch_configure(&p->host) != cudaSuccess) {
+    delete p;
+    return MORPH_ERR_CUDA;
+  }
+  const BatchDev L = batch_dev_layout(p->host);
+  if (cudaMalloc(&p->dmem, L.bytes) != cudaSuccess) {
+    delete p;
+    return MORPH_ERR_NOMEM;
+  }
+  uint8_t* base = static_cast<uint8_t*>(p->dmem);
+  cudaError_t e = cudaMemcpy(base + L.maps_off, p->host.maps.data(), p->host.maps.size() * sizeof(CUtensorMap),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + L.imgs_off, p->host.imgs.data(), p->host.imgs.size() * sizeof(BatchImage),
+                   cudaMemcpyHostToDevice);
+  // Capture the counter reset and the persistent kernel into a graph.
+  cudaStream_t cs = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t le = batch_enqueue(p->host, reinterpret_cast<const BatchImage*>(base + L.imgs_off),
+                                   reinterpret_cast<const CUtensorMap*>(base + L.maps_off),
+                                   reinterpret_cast<int*>(base + L.counter_off), cs);
+    e = cudaStreamEndCapture(cs, &p->graph);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (cs) cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    morph_batch_plan_destroy(p);
+    return MORPH_ERR_CUDA;
+  }
+  *plan = p;
+  return MORPH_OK;
+}
+
+int morph_batch_plan_launch(void* plan, void* stream) {
+  if (!plan) return MORPH_ERR_NULL;
+  BatchPlan* p = static_cast<BatchPlan*>(plan);
+  return cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+}
+
+int morph_batch_plan_destroy(void* plan) {
+  if (!plan) return MORPH_ERR_NULL;
+  BatchPlan* p = static_cast<BatchPlan*>(plan);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(p->device);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->dmem) cudaFree(p->dmem);
+  cudaSetDevice(cur);
+  delete p;
+  return MORPH_OK;
 }
 
 int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg) {
@@ -215,7 +412,9 @@ const char* morph_status_string(int status) {
 
 int morph_device_error(void) {
   if (cudaDeviceSynchronize() != cudaSuccess) return MORPH_ERR_CUDA;
-  return fused_take_device_error();
+  const int a = fused_take_device_error();
+  const int b = batch_take_device_error();
+  return a ? a : b;
 }
 
 }  // extern "C"

@@ -1,0 +1,161 @@
+// Autotuner: measures, on the current GPU, the window size up to which the
+// direct method beats the blocked van Herk/Gil-Werman method, per pixel type
+// and per pass -- the crossovers w_x^0 / w_y^0 of the paper's section 5.3,
+// which the paper measured on an ARM CPU (59 and 69) and which differ on a
+// GPU.  Results persist as a small JSON file keyed by the device.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/morph.h"
+#include "morph_internal.h"
+#include "plan.h"
+
+namespace morph {
+namespace {
+
+constexpr int kTuneW = 2048, kTuneH = 2048;  // synthetic image for the timings
+constexpr int kReps = 5;
+
+std::string device_key() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  memset(&p, 0, sizeof(p));
+  cudaGetDeviceProperties(&p, dev);
+  int drv = 0;
+  cudaDriverGetVersion(&drv);
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|sm%d%d|%dSM|drv%d|v1", p.name, p.major, p.minor, p.multiProcessorCount, drv);
+  return buf;
+}
+
+// Median time (ms) of one forced configuration.
+float time_launch(FusedLaunch L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  if (!plan_single(&L)) return 1e30f;
+  std::vector<float> t;
+  for (int r = 0; r < kReps + 1; ++r) {
+    cudaEventRecord(e0, st);
+    if (fused_launch(L, st) != cudaSuccess) return 1e30f;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r) t.push_back(ms);  // the first run warms up
+  }
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
+bool load_cache(const char* path, const std::string& key, Tuning* t) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char buf[4096];
+  const size_t n = fread(buf, 1, sizeof(buf) - 1, f);
+  fclose(f);
+  buf[n] = 0;
+  const std::string s(buf);
+  const std::string kq = "\"device\": \"" + key + "\"";
+  if (s.find(kq) == std::string::npos) return false;
+  int v[4];
+  const char* p = strstr(buf, "\"cross\": [");
+  if (!p || sscanf(p, "\"cross\": [%d, %d, %d, %d]", &v[0], &v[1], &v[2], &v[3]) != 4) return false;
+  for (int x : v)
+    if (x < 0 || x > 100000) return false;
+  t->cross_row[0] = v[0];
+  t->cross_col[0] = v[1];
+  t->cross_row[1] = v[2];
+  t->cross_col[1] = v[3];
+  return true;
+}
+
+bool save_cache(const char* path, const std::string& key, const Tuning& t) {
+  FILE* f = fopen(path, "w");
+  if (!f) return false;
+  fprintf(f, "{\"device\": \"%s\", \"cross\": [%d, %d, %d, %d], \"order\": \"u8 x, u8 y, u16 x, u16 y\"}\n",
+          key.c_str(), t.cross_row[0], t.cross_col[0], t.cross_row[1], t.cross_col[1]);
+  return fclose(f) == 0;
+}
+
+}  // namespace
+}  // namespace morph
+
+using namespace morph;
+
+extern "C" int morph_autotune(const char* cache_path) {
+  const std::string key = device_key();
+  Tuning& t = tuning();
+  if (cache_path && load_cache(cache_path, key, &t)) {
+    t.from_autotune = 1;
+    return MORPH_OK;
+  }
+  void *src = nullptr, *dst = nullptr;
+  const size_t pitch = kTuneW * 2;
+  if (cudaMalloc(&src, pitch * kTuneH) != cudaSuccess) return MORPH_ERR_NOMEM;
+  if (cudaMalloc(&dst, pitch * kTuneH) != cudaSuccess) {
+    cudaFree(src);
+    return MORPH_ERR_NOMEM;
+  }
+  cudaMemset(src, 0x5A, pitch * kTuneH);
+  cudaStream_t st;
+  cudaEvent_t e0, e1;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int forced0 = t.forced_cfg[0], forced1 = t.forced_cfg[1];
+  int rc = MORPH_OK;
+  // Candidate windows; the direct method needs no minimum, the blocked one w >= 8.
+  const int cands[] = {8, 9, 11, 13, 15, 17, 21, 25, 31, 41, 51, 63};
+  int found[2][2] = {{7, 7}, {7, 7}};  // [type][axis 0: pass along x, 1: along y]
+  for (int e = 0; e < 2 && rc == MORPH_OK; ++e) {
+    for (int axis = 0; axis < 2 && rc == MORPH_OK; ++axis) {
+      for (int w : cands) {  // direct for w <= 7 always (the blocked method needs w >= 8)
+        FusedLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.esz = e + 1;
+        L.op = 0;
+        L.src = src;
+        L.dst = dst;
+        L.sp = L.dp = static_cast<long long>(pitch);
+        L.W = kTuneW;
+        L.H = kTuneH;
+        L.wx = axis == 0 ? w : 1;  // a 1-D window: only the measured pass runs
+        L.wy = axis == 0 ? 1 : w;
+        L.ax = L.wx / 2;
+        L.ay = L.wy / 2;
+        t.cross_row[e] = t.cross_col[e] = 1 << 30;  // direct
+        const float td = time_launch(L, st, e0, e1);
+        t.cross_row[e] = t.cross_col[e] = 0;  // blocked
+        const float tb = time_launch(L, st, e0, e1);
+        if (td >= 1e29f || tb >= 1e29f) {
+          rc = MORPH_ERR_CUDA;
+          break;
+        }
+        if (td <= tb)
+          found[e][axis] = w;
+        else
+          break;
+      }
+    }
+  }
+  for (int e = 0; e < 2; ++e) {
+    t.cross_row[e] = found[e][0];
+    t.cross_col[e] = found[e][1];
+  }
+  t.forced_cfg[0] = forced0;
+  t.forced_cfg[1] = forced1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  cudaFree(src);
+  cudaFree(dst);
+  if (rc != MORPH_OK) {
+    reset_tuning_defaults();
+    return rc;
+  }
+  t.from_autotune = 1;
+  if (cache_path && !save_cache(cache_path, key, t)) return MORPH_ERR_ARG;
+  return MORPH_OK;
+}

@@ -1,0 +1,40 @@
+// The single-image fused kernel template (one CTA per output tile) and the
+// table of its tile-shape instantiations.
+#pragma once
+
+#include "morph_internal.h"
+#include "morph_tile.cuh"
+
+namespace morph {
+
+template <typename T, int OP, int TX, int TY>
+__global__ void __launch_bounds__(kThreads, 4) fused_kernel(const __grid_constant__ CUtensorMap tin,
+                                                            const __grid_constant__ CUtensorMap tout,
+                                                            const ImgArgs a, const Geom g) {
+  __shared__ __align__(8) uint64_t bar;
+  extern __shared__ __align__(128) uint4 smem[];
+  if (a.tma_ld && threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  run_tile<T, OP, TX, TY>(a, &tin, &tout, blockIdx.x * TX, blockIdx.y * TY, g, smem, &bar, phase, a.err);
+}
+
+template <typename T, int OP>
+FusedKernelFn pick_fused_kernel(int cfg) {
+  switch (cfg) {
+    case kTile128x64: return fused_kernel<T, OP, 128, 64>;
+    case kTile64x64: return fused_kernel<T, OP, 64, 64>;
+    case kTile64x128: return fused_kernel<T, OP, 64, 128>;
+    case kTile256x32: return fused_kernel<T, OP, 256, 32>;
+    case kTile32x32: return fused_kernel<T, OP, 32, 32>;
+    case kTile128x128: return fused_kernel<T, OP, 128, 128>;
+    case kTile256x64: return fused_kernel<T, OP, 256, 64>;
+    case kTile32x128: return fused_kernel<T, OP, 32, 128>;
+  }
+  return nullptr;
+}
+
+}  // namespace morph

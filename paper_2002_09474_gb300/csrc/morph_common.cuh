@@ -38,13 +38,6 @@ template <int OP> __host__ __device__ constexpr uint32_t ident_word() {
   return OP == 0 ? 0xFFFFFFFFu : 0u;
 }
 
-// Lane-wise min (OP 0, erosion) or max (OP 1, dilation) of two packed words.
-template <typename T, int OP> __device__ __forceinline__ uint32_t pop(uint32_t a, uint32_t b);
-template <> __device__ __forceinline__ uint32_t pop<uint8_t, 0>(uint32_t a, uint32_t b) { return __vminu4(a, b); }
-template <> __device__ __forceinline__ uint32_t pop<uint8_t, 1>(uint32_t a, uint32_t b) { return __vmaxu4(a, b); }
-template <> __device__ __forceinline__ uint32_t pop<uint16_t, 0>(uint32_t a, uint32_t b) { return __vminu2(a, b); }
-template <> __device__ __forceinline__ uint32_t pop<uint16_t, 1>(uint32_t a, uint32_t b) { return __vmaxu2(a, b); }
-
 // In-register transpose of a PK x PK block of pixels held as PK words.
 // On entry v[i] holds row i (pixel j in lane j); on exit v[j] holds column j
 // (row i in lane i).  4x4 bytes: two butterfly rounds of byte permutes, first
@@ -72,6 +65,7 @@ __device__ __forceinline__ void transpose_block(uint32_t (&v)[2]) {
 // ---------------------------------------------------------------------------
 // Shared-memory / TMA / mbarrier wrappers (inline PTX).
 // ---------------------------------------------------------------------------
+#ifndef MORPH_HOST_EMU
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -109,16 +103,26 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
   return t;
 }
 
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 // Waits for the barrier phase with the given parity to complete; gives up
-// after kWaitLimitNs and returns false.
+// after kWaitLimitNs and returns false.  try_wait suspends the thread in
+// hardware until the phase completes or a short system time limit passes.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  if (mbar_test_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
-  unsigned ns = 32;
-  while (!mbar_test_wait(bar, parity)) {
+  while (!mbar_try_wait(bar, parity)) {
     if (global_timer_ns() - t0 > kWaitLimitNs) return false;
-    __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
   }
   return true;
 }
@@ -142,5 +146,34 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
+
+// 2-D tiled TMA store of one box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_addr(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+#else
+// Host stand-ins with the same signatures, defined by the CPU emulator of the
+// kernels (tests/emu); only compiled when MORPH_HOST_EMU is set.
+void mbar_init(uint64_t* bar, uint32_t count);
+void fence_barrier_init();
+void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes);
+bool mbar_try_wait(uint64_t* bar, uint32_t parity);
+bool mbar_wait_bounded(uint64_t* bar, uint32_t parity);
+void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y);
+void fence_proxy_async_smem();
+void prefetch_tensormap(const CUtensorMap* map);
+void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y);
+void bulk_commit();
+void bulk_wait_read_all();
+
+#endif
 
 }  // namespace morph

@@ -5,48 +5,37 @@
 #include <cudaTypedefs.h>
 
 #include "morph_internal.h"
-#include "morph_tile.cuh"
+#include "batch.h"
+#include "fused_kernel.cuh"
 
 namespace morph {
 
+// Device error word of the fused kernels (kernels get its address).
 __device__ int g_fused_err;
-
-template <typename T, int OP, int TX, int TY>
-__global__ void __launch_bounds__(kThreads, 2) fused_kernel(const __grid_constant__ CUtensorMap tin,
-                                                         const __grid_constant__ CUtensorMap tout,
-                                                         const ImgArgs a, const Geom g) {
-  __shared__ __align__(8) uint64_t bar;
-  extern __shared__ __align__(128) uint4 smem[];
-  if (a.tma_ld && threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    fence_barrier_init();
-  }
-  __syncthreads();
-  uint32_t phase = 0;
-  run_tile<T, OP, TX, TY>(a, &tin, &tout, blockIdx.x * TX, blockIdx.y * TY, g, smem, &bar, phase,
-                          &g_fused_err);
-}
 
 namespace {
 
-using KernelFn = void (*)(const CUtensorMap, const CUtensorMap, const ImgArgs, const Geom);
-
-template <typename T, int OP>
-KernelFn pick_kernel(int cfg) {
-  switch (cfg) {
-    case kTile128x64: return fused_kernel<T, OP, 128, 64>;
-    case kTile64x64: return fused_kernel<T, OP, 64, 64>;
-    case kTile64x128: return fused_kernel<T, OP, 64, 128>;
-    case kTile256x32: return fused_kernel<T, OP, 256, 32>;
-    case kTile32x32: return fused_kernel<T, OP, 32, 32>;
-    case kTile32x128: return fused_kernel<T, OP, 32, 128>;
-  }
-  return nullptr;
-}
+using KernelFn = FusedKernelFn;
 
 KernelFn kernel_for(int esz, int op, int cfg) {
-  if (esz == 1) return op == 0 ? pick_kernel<uint8_t, 0>(cfg) : pick_kernel<uint8_t, 1>(cfg);
-  return op == 0 ? pick_kernel<uint16_t, 0>(cfg) : pick_kernel<uint16_t, 1>(cfg);
+  if (cfg < 0 || cfg >= kNumTileCfg) return nullptr;
+  if (esz == 1) return op == 0 ? fused_kernel_u8_erode(cfg) : fused_kernel_u8_dilate(cfg);
+  return op == 0 ? fused_kernel_u16_erode(cfg) : fused_kernel_u16_dilate(cfg);
+}
+
+// Address of g_fused_err on the current device (cached per device).
+int* fused_err_ptr() {
+  static int* ptrs[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_fused_err) != cudaSuccess) return nullptr;
+    ptrs[dev] = static_cast<int*>(p);
+  }
+  return ptrs[dev];
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -71,6 +60,9 @@ bool encode_tensor_map_2d(CUtensorMap* map, const void* base, int esz, int W, in
   if (!fn) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15) || pitch >= (1ll << 40)) return false;
   if (box_w < 1 || box_w > 256 || box_h < 1 || box_h > 256 || (box_w * esz) % 16) return false;
+  // A box larger than the tensor is not used: the kernels' transfer counts
+  // assume full boxes.
+  if (box_w > W || box_h > H) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
   cuuint32_t box[2] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h)};
@@ -80,6 +72,32 @@ bool encode_tensor_map_2d(CUtensorMap* map, const void* base, int esz, int W, in
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+void fill_img_args(const FusedLaunch& L, const Geom& g, int TX, int TY, ImgArgs* ap, CUtensorMap* tin,
+                   CUtensorMap* tout) {
+  ImgArgs& a = *ap;
+  a.src = static_cast<const uint8_t*>(L.src);
+  a.dst = static_cast<uint8_t*>(L.dst);
+  a.sp = L.sp;
+  a.dp = L.dp;
+  a.W = L.W;
+  a.H = L.H;
+  a.wx = L.wx;
+  a.wy = L.wy;
+  a.ax = L.ax;
+  a.ay = L.ay;
+  a.blk_y = L.vhgw_col && L.wy > 1;
+  a.blk_x = L.vhgw_row && L.wx > 1;
+  a.err = fused_err_ptr();
+  a.ld_vec = (reinterpret_cast<uintptr_t>(L.src) % 4 == 0) && (L.sp % 4 == 0);
+  a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % 4 == 0) && (L.dp % 4 == 0);
+  memset(tin, 0, sizeof(*tin));
+  memset(tout, 0, sizeof(*tout));
+  a.tma_ld = encode_tensor_map_2d(tin, L.src, L.esz, L.W, L.H, L.sp, 128 / L.esz, g.bh) ? 1 : 0;
+  // TMA stores only with 128-byte box rows (tiles at least 128 bytes wide),
+  // the form proven on the GPU; the kernel uses them for whole tiles only.
+  a.tma_st = (TX * L.esz >= 128) && encode_tensor_map_2d(tout, L.dst, L.esz, L.W, L.H, L.dp, 128 / L.esz, TY);
 }
 
 int fused_smem_bytes(const FusedLaunch& L) {
@@ -93,34 +111,19 @@ cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
   if (g.smem_bytes > kMaxSmemBytes) return cudaErrorInvalidConfiguration;
   KernelFn k = kernel_for(L.esz, L.op, L.cfg);
   if (!k) return cudaErrorInvalidValue;
-  static bool opted[2][2][kNumTileCfg] = {};
-  bool& done = opted[L.esz - 1][L.op][L.cfg];
+  static bool opted[64][2][2][kNumTileCfg] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  bool& done = opted[dev & 63][L.esz - 1][L.op][L.cfg];
   if (!done) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
     if (e != cudaSuccess) return e;
     done = true;
   }
   ImgArgs a;
-  a.src = static_cast<const uint8_t*>(L.src);
-  a.dst = static_cast<uint8_t*>(L.dst);
-  a.sp = L.sp;
-  a.dp = L.dp;
-  a.W = L.W;
-  a.H = L.H;
-  a.wx = L.wx;
-  a.wy = L.wy;
-  a.ax = L.ax;
-  a.ay = L.ay;
-  a.blk_y = L.vhgw_col && L.wy > 1;
-  a.blk_x = L.vhgw_row && L.wx > 1;
-  a.ld_vec = (reinterpret_cast<uintptr_t>(L.src) % 4 == 0) && (L.sp % 4 == 0);
-  a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % 4 == 0) && (L.dp % 4 == 0);
   CUtensorMap tin, tout;
-  memset(&tin, 0, sizeof(tin));
-  memset(&tout, 0, sizeof(tout));
-  a.tma_ld = encode_tensor_map_2d(&tin, L.src, L.esz, L.W, L.H, L.sp, 128 / L.esz, g.bh) ? 1 : 0;
-  const int sbox = TX * L.esz < 128 ? TX * L.esz : 128;
-  a.tma_st = encode_tensor_map_2d(&tout, L.dst, L.esz, L.W, L.H, L.dp, sbox / L.esz, TY) ? 1 : 0;
+  fill_img_args(L, g, TX, TY, &a, &tin, &tout);
+  if (!a.err) return cudaErrorInvalidDevice;
   dim3 grid(cdiv(L.W, TX), cdiv(L.H, TY));
   k<<<grid, kThreads, g.smem_bytes, stream>>>(tin, tout, a, g);
   return cudaGetLastError();

@@ -23,7 +23,8 @@ struct Geom {
   int iw_pix;    // pixels needed per input row from the load start: ox + TX + wx - 1
   int noct;      // octets (8 pixels) per input row
   int k0;        // first octet holding needed pixels
-  int nbx;       // 128-byte TMA boxes per input row
+  int nbx;       // TMA boxes per input row
+  int box;       // bytes per box row (128)
   int ih;        // input rows: TY + wy - 1
   int nby, bh;   // TMA boxes down the tile and their height
   int ihp;       // rows allocated per box column (nby * bh)
@@ -46,10 +47,13 @@ __host__ __device__ inline Geom make_geom(int esz, int TX, int TY, int wx, int w
   g.iw_pix = g.ox + TX + wx - 1;
   g.noct = cdiv(g.iw_pix, 8);
   g.k0 = g.ox / 8;
+  // TMA boxes are 128 bytes wide (the form proven on the GPU; row-sized boxes
+  // of 32-96 bytes were seen to fault, see the design notes).
   g.nbx = cdiv(g.noct * 8 * esz, 128);
+  g.box = 128;
   g.ih = TY + wy - 1;
   g.nby = cdiv(g.ih, 256);
-  g.bh = cdiv(g.ih, g.nby);
+  g.bh = g.nby == 1 ? g.ih : round_up(cdiv(g.ih, g.nby), 8);  // keeps boxes 128-byte aligned
   g.ihp = g.nby * g.bh;
   g.nchy = cdiv(g.ih, kBlk);
   g.nrx = TX + wx - 1;
@@ -58,12 +62,16 @@ __host__ __device__ inline Geom make_geom(int esz, int TX, int TY, int wx, int w
   blk_y = blk_y && wy > 1;
   blk_x = blk_x && wx > 1;
   const int ntc = TY / 8;
-  const int s0 = g.nbx * g.ihp * 8;
-  const int sy = blk_y ? TY * g.noct : 0, ty = blk_y ? g.nchy * g.noct : 0;
-  const int ysc = 2 * round_up(sy, 8) + ty;
+  const int s0 = cdiv(g.nbx * g.ihp * g.box, 16);
+  // blocked-method scratch: S (nout rows), P (rows of blocks jlo .. jhi-1,
+  // jlo = (w-1)/8, jhi = ceil((w-1+nout)/8)) and one total per block
+  const int npy = kBlk * (cdiv(wy - 1 + TY, kBlk) - (wy - 1) / kBlk);
+  const int npx = kBlk * (cdiv(wx - 1 + TX, kBlk) - (wx - 1) / kBlk);
+  const int sy = blk_y ? TY * g.noct : 0, py = blk_y ? npy * g.noct : 0, ty = blk_y ? g.nchy * g.noct : 0;
+  const int ysc = round_up(sy, 8) + round_up(py, 8) + ty;
   const int s1t = (wx > 1) ? g.t_rows * ntc : 0;
-  const int sx = blk_x ? TX * ntc : 0, tx = blk_x ? g.nchx * ntc : 0;
-  const int xsc = 2 * round_up(sx, 8) + tx;
+  const int sx = blk_x ? TX * ntc : 0, px = blk_x ? npx * ntc : 0, tx = blk_x ? g.nchx * ntc : 0;
+  const int xsc = round_up(sx, 8) + round_up(px, 8) + tx;
   const int s2 = TY * TX * esz / 16;
   // Buffers share two regions A (offset 0) and B according to their live
   // ranges: the pass along y reads S0 and writes either its scratch or, for
@@ -115,11 +123,11 @@ __host__ __device__ inline Geom make_geom(int esz, int TX, int TY, int wx, int w
   g.off_s0 = 0;
   g.off_sy = place(where_sy, 0);
   g.off_py = place(where_sy, round_up(sy, 8));
-  g.off_ty = place(where_sy, 2 * round_up(sy, 8));
+  g.off_ty = place(where_sy, round_up(sy, 8) + round_up(py, 8));
   g.off_s1t = place(where_s1t, 0);
   g.off_sx = place(where_sx, 0);
   g.off_px = place(where_sx, round_up(sx, 8));
-  g.off_tx = place(where_sx, 2 * round_up(sx, 8));
+  g.off_tx = place(where_sx, round_up(sx, 8) + round_up(px, 8));
   g.off_s2 = place(where_s2, 0);
   g.smem_bytes = 16 * (offb + round_up(b, 8));
   return g;

@@ -17,15 +17,17 @@ enum TileCfg : int {
   kTile64x128 = 2,
   kTile256x32 = 3,
   kTile32x32 = 4,
-  kTile32x128 = 5,
-  kNumTileCfg = 6
+  kTile128x128 = 5,
+  kTile256x64 = 6,
+  kTile32x128 = 7,
+  kNumTileCfg = 8
 };
 inline int tile_tx(int cfg) {
-  static const int tx[kNumTileCfg] = {128, 64, 64, 256, 32, 32};
+  static const int tx[kNumTileCfg] = {128, 64, 64, 256, 32, 128, 256, 32};
   return tx[cfg];
 }
 inline int tile_ty(int cfg) {
-  static const int ty[kNumTileCfg] = {64, 64, 128, 32, 32, 128};
+  static const int ty[kNumTileCfg] = {64, 64, 128, 32, 32, 128, 64, 128};
   return ty[cfg];
 }
 
@@ -48,10 +50,24 @@ struct FusedLaunch {
 // Shared-memory bytes the fused kernel needs for this launch (0 if the
 // configuration is invalid).
 int fused_smem_bytes(const FusedLaunch& L);
+// Kernel entry of one (pixel type, op, tile configuration); defined in the
+// instantiation units fused_inst_*.cu.
+struct ImgArgs;
+struct Geom;
+using FusedKernelFn = void (*)(const CUtensorMap, const CUtensorMap, const ImgArgs, const Geom);
+FusedKernelFn fused_kernel_u8_erode(int cfg);
+FusedKernelFn fused_kernel_u8_dilate(int cfg);
+FusedKernelFn fused_kernel_u16_erode(int cfg);
+FusedKernelFn fused_kernel_u16_dilate(int cfg);
+
 // Enqueues the fused kernel; returns a cudaError_t.
 cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream);
 // Reads and clears the fused kernels' device error word.
 int fused_take_device_error();
+
+// Enqueues the tiled transpose kernel: dst (W rows of H pixels) = src^T.
+cudaError_t transpose_launch(const void* src, long long sp, void* dst, long long dp, int W, int H, int esz,
+                             cudaStream_t stream);
 
 // Encodes a 2-D tiled tensor map over a pitched image (driver entry point
 // resolved through the runtime).  Returns false if TMA cannot describe it.

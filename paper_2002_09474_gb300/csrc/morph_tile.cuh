@@ -30,8 +30,8 @@
 //   3. Pass along x (wx x 1 element, section 5.2) on S1T with the same two
 //      methods -- the paper's "transpose, vertical pass, transpose" (sections
 //      1 and 5.2.1) -- and the 8x8 results transposed back into row-major S2.
-//   4. S2 leaves by a TMA 2-D store (clipped to the image by the hardware) or
-//      by plain stores.
+//   4. S2 leaves by a TMA 2-D store when the tile lies wholly inside the
+//      image, otherwise by plain stores checked pixel by pixel.
 // A window of width 1 skips its pass and the transposes around it.
 // Each image pixel crosses HBM once in and once out; tile halos are re-read
 // from L2.
@@ -42,7 +42,7 @@
 
 namespace morph {
 
-constexpr int kThreads = 256;  // threads per CTA of every tile kernel
+constexpr int kThreads = 128;  // threads per CTA of every tile kernel
 
 // ---------------------------------------------------------------------------
 // Packed helpers on octets (uint4 = 8 pixels in 16-bit lanes)
@@ -103,6 +103,7 @@ struct ImgArgs {
   int tma_st;          // 1: S2 leaves by TMA through the output tensor map
   int ld_vec;          // 1: src rows allow aligned 32-bit loads
   int st_vec;          // 1: dst rows allow aligned 32-bit stores
+  int* err;            // device error word (set when a bounded wait gives up)
 };
 
 // ---------------------------------------------------------------------------
@@ -155,16 +156,23 @@ __device__ __forceinline__ void direct_group(const In& in, int r0, int w, uint4 
 // 16-bit lanes.
 // ---------------------------------------------------------------------------
 // Octet k of the TMA landing buffer (128-byte boxes, `ihp` rows per box column).
+// Byte offset of byte b of row r in the TMA landing buffer: one box per row
+// (box = the row) or 128-byte boxes stacked per box column of `ihp` rows.
+__device__ __forceinline__ int s0_off(int r, int b, const Geom& g) {
+  return g.nbx == 1 ? r * g.box + b : (b >> 7) * (g.ihp * 128) + r * 128 + (b & 127);
+}
+
 template <typename T>
 struct S0Col {
   const uint8_t* base;
-  __device__ __forceinline__ S0Col(const uint8_t* s0, int k, int ihp) {
-    const int byte = k * 8 * static_cast<int>(sizeof(T));
-    base = s0 + (byte >> 7) * (ihp * 128) + (byte & 127);
+  int stride;
+  __device__ __forceinline__ S0Col(const uint8_t* s0, int k, const Geom& g) {
+    base = s0 + s0_off(0, k * 8 * static_cast<int>(sizeof(T)), g);
+    stride = g.nbx == 1 ? g.box : 128;
   }
   __device__ __forceinline__ uint4 operator()(int r) const {
-    if (sizeof(T) == 1) return widen8(*reinterpret_cast<const uint2*>(base + r * 128));
-    return *reinterpret_cast<const uint4*>(base + r * 128);
+    if (sizeof(T) == 1) return widen8(*reinterpret_cast<const uint2*>(base + r * stride));
+    return *reinterpret_cast<const uint4*>(base + r * stride);
   }
 };
 
@@ -178,6 +186,14 @@ struct TCol {
   __device__ __forceinline__ uint4 operator()(int xr) const {
     return base[xr * ntc + (c ^ ((xr >> 3) & MT))];
   }
+};
+
+// A block-aligned run of S1T rows whose swizzled chunk is fixed: row i at
+// base[i * stride].
+struct TColB {
+  const uint4* base;
+  int stride;
+  __device__ __forceinline__ uint4 operator()(int i) const { return base[i * stride]; }
 };
 
 // S2 (output tile, original pixel type), octet k: rows of `SBOX`-byte boxes.
@@ -212,93 +228,124 @@ __device__ __forceinline__ void transpose8(const uint4 (&v)[8], uint4 (&t)[8]) {
 }
 
 // ---------------------------------------------------------------------------
-// Blocked large-window method, phase 1: block j (rows 8j .. 8j+7 of the
-// column, rows >= nrows read as the identity) -> suffix S (stored for rows
-// < nout), prefix P (stored at row - (w-1) for rows w-1 .. w-2+nout) and the
-// block total T[j].  Phase 2 then gives out[s] = op(S[s], P[s], totals of the
-// blocks strictly between the blocks of s and s+w-1).
+// Blocked large-window method.  The scanned column is cut into blocks of 8
+// rows (block j = rows 8j .. 8j+7).  Phase 1 (one thread per block) loads the
+// block into registers and stores its suffix op S (rows of blocks j < nout/8),
+// its prefix op P (blocks jlo <= j < jhi: rows w-1 .. w-2+nout, kept from row
+// 8*jlo on) and its total T[j].  Phase 2 (one thread per 8 outputs) gives
+//   out[s] = op(S[s], P[s+w-1], T[j] for the blocks strictly inside),
+// a window starting in one block and ending in a later one (w >= 8).
 // ---------------------------------------------------------------------------
-template <int OP, class In, class St>
-__device__ __forceinline__ void blocked_scan(const In& in, int j, int nrows, int w, int nout, const St& st) {
+struct BlkGeo {
+  int nrows;  // input rows of the pass (rows >= nrows read as the identity)
+  int nout;   // outputs (a multiple of 8)
+  int w;      // window
+  int jlo;    // first block whose prefix is kept: (w-1)/8
+  int jhi;    // one past the last: ceil((w-1+nout)/8)
+};
+__device__ __forceinline__ BlkGeo blk_geo(int nrows, int nout, int w) {
+  BlkGeo b;
+  b.nrows = nrows;
+  b.nout = nout;
+  b.w = w;
+  b.jlo = (w - 1) / kBlk;
+  b.jhi = (w - 1 + nout + kBlk - 1) / kBlk;
+  return b;
+}
+
+// BlkGeo for a phase-1 call that passes rows relative to block j (block 0 of
+// the shifted view is block j of the pass).
+__device__ __forceinline__ BlkGeo bg_shift(const BlkGeo& b, int j) {
+  BlkGeo s = b;
+  s.nrows = b.nrows - kBlk * j;
+  s.nout = b.nout - kBlk * j;
+  s.jlo = b.jlo - j;
+  s.jhi = b.jhi - j;
+  return s;
+}
+
+// Phase 1 for block j.  sp/pp/tp: where rows 8j.. of S / P and T[j] go,
+// consecutive rows `stride` uint4 apart.
+template <int OP, class In>
+__device__ __forceinline__ void blocked_scan(const In& in, int j, const BlkGeo& b, uint4* sp, uint4* pp,
+                                             uint4* tp, int stride) {
   const uint32_t id = ident_word<OP>();
   uint4 v[kBlk];
   const int r0 = j * kBlk;
+  if (r0 + kBlk <= b.nrows) {
 #pragma unroll
-  for (int i = 0; i < kBlk; ++i) v[i] = (r0 + i < nrows) ? in(r0 + i) : make_uint4(id, id, id, id);
-  uint4 p = v[0];
+    for (int i = 0; i < kBlk; ++i) v[i] = in(r0 + i);
+  } else {
 #pragma unroll
-  for (int i = 0; i < kBlk; ++i) {
-    if (i) p = op4<OP>(p, v[i]);
-    const int e = r0 + i - (w - 1);
-    if (e >= 0 && e < nout) st.p(e, p);
+    for (int i = 0; i < kBlk; ++i) v[i] = (r0 + i < b.nrows) ? in(r0 + i) : make_uint4(id, id, id, id);
+  }
+  if (j >= b.jlo && j < b.jhi) {
+    uint4 p = v[0];
+    pp[0] = p;
+#pragma unroll
+    for (int i = 1; i < kBlk; ++i) {
+      p = op4<OP>(p, v[i]);
+      pp[i * stride] = p;
+    }
   }
   uint4 sfx = v[kBlk - 1];
+  const bool keep_s = r0 < b.nout;
+  if (keep_s) sp[(kBlk - 1) * stride] = sfx;
 #pragma unroll
-  for (int i = kBlk - 1; i >= 0; --i) {
-    if (i < kBlk - 1) sfx = op4<OP>(sfx, v[i]);
-    if (r0 + i < nout) st.s(r0 + i, sfx);
+  for (int i = kBlk - 2; i >= 0; --i) {
+    sfx = op4<OP>(sfx, v[i]);
+    if (keep_s) sp[i * stride] = sfx;
   }
-  st.t(j, sfx);
+  *tp = sfx;
 }
 
-// Phase 2 for outputs s = 8k .. 8k+7 (all < nout).
+// Phase 2 for outputs s = 8k .. 8k+7.  The window of output 8k+i ends in
+// block ce0 for i < isplit and in block ce0+1 after; ld gives S row s
+// (s_at), P for output i (p_at) and T[j] (t_at).
 template <int OP, class Ld>
 __device__ __forceinline__ void blocked_combine(const Ld& ld, int k, int w, uint4 (&out)[kBlk]) {
   const uint32_t id = ident_word<OP>();
-  const int ce0 = (k * kBlk + w - 1) / kBlk;  // block of the first window's end
-  uint4 ma = make_uint4(id, id, id, id);      // totals of blocks k+1 .. ce0-1
-  for (int j = k + 1; j < ce0; ++j) ma = op4<OP>(ma, ld.t(j));
-  const uint4 mb = (ce0 > k) ? op4<OP>(ma, ld.t(ce0)) : ma;  // ... k+1 .. ce0
+  const int e0 = k * kBlk + w - 1;
+  const int ce0 = e0 / kBlk;
+  const int isplit = kBlk * (ce0 + 1) - e0;
+  uint4 ma = make_uint4(id, id, id, id);  // totals of blocks k+1 .. ce0-1
+  for (int j = k + 1; j < ce0; ++j) ma = op4<OP>(ma, ld.t_at(j));
+  const uint4 mb = (ce0 > k) ? op4<OP>(ma, ld.t_at(ce0)) : ma;  // ... k+1 .. ce0
 #pragma unroll
   for (int i = 0; i < kBlk; ++i) {
-    const int s = k * kBlk + i;
-    const uint4 m = ((s + w - 1) / kBlk == ce0) ? ma : mb;
-    out[i] = op4<OP>(op4<OP>(ld.s(s), ld.p(s)), m);
+    const uint4 m = (i < isplit) ? ma : mb;
+    out[i] = op4<OP>(op4<OP>(ld.s_at(i), ld.p_at(i, isplit)), m);
   }
 }
 
-// Scratch of the blocked method on a plain row-major buffer (pass along y:
-// lanes of a warp take consecutive columns, so no swizzle is needed).
-struct YScratch {
-  uint4 *sb, *pb, *tb;
-  int pitch, c;
-  __device__ __forceinline__ void s(int r, uint4 v) const { sb[r * pitch + c] = v; }
-  __device__ __forceinline__ void p(int r, uint4 v) const { pb[r * pitch + c] = v; }
-  __device__ __forceinline__ void t(int j, uint4 v) const { tb[j * pitch + c] = v; }
-  __device__ __forceinline__ uint4 s(int r) const { return sb[r * pitch + c]; }
-  __device__ __forceinline__ uint4 p(int r) const { return pb[r * pitch + c]; }
-  __device__ __forceinline__ uint4 t(int j) const { return tb[j * pitch + c]; }
+// Phase-2 view of the y-pass scratch (row-major, octet column c).
+struct YLd {
+  const uint4 *s, *p, *t;  // S row 8k, P row for output 8k, T row 0 -- all at column c
+  int pitch;
+  __device__ __forceinline__ uint4 s_at(int i) const { return s[i * pitch]; }
+  __device__ __forceinline__ uint4 p_at(int i, int) const { return p[i * pitch]; }
+  __device__ __forceinline__ uint4 t_at(int j) const { return t[j * pitch]; }
 };
 
-// Scratch of the blocked method for the pass along x: phase 2 gives lanes
-// consecutive 8-row groups, so chunk indices are XOR-swizzled by row/8.
+// Phase-2 view of the x-pass scratch: rows of NTC chunks, chunk c stored at
+// c ^ ((row/8) & MT) so that lanes working on consecutive 8-row groups hit
+// distinct banks.
 template <int MT>
-struct XScratch {
-  uint4 *sb, *pb, *tb;
-  int ntc, c;
-  __device__ __forceinline__ int at(int r) const { return r * ntc + (c ^ ((r >> 3) & MT)); }
-  __device__ __forceinline__ int att(int j) const { return j * ntc + (c ^ (j & MT)); }
-  __device__ __forceinline__ void s(int r, uint4 v) const { sb[at(r)] = v; }
-  __device__ __forceinline__ void p(int r, uint4 v) const { pb[at(r)] = v; }
-  __device__ __forceinline__ void t(int j, uint4 v) const { tb[att(j)] = v; }
-  __device__ __forceinline__ uint4 s(int r) const { return sb[at(r)]; }
-  __device__ __forceinline__ uint4 p(int r) const { return pb[at(r)]; }
-  __device__ __forceinline__ uint4 t(int j) const { return tb[att(j)]; }
+struct XLd {
+  const uint4 *sb, *pb, *tb;
+  int c, ntc, k, prow0;  // prow0: P buffer row of output 8k
+  __device__ __forceinline__ uint4 s_at(int i) const {
+    return sb[(kBlk * k + i) * ntc + (c ^ (k & MT))];
+  }
+  __device__ __forceinline__ uint4 p_at(int i, int) const {
+    const int r = prow0 + i;
+    return pb[r * ntc + (c ^ ((r >> 3) & MT))];
+  }
+  __device__ __forceinline__ uint4 t_at(int j) const { return tb[j * ntc + (c ^ (j & MT))]; }
 };
 
 template <typename T> __device__ __forceinline__ uint32_t load_px(const uint8_t* row, int x) {
   return reinterpret_cast<const T*>(row)[x];
-}
-
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(smem_addr(src)), "r"(x), "r"(y)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -328,10 +375,10 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
   if (a.tma_ld) {
     if (tid == 0) {
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(bar, static_cast<uint32_t>(g.nbx * g.nby * 128 * g.bh));
+      mbar_arrive_expect_tx(bar, static_cast<uint32_t>(g.nbx * g.nby * g.box * g.bh));
       for (int bx = 0; bx < g.nbx; ++bx)
         for (int by = 0; by < g.nby; ++by)
-          tma_load_2d(s0 + (bx * g.ihp + by * g.bh) * 128, tin, bar, xs + bx * (128 / E), ys + by * g.bh);
+          tma_load_2d(s0 + (bx * g.ihp + by * g.bh) * g.box, tin, bar, xs + bx * (g.box / E), ys + by * g.bh);
     }
     const bool ok = mbar_wait_bounded(bar, phase);
     phase ^= 1u;
@@ -341,11 +388,10 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     }
     // TMA fills out-of-image pixels with 0: the identity of max, not of min.
     if (OP == 0 && border) {
-      uint32_t* s0w = reinterpret_cast<uint32_t*>(s0);
       for (Strided2D i(w_hi - w_lo, tid, kThreads); i.r < g.ih; i.next()) {
         const int c = w_lo + i.c, r = i.r;
         const int y = ys + r;
-        uint32_t* pw = s0w + (c >> 5) * (g.ihp * 32) + r * 32 + (c & 31);
+        uint32_t* pw = reinterpret_cast<uint32_t*>(s0 + s0_off(r, 4 * c, g));
         if (y < 0 || y >= a.H) {
           *pw = IDW;
         } else {
@@ -361,7 +407,6 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
       __syncthreads();
     }
   } else {
-    uint32_t* s0w = reinterpret_cast<uint32_t*>(s0);
     for (Strided2D i(w_hi - w_lo, tid, kThreads); i.r < g.ih; i.next()) {
       const int c = w_lo + i.c, r = i.r;
       const int y = ys + r;
@@ -382,7 +427,7 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
           }
         }
       }
-      s0w[(c >> 5) * (g.ihp * 32) + r * 32 + (c & 31)] = v;
+      *reinterpret_cast<uint32_t*>(s0 + s0_off(r, 4 * c, g)) = v;
     }
     __syncthreads();
   }
@@ -390,7 +435,6 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
   uint8_t* s2 = reinterpret_cast<uint8_t*>(smem + g.off_s2);
   uint4* s1t = smem + g.off_s1t;
   const int nk = g.noct - g.k0;  // octet columns of S0 the pass along y covers
-  const YScratch ysc0{smem + g.off_sy, smem + g.off_py, smem + g.off_ty, g.noct, 0};
 
   // Emits the 8 y-pass outputs rows 8k..8k+7 of octet column c.
   auto emit_y = [&](int c, int k, const uint4 (&o)[kBlk]) {
@@ -401,11 +445,16 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     } else {
       uint4 t[kBlk];
       transpose8(o, t);
+      // S1T row 8c+px is pixel column xr = 8c+px-ox (relative to the first
+      // needed one); its chunk k is stored at k ^ ((xr/8) & MT).  Rows with
+      // xr < 0 are never read.
+      const int xr0 = kBlk * c - g.ox;
+      const int split = (xr0 & 7) ? kBlk - (xr0 & 7) : kBlk;
+      const int ca = k ^ ((xr0 >> 3) & MT), cb = k ^ (((xr0 + 7) >> 3) & MT);
+      uint4* row = s1t + (kBlk * c) * NTC;
 #pragma unroll
-      for (int px = 0; px < kBlk; ++px) {
-        const int xr = 8 * c + px - g.ox;  // pixel column relative to the first needed one
-        if (xr >= 0) s1t[(g.ox + xr) * NTC + (k ^ ((xr >> 3) & MT))] = t[px];
-      }
+      for (int px = 0; px < kBlk; ++px)
+        if (xr0 + px >= 0) row[px * NTC + (px < split ? ca : cb)] = t[px];
     }
   };
 
@@ -413,33 +462,37 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
   if (a.wy == 1 && a.wx > 1) {
     for (Strided2D i(nk, tid, kThreads); i.r < NTC; i.next()) {  // transpose only
       const int c = g.k0 + i.c, k = i.r;
-      const S0Col<T> col(s0, c, g.ihp);
+      const S0Col<T> col(s0, c, g);
       uint4 o[kBlk];
 #pragma unroll
       for (int q = 0; q < kBlk; ++q) o[q] = col(kBlk * k + q);
       emit_y(c, k, o);
     }
   } else if (a.blk_y) {
+    const BlkGeo bg = blk_geo(g.ih, TY, a.wy);
+    uint4* sy = smem + g.off_sy;
+    uint4* py = smem + g.off_py;
+    uint4* ty = smem + g.off_ty;
+    const int pitch = g.noct;
     for (Strided2D i(nk, tid, kThreads); i.r < g.nchy; i.next()) {
-      const int c = g.k0 + i.c;
-      YScratch st = ysc0;
-      st.c = c;
-      blocked_scan<OP>(S0Col<T>(s0, c, g.ihp), i.r, g.ih, a.wy, TY, st);
+      const int c = g.k0 + i.c, j = i.r;
+      blocked_scan<OP>(S0Col<T>(s0, c, g), j, bg, sy + (kBlk * j) * pitch + c,
+                       py + (kBlk * (j - bg.jlo)) * pitch + c, ty + j * pitch + c, pitch);
     }
     __syncthreads();
     for (Strided2D i(nk, tid, kThreads); i.r < NTC; i.next()) {
-      const int c = g.k0 + i.c;
-      YScratch ld = ysc0;
-      ld.c = c;
+      const int c = g.k0 + i.c, k = i.r;
+      const YLd ld{sy + (kBlk * k) * pitch + c, py + (kBlk * k + a.wy - 1 - kBlk * bg.jlo) * pitch + c,
+                   ty + c, pitch};
       uint4 o[kBlk];
-      blocked_combine<OP>(ld, i.r, a.wy, o);
-      emit_y(c, i.r, o);
+      blocked_combine<OP>(ld, k, a.wy, o);
+      emit_y(c, k, o);
     }
   } else {
     for (Strided2D i(nk, tid, kThreads); i.r < NTC; i.next()) {
       const int c = g.k0 + i.c;
       uint4 o[kBlk];
-      direct_group<OP, kBlk>(S0Col<T>(s0, c, g.ihp), kBlk * i.r, a.wy, o);
+      direct_group<OP, kBlk>(S0Col<T>(s0, c, g), kBlk * i.r, a.wy, o);
       emit_y(c, i.r, o);
     }
   }
@@ -456,18 +509,22 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
       for (int r = 0; r < kBlk; ++r) out.store(kBlk * c + r, rw[r]);
     };
     if (a.blk_x) {
-      const XScratch<MT> xsc0{smem + g.off_sx, smem + g.off_px, smem + g.off_tx, NTC, 0};
+      const BlkGeo bg = blk_geo(g.nrx, TX, a.wx);
+      uint4* sx = smem + g.off_sx;
+      uint4* px = smem + g.off_px;
+      uint4* tx = smem + g.off_tx;
       for (int it = tid; it < NTC * g.nchx; it += kThreads) {
         const int c = it % NTC, j = it / NTC;
-        XScratch<MT> st = xsc0;
-        st.c = c;
-        blocked_scan<OP>(TCol<MT>{s1x, NTC, c}, j, g.nrx, a.wx, TX, st);
+        const int cs = c ^ (j & MT);                 // S rows 8j.. (block-aligned)
+        const int cp = c ^ ((j - bg.jlo) & MT);      // P rows 8(j-jlo)..
+        const TColB in{s1x + (kBlk * j) * NTC + cs, NTC};
+        blocked_scan<OP>(in, 0, bg_shift(bg, j), sx + (kBlk * j) * NTC + cs,
+                         px + (kBlk * (j - bg.jlo)) * NTC + cp, tx + j * NTC + (c ^ (j & MT)), NTC);
       }
       __syncthreads();
       for (int it = tid; it < NXO * NTC; it += kThreads) {
         const int k = it % NXO, c = it / NXO;
-        XScratch<MT> ld = xsc0;
-        ld.c = c;
+        const XLd<MT> ld{sx, px, tx, c, NTC, k, kBlk * k + a.wx - 1 - kBlk * bg.jlo};
         uint4 o[kBlk];
         blocked_combine<OP>(ld, k, a.wx, o);
         emit_x(c, k, o);
@@ -483,7 +540,9 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
   }
 
   // ---- 4. store S2 ---------------------------------------------------------------
-  if (a.tma_st) {
+  // The TMA store is used only for tiles that lie wholly inside the image;
+  // tiles on the right or bottom edge take the plain, per-pixel-checked path.
+  if (a.tma_st && x0 + TX <= a.W && y0 + TY <= a.H) {
     fence_proxy_async_smem();  // make this thread's S2 writes visible to the TMA unit
     __syncthreads();
     if (tid == 0) {

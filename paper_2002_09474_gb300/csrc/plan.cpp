@@ -9,39 +9,44 @@ namespace morph {
 namespace {
 Tuning g_tuning;
 bool g_init = false;
+}  // namespace
 
-// Relative cost of one launch configuration per output pixel, from the work
-// each phase does on the tile (input area for the load and the y pass, the
-// x pass on the y-pass output, two transposes) and a penalty for low
-// occupancy.  Only used to rank tile shapes; the autotuner can override.
+// Estimated time of one launch configuration (arbitrary units): each phase
+// of a tile costs (rounds of 128 threads over its work items) x (work per
+// item); tiles run in waves of (152 SMs x CTAs per SM).  Only used to rank
+// tile shapes; the autotuner measures the classes it is asked about.
 double tile_cost(const FusedLaunch& L, int cfg) {
-  const double TX = tile_tx(cfg), TY = tile_ty(cfg);
-  const Geom g = make_geom(L.esz, tile_tx(cfg), tile_ty(cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
+  const int TX = tile_tx(cfg), TY = tile_ty(cfg);
+  const Geom g = make_geom(L.esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
   if (g.smem_bytes > kMaxSmemBytes) return 1e30;
-  const double iw = 8.0 * (g.noct - g.k0), ih = g.ih;
-  double cost = iw * ih / (TX * TY) * 0.5;  // TMA landing, border fix-up
+  const double thr = 128.0;
+  auto rounds = [&](double items) { return std::ceil(items / thr); };
+  const double nk = g.noct - g.k0, ntc = TY / 8.0, nxo = TX / 8.0;
+  double t = 4.0 + rounds(g.ih * g.noct * 2.0 * L.esz / 4.0) * 0.5;  // landing, fix-up
   if (L.wy > 1) {
-    // y pass per output octet: blocked = scan of (ih/TY) inputs + combine,
-    // direct = (w+7)/8 row reads per output
-    const double per = L.vhgw_col ? 2.0 * ih / TY + 2.0 + L.wy / 64.0 : (L.wy + 7.0) / 8.0 + 1.0;
-    cost += iw / TX * per;
+    if (L.vhgw_col)
+      t += rounds(nk * g.nchy) * 10.0 + rounds(nk * ntc) * (20.0 + L.wy / 8.0);
+    else
+      t += rounds(nk * ntc) * (8.0 + L.wy) * 1.2;
+  } else if (L.wx > 1) {
+    t += rounds(nk * ntc) * 10.0;
   }
   if (L.wx > 1) {
-    const double xin = (TX + L.wx - 1) / TX;
-    const double per = L.vhgw_row ? 2.0 * xin + 2.0 + L.wx / 64.0 : (L.wx + 7.0) / 8.0 + 1.0;
-    cost += 1.0 * iw / TX + 1.0 + per;  // transposes + the pass
+    if (L.vhgw_row)
+      t += rounds(ntc * g.nchx) * 10.0 + rounds(nxo * ntc) * (28.0 + L.wx / 8.0);
+    else
+      t += rounds(nxo * ntc) * ((8.0 + L.wx) * 1.2 + 8.0);
   }
-  // CTAs per SM from shared memory and from registers (2 CTAs of 256 threads)
-  int per_sm = (232448) / (g.smem_bytes + 1024);
-  if (per_sm > 2) per_sm = 2;
+  int per_sm = 232448 / (g.smem_bytes + 1024);
+  if (per_sm > 4) per_sm = 4;
   if (per_sm < 1) per_sm = 1;
-  cost *= per_sm >= 2 ? 1.0 : 1.4;
-  // few CTAs for a small image: the GPU (152 SMs) is not filled
-  const double ctas = std::ceil(L.W / TX) * std::ceil(L.H / TY);
-  if (ctas < 152.0 * per_sm) cost *= 1.0 + 0.5 * (1.0 - ctas / (152.0 * per_sm));
-  return cost;
+  const double ntiles = std::ceil(static_cast<double>(L.W) / TX) * std::ceil(static_cast<double>(L.H) / TY);
+  const double slots = 152.0 * per_sm;
+  const double waves = std::ceil(ntiles / slots);
+  // CTAs sharing an SM hide each other's latency but share its issue slots
+  const double share = per_sm >= 3 ? 0.55 : per_sm == 2 ? 0.7 : 1.0;
+  return waves * t * (ntiles < slots ? 1.0 : share * per_sm) / per_sm * 4.0;
 }
-}  // namespace
 
 void reset_tuning_defaults() {
   for (int e = 0; e < 2; ++e) {

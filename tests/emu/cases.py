@@ -1,0 +1,66 @@
+"""Launch cases for the CPU emulator of the fused kernel (the same shapes,
+windows, anchors, methods, tile shapes and pitches as the GPU parity tests).
+Prints one case per line: esz op W H spad soff dpad doff wx wy ax ay cfg
+cross_x cross_y seed."""
+import itertools
+import sys
+
+DIRECT, BLOCKED = 1000000, 0
+
+
+def aligned_pad(w, esz):
+    return (16 - (w * esz) % 16) % 16
+
+
+def cases(full=True):
+    seed = 1
+    out = []
+
+    def add(esz, op, w, h, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, cx, cy):
+        nonlocal seed
+        out.append((esz, op, w, h, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, cx, cy, seed))
+        seed += 1
+
+    shapes = [(1, 1), (2, 3), (5, 17), (33, 7), (67, 130), (129, 257), (200, 300)]
+    wins = [(1, 1), (3, 3), (2, 5), (7, 1), (1, 9), (4, 4), (8, 8), (9, 16), (17, 8), (15, 15),
+            (31, 7), (64, 65), (61, 61)]
+    methods = {"direct": (DIRECT, DIRECT), "vhgw": (BLOCKED, BLOCKED), "mixed": (BLOCKED, DIRECT)}
+    for esz in (1, 2):
+        for m, (cx, cy) in methods.items():
+            for (h, w) in shapes:
+                for n, (wx, wy) in enumerate(wins):
+                    for op in (0, 1):
+                        pad = aligned_pad(w, esz) if (n + op) % 2 else 0
+                        add(esz, op, w, h, pad, 0, pad, 0, wx, wy, wx // 2, wy // 2, -1, cx, cy)
+        for cfg in range(8):
+            for c in (DIRECT, BLOCKED):
+                for (wx, wy, ax, ay) in ((3, 5, 1, 2), (8, 2, 7, 0), (21, 51, 10, 25), (101, 1, 50, 0),
+                                         (1, 33, 0, 16), (127, 127, 63, 63)):
+                    for op in (0, 1):
+                        for pad in (0, aligned_pad(301, esz)):
+                            add(esz, op, 301, 177, pad, 0, pad, 0, wx, wy, ax, ay, cfg, c, c)
+        for c in (DIRECT, BLOCKED):
+            for (wx, wy) in ((4, 3), (6, 6), (5, 2)):
+                for ax, ay in itertools.product(range(wx), range(wy)):
+                    add(esz, 0, 70, 45, aligned_pad(70, esz), 0, aligned_pad(70, esz), 0, wx, wy, ax, ay,
+                        -1, c, c)
+        for pad, off, dpad, doff in [(0, 0, 0, 0), (aligned_pad(150, esz), 0, 32, 0), (13 * esz, 0, 13 * esz, 0),
+                                     (6, 4, 2, 8), (esz, esz, 3 * esz, esz)]:
+            for (wx, wy) in ((3, 3), (17, 9), (40, 40)):
+                for op in (0, 1):
+                    add(esz, op, 150, 90, pad, off, dpad, doff, wx, wy, wx // 2, wy // 2, -1, -1, -1)
+        for (wx, wy, ax, ay) in ((75, 47, 37, 23), (200, 3, 0, 1), (3, 500, 2, 499), (1000, 1000, 1, 998)):
+            for op in (0, 1):
+                add(esz, op, 37, 23, aligned_pad(37, esz), 0, 0, 0, wx, wy, ax, ay, -1, -1, -1)
+        if full:
+            for cfg in range(8):
+                for c in (DIRECT, BLOCKED):
+                    for (wx, wy) in ((3, 3), (1, 17), (17, 1), (21, 51)):
+                        for op in (0, 1):
+                            add(esz, op, 512, 256, 0, 0, 0, 0, wx, wy, wx // 2, wy // 2, cfg, c, c)
+    return out
+
+
+if __name__ == "__main__":
+    for c in cases(full="--quick" not in sys.argv):
+        print(*c)

@@ -1,0 +1,398 @@
+// CPU emulator of the fused erosion/dilation tile kernel -- TEST
+// INFRASTRUCTURE ONLY.
+//
+// Compiles the kernel's own tile code (paper_2002_09474_gb300/csrc/
+// morph_tile.cuh) for the host with MORPH_HOST_EMU set, runs every CTA as
+// kThreads std::threads meeting at a real barrier for __syncthreads, and
+// models the TMA unit and the mbarrier transaction count in software.  Built
+// with AddressSanitizer, so any shared-memory access outside a CTA's exact
+// dynamic allocation and any global access outside the image buffers stops
+// the run.  It also checks the rules the hardware does not check for us:
+// TMA coordinates 16-byte aligned, no store box starting outside the tensor,
+// boxes no larger than the tensor, transfer counts that match the expected
+// bytes.  Results are compared with the brute-force oracle.
+//
+// Input, one case per line on stdin:
+//   esz op W H spad soff dpad doff wx wy ax ay cfg cross_x cross_y seed
+// (pads/offsets in bytes; cfg -1 = the planner's choice).  Output: one line
+// per case, "OK ..." or "FAIL ...".
+#define MORPH_HOST_EMU 1
+
+#include <atomic>
+#include <mutex>
+#include <barrier>
+#include <chrono>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+// ---- device-language shim (host definitions of what the tile code uses) ----
+thread_local uint3 emu_threadIdx;
+#define threadIdx emu_threadIdx
+
+struct EmuCta {
+  std::barrier<>* bar = nullptr;
+  std::atomic<int> orflag{0};
+  // mbarrier: a phase completes when its arrivals are in and its transaction
+  // count is back to zero; the phase bit then flips.
+  std::mutex mu;
+  int count = 1, pending = 1;
+  long long tx = 0;
+  int phase_bit = 0;
+  const uint8_t* smem = nullptr;
+  size_t smem_size = 0;
+  std::atomic<int> errors{0};
+  std::string first_error;
+  std::atomic<int> partial_stores{0};
+};
+thread_local EmuCta* g_cta = nullptr;
+
+static void emu_error(const char* what) {
+  if (g_cta->errors.fetch_add(1) == 0) g_cta->first_error = what;
+}
+
+static inline void __syncthreads() { g_cta->bar->arrive_and_wait(); }
+static inline int __syncthreads_or(int p) {
+  if (p) g_cta->orflag.store(1);
+  g_cta->bar->arrive_and_wait();
+  const int r = g_cta->orflag.load();
+  g_cta->bar->arrive_and_wait();
+  if (threadIdx.x == 0) g_cta->orflag.store(0);
+  g_cta->bar->arrive_and_wait();
+  return r;
+}
+static inline unsigned int __vminu2(unsigned int a, unsigned int b) {
+  const unsigned lo = (a & 0xFFFFu) < (b & 0xFFFFu) ? (a & 0xFFFFu) : (b & 0xFFFFu);
+  const unsigned hi = (a >> 16) < (b >> 16) ? (a >> 16) : (b >> 16);
+  return lo | (hi << 16);
+}
+static inline unsigned int __vmaxu2(unsigned int a, unsigned int b) {
+  const unsigned lo = (a & 0xFFFFu) > (b & 0xFFFFu) ? (a & 0xFFFFu) : (b & 0xFFFFu);
+  const unsigned hi = (a >> 16) > (b >> 16) ? (a >> 16) : (b >> 16);
+  return lo | (hi << 16);
+}
+// Byte selection from the 8-byte value {y, x}: result byte i is byte
+// (s >> 4i) & 7 (bit 3 of each selector nibble replicates that byte's sign).
+static inline unsigned int __byte_perm(unsigned int x, unsigned int y, unsigned int s) {
+  const uint64_t v = (static_cast<uint64_t>(y) << 32) | x;
+  unsigned int r = 0;
+  for (int i = 0; i < 4; ++i) {
+    const unsigned sel = (s >> (4 * i)) & 0xF;
+    unsigned byte = static_cast<unsigned>(v >> (8 * (sel & 7))) & 0xFFu;
+    if (sel & 8) byte = (byte & 0x80u) ? 0xFFu : 0u;
+    r |= byte << (8 * i);
+  }
+  return r;
+}
+static inline int atomicExch(int* p, int v) { return __atomic_exchange_n(p, v, __ATOMIC_SEQ_CST); }
+
+#include "morph_tile.cuh"
+
+// ---- TMA / mbarrier model ------------------------------------------------------
+struct EmuMap {
+  const uint8_t* base;
+  uint8_t* wbase;
+  int esz, W, H;
+  long long pitch;
+  int bw, bh;  // box, in elements
+};
+static_assert(sizeof(EmuMap) <= sizeof(CUtensorMap), "map too large");
+
+static void check_smem(const void* p, size_t bytes, size_t align, const char* what) {
+  const uint8_t* b = static_cast<const uint8_t*>(p);
+  if (b < g_cta->smem || b + bytes > g_cta->smem + g_cta->smem_size) emu_error(what);
+  if ((b - g_cta->smem) % align) emu_error("TMA shared-memory address misaligned");
+}
+
+namespace morph {
+static void mbar_check_complete() {  // caller holds g_cta->mu
+  if (g_cta->pending == 0 && g_cta->tx == 0) {
+    g_cta->phase_bit ^= 1;
+    g_cta->pending = g_cta->count;
+  }
+}
+void mbar_init(uint64_t*, uint32_t count) {
+  std::lock_guard<std::mutex> l(g_cta->mu);
+  g_cta->count = g_cta->pending = static_cast<int>(count);
+  g_cta->tx = 0;
+  g_cta->phase_bit = 0;
+}
+void fence_barrier_init() {}
+void mbar_arrive_expect_tx(uint64_t*, uint32_t bytes) {
+  std::lock_guard<std::mutex> l(g_cta->mu);
+  g_cta->tx += bytes;
+  g_cta->pending -= 1;
+  mbar_check_complete();
+}
+bool mbar_try_wait(uint64_t*, uint32_t parity) {
+  std::lock_guard<std::mutex> l(g_cta->mu);
+  return g_cta->phase_bit != static_cast<int>(parity);
+}
+bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const auto t0 = std::chrono::steady_clock::now();
+  while (!mbar_try_wait(bar, parity)) {
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(5)) {
+      std::lock_guard<std::mutex> l(g_cta->mu);
+      emu_error(g_cta->tx < 0 ? "TMA delivered more bytes than expected"
+                              : "TMA transfer count never reached the expected bytes (the wait times out)");
+      return false;
+    }
+    std::this_thread::yield();
+  }
+  return true;
+}
+void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t*, int x, int y) {
+  const EmuMap* m = reinterpret_cast<const EmuMap*>(map);
+  if ((static_cast<long long>(x) * m->esz) % 16) emu_error("TMA load x not 16-byte aligned");
+  if (m->bw > m->W || m->bh > m->H) emu_error("TMA box larger than the tensor");
+  const size_t row = static_cast<size_t>(m->bw) * m->esz;
+  check_smem(dst, row * m->bh, 128, "TMA load box outside shared memory");
+  uint8_t* d = static_cast<uint8_t*>(dst);
+  for (int r = 0; r < m->bh; ++r)
+    for (int c = 0; c < m->bw; ++c) {
+      const int gx = x + c, gy = y + r;
+      for (int b = 0; b < m->esz; ++b) {
+        uint8_t v = 0;
+        if (gx >= 0 && gx < m->W && gy >= 0 && gy < m->H) v = m->base[gy * m->pitch + gx * m->esz + b];
+        d[r * row + c * m->esz + b] = v;
+      }
+    }
+  std::lock_guard<std::mutex> l(g_cta->mu);
+  g_cta->tx -= static_cast<long long>(row) * m->bh;
+  mbar_check_complete();
+}
+void fence_proxy_async_smem() {}
+void prefetch_tensormap(const CUtensorMap*) {}
+void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  const EmuMap* m = reinterpret_cast<const EmuMap*>(map);
+  if (x < 0 || y < 0) emu_error("TMA store starts at a negative coordinate");
+  if (x >= m->W || y >= m->H) emu_error("TMA store starts outside the tensor");
+  if ((static_cast<long long>(x) * m->esz) % 16) emu_error("TMA store x not 16-byte aligned");
+  if (m->bw > m->W || m->bh > m->H) emu_error("TMA store box larger than the tensor");
+  if (x + m->bw > m->W || y + m->bh > m->H) g_cta->partial_stores++;
+  const size_t row = static_cast<size_t>(m->bw) * m->esz;
+  check_smem(src, row * m->bh, 128, "TMA store box outside shared memory");
+  const uint8_t* s = static_cast<const uint8_t*>(src);
+  for (int r = 0; r < m->bh; ++r)
+    for (int c = 0; c < m->bw; ++c) {
+      const int gx = x + c, gy = y + r;
+      if (gx < m->W && gy < m->H)
+        for (int b = 0; b < m->esz; ++b) m->wbase[gy * m->pitch + gx * m->esz + b] = s[r * row + c * m->esz + b];
+    }
+}
+void bulk_commit() {}
+void bulk_wait_read_all() {}
+}  // namespace morph
+
+// ---- host side: planner (linked from plan.cpp) ----------------------------------
+#include "morph_internal.h"
+#include "plan.h"
+namespace morph {
+int fused_smem_bytes(const FusedLaunch& L) {
+  if (L.cfg < 0 || L.cfg >= kNumTileCfg) return 0;
+  return make_geom(L.esz, tile_tx(L.cfg), tile_ty(L.cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row).smem_bytes;
+}
+}  // namespace morph
+
+extern "C" int oracle_morph(const void* src, int esz, int W, int H, long long pitch, int wx, int wy, int ax,
+                            int ay, int op, void* dst, long long dpitch);
+
+using namespace morph;
+
+using CtaFn = void (*)(const ImgArgs&, const CUtensorMap*, const CUtensorMap*, int, int, const Geom&, uint4*,
+                       uint64_t*, uint32_t&, int*);
+
+template <typename T, int OP, int TX, int TY>
+void cta_body(const ImgArgs& a, const CUtensorMap* tin, const CUtensorMap* tout, int x0, int y0, const Geom& g,
+              uint4* smem, uint64_t* bar, uint32_t& phase, int* err) {
+  run_tile<T, OP, TX, TY>(a, tin, tout, x0, y0, g, smem, bar, phase, err);
+}
+
+template <typename T, int OP>
+CtaFn pick(int cfg) {
+  switch (cfg) {
+    case kTile128x64: return cta_body<T, OP, 128, 64>;
+    case kTile64x64: return cta_body<T, OP, 64, 64>;
+    case kTile64x128: return cta_body<T, OP, 64, 128>;
+    case kTile256x32: return cta_body<T, OP, 256, 32>;
+    case kTile32x32: return cta_body<T, OP, 32, 32>;
+    case kTile128x128: return cta_body<T, OP, 128, 128>;
+    case kTile256x64: return cta_body<T, OP, 256, 64>;
+    case kTile32x128: return cta_body<T, OP, 32, 128>;
+  }
+  return nullptr;
+}
+
+static void clip_window(int n, int w, int a, int* w_out, int* a_out) {
+  const int before = a < n - 1 ? a : n - 1;
+  const int after = (w - 1 - a) < n - 1 ? (w - 1 - a) : n - 1;
+  *a_out = before;
+  *w_out = before + after + 1;
+}
+
+// A pool of kThreads workers that run one CTA's body per pool_run call.
+#include <functional>
+static std::function<void(int)> g_job;
+static std::barrier<>* g_start = nullptr;
+static std::barrier<>* g_done = nullptr;
+static bool g_quit = false;
+static void pool_init() {
+  static std::barrier<> start(kThreads + 1), done(kThreads + 1);
+  g_start = &start;
+  g_done = &done;
+  for (int t = 0; t < kThreads; ++t)
+    std::thread([t] {
+      for (;;) {
+        g_start->arrive_and_wait();
+        if (g_quit) return;
+        g_job(t);
+        g_done->arrive_and_wait();
+      }
+    }).detach();
+}
+static void pool_run(std::function<void(int)> job) {
+  g_job = std::move(job);
+  g_start->arrive_and_wait();
+  g_done->arrive_and_wait();
+}
+
+static uint64_t splitmix(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+int main() {
+  int esz, op, W, H, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, crx, cry;
+  unsigned long long seed;
+  int failures = 0, cases = 0;
+  pool_init();
+  while (scanf("%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %llu", &esz, &op, &W, &H, &spad, &soff, &dpad, &doff,
+               &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed) == 16) {
+    ++cases;
+    const long long sp = static_cast<long long>(W) * esz + spad, dp = static_cast<long long>(W) * esz + dpad;
+    // Exact-size buffers: ASan flags any byte outside [offset, last pixel].
+    const size_t sbytes = soff + (H - 1) * sp + static_cast<size_t>(W) * esz;
+    const size_t dbytes = doff + (H - 1) * dp + static_cast<size_t>(W) * esz;
+    uint8_t* sbuf = static_cast<uint8_t*>(aligned_alloc(256, (sbytes + 255) / 256 * 256));
+    uint8_t* dbuf = static_cast<uint8_t*>(aligned_alloc(256, (dbytes + 255) / 256 * 256));
+    // aligned_alloc rounds the size up; poison nothing extra ourselves but
+    // check guard bytes below.
+    uint64_t st = seed;
+    for (size_t i = 0; i < sbytes; ++i) sbuf[i] = static_cast<uint8_t>(splitmix(st));
+    memset(dbuf, 0xA5, dbytes);
+    const uint8_t* src = sbuf + soff;
+    uint8_t* dst = dbuf + doff;
+
+    Tuning& t = tuning();
+    reset_tuning_defaults();
+    if (crx >= 0) t.cross_row[esz - 1] = crx;
+    if (cry >= 0) t.cross_col[esz - 1] = cry;
+    t.forced_cfg[esz - 1] = cfg;
+    FusedLaunch L{};
+    L.esz = esz;
+    L.op = op;
+    L.src = src;
+    L.dst = dst;
+    L.sp = sp;
+    L.dp = dp;
+    L.W = W;
+    L.H = H;
+    clip_window(W, wx, ax, &L.wx, &L.ax);
+    clip_window(H, wy, ay, &L.wy, &L.ay);
+    if (!plan_single(&L)) {
+      printf("FAIL case %d: no plan\n", cases);
+      ++failures;
+      continue;
+    }
+    const int TX = tile_tx(L.cfg), TY = tile_ty(L.cfg);
+    const Geom g = make_geom(esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
+    ImgArgs a{};
+    a.src = src;
+    a.dst = dst;
+    a.sp = sp;
+    a.dp = dp;
+    a.W = W;
+    a.H = H;
+    a.wx = L.wx;
+    a.wy = L.wy;
+    a.ax = L.ax;
+    a.ay = L.ay;
+    a.blk_y = L.vhgw_col && L.wy > 1;
+    a.blk_x = L.vhgw_row && L.wx > 1;
+    a.ld_vec = (reinterpret_cast<uintptr_t>(src) % 4 == 0) && (sp % 4 == 0);
+    a.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
+    int errword = 0;
+    a.err = &errword;
+    // the launcher's TMA decisions (same rules as encode_tensor_map_2d)
+    auto tma_ok = [&](const void* base, long long pitch, int bw, int bh) {
+      return !(reinterpret_cast<uintptr_t>(base) & 15) && !(pitch & 15) && bw >= 1 && bw <= 256 && bh >= 1 &&
+             bh <= 256 && (bw * esz) % 16 == 0 && bw <= W && bh <= H;
+    };
+    CUtensorMap tin{}, tout{};
+    EmuMap mi{src, nullptr, esz, W, H, sp, g.box / esz, g.bh};
+    const int sbox = TX * esz < 128 ? TX * esz : 128;
+    EmuMap mo{nullptr, dst, esz, W, H, dp, sbox / esz, TY};
+    a.tma_ld = tma_ok(src, sp, mi.bw, mi.bh);
+    a.tma_st = TX * esz >= 128 && tma_ok(dst, dp, mo.bw, mo.bh);
+    memcpy(&tin, &mi, sizeof(mi));
+    memcpy(&tout, &mo, sizeof(mo));
+    CtaFn fn = esz == 1 ? (op == 0 ? pick<uint8_t, 0>(L.cfg) : pick<uint8_t, 1>(L.cfg))
+                        : (op == 0 ? pick<uint16_t, 0>(L.cfg) : pick<uint16_t, 1>(L.cfg));
+    const int gx = cdiv(W, TX), gy = cdiv(H, TY);
+    int errors = 0, partial = 0;
+    std::string first;
+    for (int by = 0; by < gy; ++by)
+      for (int bx = 0; bx < gx; ++bx) {
+        EmuCta cta;
+        std::barrier<> bar(kThreads);
+        cta.bar = &bar;
+        uint4* smem = static_cast<uint4*>(aligned_alloc(128, (g.smem_bytes + 127) / 128 * 128));
+        cta.smem = reinterpret_cast<const uint8_t*>(smem);
+        cta.smem_size = g.smem_bytes;
+        uint64_t mbar = 0;
+        pool_run([&](int tid) {
+          g_cta = &cta;
+          emu_threadIdx = make_uint3(tid, 0, 0);
+          uint32_t phase = 0;
+          __syncthreads();
+          fn(a, &tin, &tout, bx * TX, by * TY, g, smem, &mbar, phase, a.err);
+        });
+        free(smem);
+        errors += cta.errors.load();
+        partial += cta.partial_stores.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+    // compare with the oracle, and check the bytes between rows are untouched
+    std::vector<uint8_t> want(static_cast<size_t>(W) * H * esz);
+    oracle_morph(src, esz, W, H, sp, wx, wy, ax, ay, op, want.data(), static_cast<long long>(W) * esz);
+    long long bad = 0, guard = 0;
+    for (int y = 0; y < H; ++y) {
+      if (memcmp(dst + y * dp, want.data() + static_cast<size_t>(y) * W * esz, static_cast<size_t>(W) * esz)) ++bad;
+      if (y < H - 1)
+        for (long long b = static_cast<long long>(W) * esz; b < dp; ++b)
+          if (dst[y * dp + b] != 0xA5) ++guard;
+    }
+    for (int b = 0; b < doff; ++b)
+      if (dbuf[b] != 0xA5) ++guard;
+    const bool ok = !errors && !bad && !guard && !errword;
+    if (!ok) ++failures;
+    printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d partial_st %d "
+           "rows_bad %lld guard %lld dev_err %d %s\n",
+           ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
+           a.tma_st, partial, bad, guard, errword, first.c_str());
+    fflush(stdout);
+    free(sbuf);
+    free(dbuf);
+  }
+  fprintf(stderr, "%d cases, %d failures\n", cases, failures);
+  return failures ? 1 : 0;
+}

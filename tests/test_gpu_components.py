@@ -1,0 +1,174 @@
+"""GPU parity of the transpose kernels (section 4), the batched persistent
+launch and its CUDA-graph plan, the host-buffer entry point and the
+autotuner -- all bit-exact against the CPU oracle."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_09474_gb300 import synth
+
+from gpu_util import DeviceImage, need_cuda
+
+pytestmark = pytest.mark.gpu
+OPS = ("erode", "dilate")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    need_cuda()
+    from paper_2002_09474_gb300 import morph
+    morph.morph_reset_tuning()
+    yield morph
+    morph.morph_reset_tuning()
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_transpose(lib, dtype):
+    torch = need_cuda()
+    g = synth.rng(200)
+    esz = np.dtype(dtype).itemsize
+    fn = lib.transpose_u8 if dtype == np.uint8 else lib.transpose_u16
+    for (h, w) in ((1, 1), (3, 5), (8, 8), (16, 16), (64, 64), (65, 63), (100, 257), (512, 300)):
+        img = synth.uniform_image(w, h, dtype, gen=g)
+        for spad, dpad in ((0, 0), ((16 - w * esz % 16) % 16, (16 - h * esz % 16) % 16), (6, 2)):
+            src = DeviceImage(torch, h, w, dtype, pad=spad, fill=img)
+            dst = DeviceImage(torch, w, h, dtype, pad=dpad)
+            rc = fn(src.ptr, w, h, src.pitch, dst.ptr, dst.pitch, 0)
+            assert rc == 0, lib.status_string(rc)
+            torch.cuda.synchronize()
+            assert dst.untouched_outside()
+            np.testing.assert_array_equal(dst.read(), oracle.transpose(img))
+            np.testing.assert_array_equal(dst.read(), img.T)
+
+
+def test_transpose_commutes_with_erosion(lib):
+    """erode(S^T, wy x wx) = erode(S, wx x wy)^T through the GPU path."""
+    torch = need_cuda()
+    img = synth.uniform_image(200, 130, np.uint8, seed=201)
+    s = torch.from_numpy(img).cuda()
+    t = torch.empty((200, 130), dtype=torch.uint8, device="cuda")
+    lib.transpose(s, t)
+    e1 = torch.empty_like(s)
+    e2 = torch.empty_like(t)
+    lib.apply(s, e1, 21, 5, op=0)
+    lib.apply(t, e2, 5, 21, op=0)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(e1.cpu().numpy().T, e2.cpu().numpy())
+
+
+def _batch(lib, torch, specs, g):
+    """Device images for specs (u8/u16 mixed), descriptors, and the expected
+    oracle outputs."""
+    imgs, outs, descs, want = [], [], [], []
+    for (w, h, wx, wy, ax, ay, op, dt) in specs:
+        img = synth.uniform_image(w, h, dt, gen=g)
+        src = torch.from_numpy(img).cuda()
+        dst = torch.full_like(src, 0x5A)
+        imgs.append(src)
+        outs.append(dst)
+        d = lib.MorphDesc()
+        d.src, d.dst, d.width, d.height = src.data_ptr(), dst.data_ptr(), w, h
+        d.src_pitch = d.dst_pitch = w * np.dtype(dt).itemsize
+        d.wx, d.wy, d.anchor_x, d.anchor_y = wx, wy, ax, ay
+        d.op = op
+        d.dtype = lib.MORPH_U8 if dt == np.uint8 else lib.MORPH_U16
+        descs.append(d)
+        want.append(oracle.morph(img, wx, wy, ax, ay, OPS[op]))
+    arr = (lib.MorphDesc * len(descs))(*descs)
+    return imgs, outs, arr, want
+
+
+def _random_specs(g, n, side_hi=300, w_hi=63, dtypes=(np.uint8, np.uint16)):
+    specs = []
+    for _ in range(n):
+        w, h = int(g.integers(1, side_hi)), int(g.integers(1, side_hi))
+        wx, wy = int(g.integers(1, w_hi + 1)), int(g.integers(1, w_hi + 1))
+        specs.append((w, h, wx, wy, wx // 2, wy // 2, int(g.integers(0, 2)),
+                      dtypes[int(g.integers(0, len(dtypes)))]))
+    return specs
+
+
+def test_batch_single_launch(lib):
+    torch = need_cuda()
+    g = synth.rng(210)
+    specs = _random_specs(g, 60) + [(1, 1, 1, 1, 0, 0, 0, np.uint8), (2048, 3, 63, 1, 31, 0, 1, np.uint8),
+                                     (3, 700, 1, 63, 0, 31, 0, np.uint16)]
+    imgs, outs, arr, want = _batch(lib, torch, specs, g)
+    rc = lib.morph_batch(arr, len(specs), 0)
+    assert rc == 0, lib.status_string(rc)
+    assert lib.morph_device_error() == 0
+    for i, (o, w) in enumerate(zip(outs, want)):
+        np.testing.assert_array_equal(o.cpu().numpy(), w, err_msg=str(specs[i]))
+
+
+def test_batch_plan_graph_replays(lib):
+    torch = need_cuda()
+    g = synth.rng(211)
+    specs = _random_specs(g, 40)
+    imgs, outs, arr, want = _batch(lib, torch, specs, g)
+    plan = ctypes.c_void_p()
+    rc = lib.morph_batch_plan_create(arr, len(specs), ctypes.byref(plan))
+    assert rc == 0, lib.status_string(rc)
+    try:
+        for _ in range(3):
+            for o in outs:
+                o.fill_(0x5A)
+            rc = lib.morph_batch_plan_launch(plan, 0)
+            assert rc == 0, lib.status_string(rc)
+            assert lib.morph_device_error() == 0
+            for i, (o, w) in enumerate(zip(outs, want)):
+                np.testing.assert_array_equal(o.cpu().numpy(), w, err_msg=str(specs[i]))
+    finally:
+        assert lib.morph_batch_plan_destroy(plan) == 0
+
+
+def test_batch_matches_single_calls(lib):
+    """Each image's batched result equals its single-image result."""
+    torch = need_cuda()
+    g = synth.rng(212)
+    specs = [s for s in _random_specs(g, 30, side_hi=600, dtypes=(np.uint8,))]
+    imgs, outs, arr, want = _batch(lib, torch, specs, g)
+    assert lib.morph_batch(arr, len(specs), 0) == 0
+    for (w, h, wx, wy, ax, ay, op, dt), src, o in zip(specs, imgs, outs):
+        single = torch.empty_like(src)
+        lib.apply(src, single, wx, wy, ax, ay, op=op)
+        torch.cuda.synchronize()
+        assert torch.equal(single, o)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_host_buffer_entry_point(lib, dtype):
+    torch = need_cuda()
+    g = synth.rng(220)
+    img = synth.uniform_image(333, 211, dtype, gen=g)
+    tdt = torch.uint8 if dtype == np.uint8 else torch.uint16
+    for pinned in (False, True):
+        src = torch.from_numpy(img.copy())
+        dst = torch.zeros((211, 333), dtype=tdt)
+        if pinned:
+            src, dst = src.pin_memory(), dst.pin_memory()
+        for (wx, wy, op) in ((3, 3, 0), (21, 51, 1), (127, 1, 0)):
+            lib.apply_host(src, dst, wx, wy, op=op)
+            np.testing.assert_array_equal(dst.numpy(), oracle.morph(img, wx, wy, wx // 2, wy // 2, OPS[op]))
+    assert lib.morph_release_staging() == 0
+
+
+def test_autotune_and_cache(lib, tmp_path):
+    torch = need_cuda()
+    path = str(tmp_path / "tune.json")
+    assert lib.morph_autotune(path) == 0
+    text = open(path).read()
+    assert '"cross"' in text and "GB300" in text.upper() or '"device"' in text
+    # a second call loads the cache; results stay exact either way
+    assert lib.morph_autotune(path) == 0
+    img = synth.uniform_image(300, 200, np.uint8, seed=221)
+    s = torch.from_numpy(img).cuda()
+    for (wx, wy) in ((9, 9), (15, 31), (63, 5)):
+        o = torch.empty_like(s)
+        lib.apply(s, o, wx, wy, op=0)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(o.cpu().numpy(), oracle.morph(img, wx, wy, wx // 2, wy // 2, "erode"))
+    lib.morph_reset_tuning()

@@ -30,6 +30,12 @@ def lib():
     morph.morph_reset_tuning()
 
 
+def aligned_pad(w, dtype):
+    """Row padding that makes the pitch a multiple of 16 bytes (TMA path)."""
+    row = w * np.dtype(dtype).itemsize
+    return (16 - row % 16) % 16
+
+
 def run(lib, torch, img, wx, wy, ax, ay, op, pad=0, offset=0, dst_pad=None, dst_offset=0):
     h, w = img.shape
     src = DeviceImage(torch, h, w, img.dtype, pad=pad, offset=offset, fill=img)
@@ -40,6 +46,7 @@ def run(lib, torch, img, wx, wy, ax, ay, op, pad=0, offset=0, dst_pad=None, dst_
                          wx, wy, ax, ay, 0)
     assert rc == 0, lib.status_string(rc)
     torch.cuda.synchronize()
+    assert lib.morph_device_error() == 0, "a kernel reported a device-side error"
     assert dst.untouched_outside(), "kernel wrote outside the destination image"
     assert src.untouched_outside()
     return dst.read()
@@ -65,16 +72,18 @@ def test_shapes_windows_methods(lib, dtype, method):
     g = synth.rng(100 + (dtype == np.uint16))
     for (h, w) in SHAPES:
         img = synth.uniform_image(w, h, dtype, gen=g)
-        for (wx, wy) in WINDOWS:
+        for n, (wx, wy) in enumerate(WINDOWS):
             ax, ay = wx // 2, wy // 2
             for op in ("erode", "dilate"):
-                got = run(lib, torch, img, wx, wy, ax, ay, op)
+                # alternate plain-load (unaligned pitch) and TMA (aligned) paths
+                pad = aligned_pad(w, dtype) if (n + (op == "dilate")) % 2 else 0
+                got = run(lib, torch, img, wx, wy, ax, ay, op, pad=pad, dst_pad=pad)
                 want = oracle.morph(img, wx, wy, ax, ay, op)
                 assert np.array_equal(got, want), (h, w, wx, wy, op, method)
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_every_tile_shape(lib, dtype, cfg):
     torch = need_cuda()
     lib.morph_reset_tuning()
@@ -83,11 +92,13 @@ def test_every_tile_shape(lib, dtype, cfg):
     for method in ("direct", "vhgw"):
         c = DIRECT if method == "direct" else VHGW
         set_methods(lib, dtype, c, c, cfg)
-        for (wx, wy, ax, ay) in ((3, 5, 1, 2), (8, 2, 7, 0), (21, 51, 10, 25), (101, 1, 50, 0)):
+        for (wx, wy, ax, ay) in ((3, 5, 1, 2), (8, 2, 7, 0), (21, 51, 10, 25), (101, 1, 50, 0),
+                                 (1, 33, 0, 16), (127, 127, 63, 63)):
             for op in ("erode", "dilate"):
-                got = run(lib, torch, img, wx, wy, ax, ay, op)
-                want = oracle.morph(img, wx, wy, ax, ay, op)
-                assert np.array_equal(got, want), (cfg, method, wx, wy, op)
+                for pad in (0, aligned_pad(301, dtype)):
+                    got = run(lib, torch, img, wx, wy, ax, ay, op, pad=pad, dst_pad=pad)
+                    want = oracle.morph(img, wx, wy, ax, ay, op)
+                    assert np.array_equal(got, want), (cfg, method, wx, wy, op, pad)
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
@@ -137,6 +148,24 @@ def test_windows_larger_than_image(lib, dtype):
             got = run(lib, torch, img, wx, wy, ax, ay, op)
             want = oracle.morph(img, wx, wy, ax, ay, op)
             assert np.array_equal(got, want), (wx, wy, ax, ay, op)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_tma_paths_on_whole_tiles(lib, dtype):
+    """Sizes that are whole multiples of every tile shape with 16-byte
+    pitches: every tile loads and stores through TMA."""
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    g = synth.rng(150)
+    img = synth.uniform_image(512, 256, dtype, gen=g)
+    for cfg in range(8):
+        for c in (DIRECT, VHGW):
+            set_methods(lib, dtype, c, c, cfg)
+            for (wx, wy) in ((3, 3), (1, 17), (17, 1), (21, 51)):
+                for op in ("erode", "dilate"):
+                    got = run(lib, torch, img, wx, wy, wx // 2, wy // 2, op)
+                    want = oracle.morph(img, wx, wy, wx // 2, wy // 2, op)
+                    assert np.array_equal(got, want), (cfg, c, wx, wy, op)
 
 
 def test_constant_and_extreme_values(lib):
