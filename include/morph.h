@@ -62,7 +62,8 @@ typedef enum {
     MORPH_ERR_NOMEM = -8,   /* a device/host allocation failed                 */
     MORPH_ERR_DTYPE = -9,   /* unknown dtype or op code                        */
     MORPH_ERR_ARG = -10,    /* any other invalid argument (count, plan, ...)   */
-    MORPH_ERR_DEVICE = -11  /* a kernel reported an error in the device word   */
+    MORPH_ERR_DEVICE = -11, /* a kernel reported an error in the device word   */
+    MORPH_ERR_LIMIT = -12   /* more images than morph_batch_noalloc accepts    */
 } morph_status;
 
 /* dtype and op codes used by morph_apply and morph_desc. */
@@ -147,6 +148,28 @@ int morph_batch(const morph_desc *descs_host, int n, void *stream);
 int morph_batch_plan_create(const morph_desc *descs_host, int n, void **plan);
 int morph_batch_plan_launch(void *plan, void *stream);
 int morph_batch_plan_destroy(void *plan);
+
+/*
+ * The paper has no counterpart to this entry point; it serves callers that
+ * may not allocate device memory at all -- code whose device memory is owned
+ * by another allocator or memory pool, real-time loops where cudaMalloc's
+ * implicit synchronisation is not allowed, or plug-in hosts that hand over
+ * only pre-allocated image buffers.  It runs the same batched persistent
+ * kernel as morph_batch, but its scratch (per-image records, tensor maps, the
+ * tile counter) lives in a fixed array in the library's device memory image,
+ * which every GPU that loads the library keeps until the process exits.  It
+ * calls no cudaMalloc/cudaFree and no allocating routine.
+ *
+ * At most MORPH_NOALLOC_MAX_IMAGES images per call (MORPH_ERR_LIMIT beyond).
+ * The first call on a device looks up the array's device address (the
+ * set-up), so make that first call before any stream capture.  All calls
+ * share the one array and its host-side staging copy: calls that overlap on
+ * the GPU, or run concurrently from several host threads, race.  The counter
+ * the kernel schedules tiles with is reset on every call.  Asynchronous on
+ * `stream`; descs_host may be reused when the call returns.
+ */
+#define MORPH_NOALLOC_MAX_IMAGES 256
+int morph_batch_noalloc(const morph_desc *descs_host, int n, void *stream);
 
 /*
  * Transpose (section 4): dst[x][y] = src[y][x].  src is width x height pixels

@@ -406,6 +406,7 @@ const char* morph_status_string(int status) {
     case MORPH_ERR_DTYPE: return "unknown dtype or op";
     case MORPH_ERR_ARG: return "invalid argument";
     case MORPH_ERR_DEVICE: return "device-side error reported by a kernel";
+    case MORPH_ERR_LIMIT: return "more images than the no-allocation entry point accepts";
   }
   return "unknown status";
 }

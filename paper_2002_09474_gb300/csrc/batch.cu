@@ -179,6 +179,17 @@ cudaError_t batch_enqueue(const BatchHost& h, const BatchImage* d_imgs, const CU
   return cudaGetLastError();
 }
 
+cudaError_t batch_enqueue_raw(int cfg, int smem, int grid, int* err, int nimg, int ntiles,
+                              const BatchImage* d_imgs, const CUtensorMap* d_maps, int* d_counter,
+                              cudaStream_t stream) {
+  BatchKernelFn k = batch_kernel_for(cfg);
+  if (!k || grid < 1 || !err) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, stream>>>(d_imgs, d_maps, nimg, ntiles, d_counter, err);
+  return cudaGetLastError();
+}
+
 int batch_take_device_error() {
   int v = 0, z = 0;
   if (cudaMemcpyFromSymbol(&v, g_batch_err, sizeof(int)) != cudaSuccess) return -1;

@@ -40,6 +40,11 @@ cudaError_t batch_configure(BatchHost* h);
 cudaError_t batch_enqueue(const BatchHost& h, const BatchImage* d_imgs, const CUtensorMap* d_maps,
                           int* d_counter, cudaStream_t stream);
 int batch_take_device_error();
+// Enqueues the counter reset and the persistent kernel for records already in
+// device memory (no host-side containers involved).
+cudaError_t batch_enqueue_raw(int cfg, int smem, int grid, int* err, int nimg, int ntiles,
+                              const BatchImage* d_imgs, const CUtensorMap* d_maps, int* d_counter,
+                              cudaStream_t stream);
 
 // Shared with the single-image launcher: kernel arguments and tensor maps of
 // one image for tile shape TX x TY.

@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "morph.h")
 MORPH_OK = 0
 MORPH_U8, MORPH_U16 = 0, 1
 MORPH_ERODE, MORPH_DILATE = 0, 1
+MORPH_NOALLOC_MAX_IMAGES = 256
 
 
 class MorphError(RuntimeError):
@@ -63,6 +64,7 @@ _SIGS = {
     "morph_apply_host": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_release_staging": [],
     "morph_batch": [ctypes.POINTER(MorphDesc), _i32, _vp],
+    "morph_batch_noalloc": [ctypes.POINTER(MorphDesc), _i32, _vp],
     "morph_batch_plan_create": [ctypes.POINTER(MorphDesc), _i32, ctypes.POINTER(_vp)],
     "morph_batch_plan_launch": [_vp, _vp],
     "morph_batch_plan_destroy": [_vp],
@@ -140,6 +142,10 @@ def morph_release_staging():
 
 def morph_batch(descs, n, stream=0):
     return _lib.morph_batch(descs, n, stream)
+
+
+def morph_batch_noalloc(descs, n, stream=0):
+    return _lib.morph_batch_noalloc(descs, n, stream)
 
 
 def morph_batch_plan_create(descs, n, plan_out):
