@@ -37,7 +37,9 @@
  *    that neighbouring tiles write.
  *  - wx, wy >= 1; 0 <= anchor < w.  A window may be larger than the image
  *    (the window is clipped to the image).
- *  - The fused single-image path allocates no device memory.
+ *  - Single-image calls allocate nothing, except the two-launch form of very
+ *    large 2-D windows (see morph_set_split), which takes its intermediate
+ *    image from the stream-ordered allocator.
  */
 #ifndef MORPH_H
 #define MORPH_H
@@ -205,6 +207,17 @@ int morph_autotune(const char *cache_path);
  */
 int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg);
 int morph_reset_tuning(void);
+
+/*
+ * Form of single-image calls with a 2-D window (section 5: the element is
+ * separable, so erosion by wx x wy is erosion by 1 x wy followed by wx x 1).
+ * mode -1 (default): run both passes fused in one kernel unless the fused
+ * tile is so large that only one CTA fits on an SM, then run them as two
+ * launches through an intermediate image the library allocates
+ * stream-ordered; 0: always fused; 1: always two launches.  The result never
+ * changes.
+ */
+int morph_set_split(int mode);
 
 /* Text for a morph_status value (static storage). */
 const char *morph_status_string(int status);

@@ -70,8 +70,31 @@ int run_single(const void* src, size_t sp, void* dst, size_t dp, int W, int H, i
   L.H = H;
   clip_window(W, wx, ax, &L.wx, &L.ax);
   clip_window(H, wy, ay, &L.wy, &L.ay);
-  if (!plan_single(&L)) return MORPH_ERR_WINDOW;
-  return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+  if (!plan_split(L)) {
+    if (!plan_single(&L)) return MORPH_ERR_WINDOW;
+    return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+  }
+  // Split form (section 5's separability): the 1 x wy pass into an
+  // intermediate image, then the wx x 1 pass from it.  The intermediate is a
+  // stream-ordered allocation (16-byte rows, so both launches can use TMA).
+  const size_t tp = (static_cast<size_t>(W) * L.esz + 15) / 16 * 16;
+  void* tmp = nullptr;
+  if (cudaMallocAsync(&tmp, tp * static_cast<size_t>(H), stream) != cudaSuccess) return MORPH_ERR_NOMEM;
+  FusedLaunch A = L, B = L;
+  A.wx = 1;
+  A.ax = 0;
+  A.dst = tmp;
+  A.dp = static_cast<long long>(tp);
+  B.wy = 1;
+  B.ay = 0;
+  B.src = tmp;
+  B.sp = static_cast<long long>(tp);
+  rc = MORPH_OK;
+  if (!plan_single(&A) || !plan_single(&B)) rc = MORPH_ERR_WINDOW;
+  if (rc == MORPH_OK && fused_launch(A, stream) != cudaSuccess) rc = MORPH_ERR_CUDA;
+  if (rc == MORPH_OK && fused_launch(B, stream) != cudaSuccess) rc = MORPH_ERR_CUDA;
+  cudaFreeAsync(tmp, stream);
+  return rc;
 }
 
 // Device staging buffers of morph_apply_host: one input/output pair per
@@ -347,6 +370,12 @@ int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg) {
   if (cross_row >= 0) t.cross_row[esz - 1] = cross_row;
   if (cross_col >= 0) t.cross_col[esz - 1] = cross_col;
   if (tile_cfg >= -1) t.forced_cfg[esz - 1] = tile_cfg;
+  return MORPH_OK;
+}
+
+int morph_set_split(int mode) {
+  if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
+  tuning().split_mode = mode;
   return MORPH_OK;
 }
 

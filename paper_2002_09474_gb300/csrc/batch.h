@@ -50,7 +50,5 @@ cudaError_t batch_enqueue_raw(int cfg, int smem, int grid, int* err, int nimg, i
 // one image for tile shape TX x TY.
 void fill_img_args(const FusedLaunch& L, const Geom& g, int TX, int TY, ImgArgs* a, CUtensorMap* tin,
                    CUtensorMap* tout);
-// The planner's cost estimate of one launch configuration.
-double tile_cost(const FusedLaunch& L, int cfg);
 
 }  // namespace morph

@@ -92,6 +92,7 @@ void fill_img_args(const FusedLaunch& L, const Geom& g, int TX, int TY, ImgArgs*
   a.err = fused_err_ptr();
   a.ld_vec = (reinterpret_cast<uintptr_t>(L.src) % 4 == 0) && (L.sp % 4 == 0);
   a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % 4 == 0) && (L.dp % 4 == 0);
+  a.st_vec16 = (reinterpret_cast<uintptr_t>(L.dst) % 16 == 0) && (L.dp % 16 == 0);
   memset(tin, 0, sizeof(*tin));
   memset(tout, 0, sizeof(*tout));
   a.tma_ld = encode_tensor_map_2d(tin, L.src, L.esz, L.W, L.H, L.sp, 128 / L.esz, g.bh) ? 1 : 0;

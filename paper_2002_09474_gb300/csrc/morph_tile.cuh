@@ -103,6 +103,7 @@ struct ImgArgs {
   int tma_st;          // 1: S2 leaves by TMA through the output tensor map
   int ld_vec;          // 1: src rows allow aligned 32-bit loads
   int st_vec;          // 1: dst rows allow aligned 32-bit stores
+  int st_vec16;        // 1: dst rows allow aligned 16-byte stores
   int* err;            // device error word (set when a bounded wait gives up)
 };
 
@@ -553,22 +554,33 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     __syncthreads();
   } else {
     __syncthreads();
-    constexpr int NW = TX * E / 4;  // 32-bit words per output row
-    for (int it = tid; it < TY * NW; it += kThreads) {
-      const int xw = it % NW, s = it / NW;
+    // 16-byte vectors where the row allows, 32-bit words or pixels at the edge
+    constexpr int NV = TX * E / 16;  // 16-byte vectors per output row
+    constexpr int VPX = 16 / E;      // pixels per vector
+    for (int it = tid; it < TY * NV; it += kThreads) {
+      const int xv = it % NV, s = it / NV;
       const int y = y0 + s;
-      const int x = x0 + xw * PPW;
+      const int x = x0 + xv * VPX;
       if (y >= a.H || x >= a.W) continue;
-      const int byte = xw * 4;
-      const uint32_t v =
-          *reinterpret_cast<const uint32_t*>(s2 + (byte / SBOX) * (TY * SBOX) + s * SBOX + byte % SBOX);
+      const int byte = xv * 16;
+      const uint8_t* sp = s2 + (byte / SBOX) * (TY * SBOX) + s * SBOX + byte % SBOX;
       uint8_t* row = a.dst + static_cast<long long>(y) * a.dp;
-      if (a.st_vec && x + PPW <= a.W) {
-        *reinterpret_cast<uint32_t*>(row + static_cast<long long>(x) * E) = v;
-      } else {
+      if (a.st_vec16 && x + VPX <= a.W) {
+        *reinterpret_cast<uint4*>(row + static_cast<long long>(x) * E) = *reinterpret_cast<const uint4*>(sp);
+        continue;
+      }
 #pragma unroll
-        for (int t = 0; t < PPW; ++t)
-          if (x + t < a.W) reinterpret_cast<T*>(row)[x + t] = static_cast<T>(v >> (8 * E * t));
+      for (int q = 0; q < 4; ++q) {
+        const int xq = x + q * PPW;
+        if (xq >= a.W) break;
+        const uint32_t v = reinterpret_cast<const uint32_t*>(sp)[q];
+        if (a.st_vec && xq + PPW <= a.W) {
+          *reinterpret_cast<uint32_t*>(row + static_cast<long long>(xq) * E) = v;
+        } else {
+#pragma unroll
+          for (int t = 0; t < PPW; ++t)
+            if (xq + t < a.W) reinterpret_cast<T*>(row)[xq + t] = static_cast<T>(v >> (8 * E * t));
+        }
       }
     }
     __syncthreads();

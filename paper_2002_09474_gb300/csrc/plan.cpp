@@ -15,6 +15,8 @@ bool g_init = false;
 // of a tile costs (rounds of 128 threads over its work items) x (work per
 // item); tiles run in waves of (152 SMs x CTAs per SM).  Only used to rank
 // tile shapes; the autotuner measures the classes it is asked about.
+int ctas_per_sm(int smem_bytes);
+
 double tile_cost(const FusedLaunch& L, int cfg) {
   const int TX = tile_tx(cfg), TY = tile_ty(cfg);
   const Geom g = make_geom(L.esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
@@ -37,15 +39,32 @@ double tile_cost(const FusedLaunch& L, int cfg) {
     else
       t += rounds(nxo * ntc) * ((8.0 + L.wx) * 1.2 + 8.0);
   }
-  int per_sm = 232448 / (g.smem_bytes + 1024);
-  if (per_sm > 4) per_sm = 4;
-  if (per_sm < 1) per_sm = 1;
+  const int per_sm = ctas_per_sm(g.smem_bytes);
   const double ntiles = std::ceil(static_cast<double>(L.W) / TX) * std::ceil(static_cast<double>(L.H) / TY);
   const double slots = 152.0 * per_sm;
   const double waves = std::ceil(ntiles / slots);
-  // CTAs sharing an SM hide each other's latency but share its issue slots
-  const double share = per_sm >= 3 ? 0.55 : per_sm == 2 ? 0.7 : 1.0;
-  return waves * t * (ntiles < slots ? 1.0 : share * per_sm) / per_sm * 4.0;
+  // A CTA is 4 warps: with fewer than 3 CTAs on an SM its barriers and loads
+  // leave the issue slots idle (measured: 1 CTA/SM ran at 6% active warps).
+  const double occ = per_sm >= 3 ? 1.0 : per_sm == 2 ? 1.35 : 2.2;
+  return waves * t * occ * (ntiles < slots ? 1.0 : per_sm) / per_sm;
+}
+
+int ctas_per_sm(int smem_bytes) {
+  int per_sm = 232448 / (smem_bytes + 1024);  // shared memory per SM / per CTA
+  if (per_sm > 4) per_sm = 4;                 // registers: 4 CTAs of 128 threads
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+bool plan_split(const FusedLaunch& L) {
+  const Tuning& t = tuning();
+  if (L.wx <= 1 || L.wy <= 1) return false;
+  if (t.split_mode == 0) return false;
+  if (t.split_mode == 1) return true;
+  // auto: split when the fused tile the planner picks (or every fused tile)
+  // would run fewer than 3 CTAs per SM
+  FusedLaunch F = L;
+  if (!plan_single(&F)) return true;
+  return ctas_per_sm(fused_smem_bytes(F)) < 3;
 }
 
 void reset_tuning_defaults() {
@@ -54,6 +73,7 @@ void reset_tuning_defaults() {
     g_tuning.cross_row[e] = 9;
     g_tuning.forced_cfg[e] = -1;
   }
+  g_tuning.split_mode = -1;
   g_tuning.from_autotune = 0;
   g_init = true;
 }

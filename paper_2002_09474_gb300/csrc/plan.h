@@ -12,6 +12,7 @@ struct Tuning {
   int cross_col[2];  // [esz-1]: pass along y uses the direct method iff wy <= cross_col
   int cross_row[2];  // [esz-1]: pass along x uses the direct method iff wx <= cross_row
   int forced_cfg[2];              // [esz-1]: tile configuration to use when it fits (-1: cost model)
+  int split_mode;                 // 2-D windows as two 1-D launches: -1 auto, 0 never, 1 always
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 
@@ -21,5 +22,12 @@ void reset_tuning_defaults();
 // Fills L->vhgw_col, L->vhgw_row and L->cfg; false if no tile configuration
 // fits the window in shared memory.
 bool plan_single(FusedLaunch* L);
+
+// Whether a 2-D window runs as a 1 x wy launch into an intermediate image and
+// a wx x 1 launch from it (auto: when the fused tile would run one CTA per
+// SM).  Estimated cost of one tile configuration, CTAs per SM for a size.
+bool plan_split(const FusedLaunch& L);
+double tile_cost(const FusedLaunch& L, int cfg);
+int ctas_per_sm(int smem_bytes);
 
 }  // namespace morph

@@ -330,6 +330,7 @@ int main() {
     a.blk_x = L.vhgw_row && L.wx > 1;
     a.ld_vec = (reinterpret_cast<uintptr_t>(src) % 4 == 0) && (sp % 4 == 0);
     a.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
+    a.st_vec16 = (reinterpret_cast<uintptr_t>(dst) % 16 == 0) && (dp % 16 == 0);
     int errword = 0;
     a.err = &errword;
     // the launcher's TMA decisions (same rules as encode_tensor_map_2d)

@@ -177,3 +177,25 @@ def test_constant_and_extreme_values(lib):
             img = np.full((40, 50), v, dtype)
             for op in ("erode", "dilate"):
                 assert np.array_equal(run(lib, torch, img, 5, 7, 2, 3, op), img)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_fused_and_two_launch_forms_agree(lib, dtype):
+    """Section 5's separability through the two-launch form (1 x wy into an
+    intermediate image, then wx x 1) and through the fused kernel."""
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    g = synth.rng(160)
+    try:
+        for (h, w) in ((1, 1), (37, 300), (257, 129), (200, 513)):
+            img = synth.uniform_image(w, h, dtype, gen=g)
+            for (wx, wy, ax, ay) in ((2, 2, 0, 1), (9, 17, 4, 8), (127, 127, 63, 63), (40, 3, 39, 0)):
+                want = {op: oracle.morph(img, wx, wy, ax, ay, op) for op in ("erode", "dilate")}
+                for mode in (0, 1):
+                    assert lib.morph_set_split(mode) == 0
+                    for op in ("erode", "dilate"):
+                        for pad in (0, aligned_pad(w, dtype)):
+                            got = run(lib, torch, img, wx, wy, ax, ay, op, pad=pad, dst_pad=pad)
+                            assert np.array_equal(got, want[op]), (h, w, wx, wy, mode, op, pad)
+    finally:
+        lib.morph_set_split(-1)
