@@ -17,6 +17,10 @@ Reported (one JSON line on rank 0):
                (host->device and device->host copies inside the timed region)
   cpu_baseline the brute-force CPU oracle on a bounded sample of the step
   breakdown    per (dtype, window) class: mean us per call, Gpixel/s, GB/s
+  batched      2000 uneven u8 images (sides 64..2048, windows 1..63): images/s
+               of one CUDA-graph persistent launch vs 2000 per-image calls
+  serving      Poisson request stream through the continuous-batching server
+               (4 GB admission budget): p50/p99 latency and throughput
 ``--impl reference`` times the CPU oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -222,6 +226,106 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def measure_batched(torch, morph, reps: int = 5) -> dict:
+    """2000 uneven u8 images: one CUDA-graph persistent launch against 2000
+    per-image morph_apply calls on one stream (inputs 2.2 GB, larger than L2).
+    Identical output is checked on every image before timing."""
+    import ctypes
+    specs = synth.batch_specs(2000, seed=5)
+    pix = synth.batch_pixels(specs, seed=5)
+    srcs = [torch.from_numpy(p).cuda() for p in pix]
+    outs = [torch.empty_like(s) for s in srcs]
+    alone = [torch.empty_like(s) for s in srcs]
+    del pix
+    arr = (morph.MorphDesc * len(specs))()
+    for d, s, o, sp in zip(arr, srcs, outs, specs):
+        d.src, d.dst, d.width, d.height = s.data_ptr(), o.data_ptr(), sp.width, sp.height
+        d.src_pitch = d.dst_pitch = sp.width
+        d.wx, d.wy, d.anchor_x, d.anchor_y, d.op = sp.wx, sp.wy, sp.ax, sp.ay, sp.op
+        d.dtype = morph.MORPH_U8
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    plan = ctypes.c_void_p()
+    rc = morph.morph_batch_plan_create(arr, len(specs), ctypes.byref(plan))
+    if rc != 0:
+        raise morph.MorphError("morph_batch_plan_create", rc)
+
+    def per_image():
+        for s, a, sp in zip(srcs, alone, specs):
+            rc = morph.morph_apply(s.data_ptr(), sp.width, a.data_ptr(), sp.width, sp.width, sp.height,
+                                   morph.MORPH_U8, sp.op, sp.wx, sp.wy, sp.ax, sp.ay, sh)
+            if rc != 0:
+                raise morph.MorphError("morph_apply", rc)
+
+    def graph():
+        rc = morph.morph_batch_plan_launch(plan, sh)
+        if rc != 0:
+            raise morph.MorphError("morph_batch_plan_launch", rc)
+
+    def batch_call():
+        rc = morph.morph_batch(arr, len(specs), sh)
+        if rc != 0:
+            raise morph.MorphError("morph_batch", rc)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    try:
+        graph()
+        per_image()
+        torch.cuda.synchronize()
+        same = all(torch.equal(o, a) for o, a in zip(outs, alone))
+        t_img = timed(per_image)
+        t_graph = timed(graph)
+        t_batch = timed(batch_call)
+    finally:
+        morph.morph_batch_plan_destroy(plan)
+    morph.check_device_error()
+    n = len(specs)
+    px = sum(sp.width * sp.height for sp in specs)
+    return {"workload": "2000 u8 images, sides uniform 64..2048, windows uniform 1..63, "
+                        "random erode/dilate (seed 5)",
+            "pixels": px, "identical_to_per_image": bool(same),
+            "graph_images_s": round(n / (t_graph * 1e-3), 1),
+            "per_image_images_s": round(n / (t_img * 1e-3), 1),
+            "morph_batch_images_s": round(n / (t_batch * 1e-3), 1),
+            "graph_gpix_s": round(px / (t_graph * 1e-3) / 1e9, 2),
+            "per_image_gpix_s": round(px / (t_img * 1e-3) / 1e9, 2),
+            "graph_vs_per_image": round(t_img / t_graph, 3),
+            "ms": {"graph": round(t_graph, 3), "per_image": round(t_img, 3), "morph_batch": round(t_batch, 3)}}
+
+
+def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0) -> list:
+    """Poisson request streams through the continuous-batching server, 4 GB
+    admission budget, inputs pre-staged in device memory (host-to-device
+    copies excluded).  A short run at the same rate warms the pools first."""
+    from paper_2002_09474_gb300 import serve
+    pool_img, pool_dev = serve.source_pool(torch, seed=6)
+    ex = serve.GpuExecutor(n_streams=4)
+    out = []
+    for rate in rates:
+        warm = serve.make_requests(rate, min(0.5, duration_s), pool_img, pool_dev, seed=60)
+        serve.Server(ex, budget_bytes=4 << 30).run(warm, timeout_s=300)
+        rs = serve.make_requests(rate, duration_s, pool_img, pool_dev, seed=6)
+        st = serve.Server(ex, budget_bytes=4 << 30).run(rs, timeout_s=300)
+        torch.cuda.synchronize()
+        d = st.summary()
+        d.update({"rate_req_s": rate, "duration_s": duration_s, "requests": len(rs),
+                  "p50_ms": round(d["p50_ms"], 3), "p99_ms": round(d["p99_ms"], 3),
+                  "throughput_req_s": round(d["throughput_req_s"], 1), "gpix_s": round(d["gpix_s"], 2)})
+        out.append(d)
+    return out
+
+
 def reduce_over_ranks(torch, dist, value: float, op: str) -> float:
     """max or sum of a float over all ranks (identity without a process group)."""
     if dist is None or not dist.is_initialized():
@@ -356,6 +460,12 @@ def run_gpu(args):
     morph.morph_release_staging()
     morph.check_device_error()
 
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = measure_batched(torch, morph)
+        extras["serving"] = measure_serving(torch, rates=args.serving_rates,
+                                            duration_s=args.serving_seconds)
+
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -373,6 +483,7 @@ def run_gpu(args):
                 "gpu_launches": len(runs) * args.steps,
                 "clocks": clk,
                 "breakdown": breakdown}
+        line.update(extras)
         if not args.no_cpu_baseline:
             v, cores, spent, desc = oracle_sample(host_imgs)
             line["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": cores,
@@ -391,6 +502,12 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the CPU oracle sample (for profiler runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and serving measurements (for profiler runs)")
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[5000.0],
+                    help="request rates of the serving measurement (req/s)")
+    ap.add_argument("--serving-seconds", type=float, default=3.0,
+                    help="length of each serving run after warm-up")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

@@ -1,0 +1,271 @@
+"""Continuous-batching request loop for erosion/dilation requests.
+
+Requests (an image, a window, an anchor, an operation) arrive over time.  The
+loop admits waiting requests in arrival order while a device-memory budget
+allows their input and output bytes, groups the newly admitted ones into a
+micro-batch that runs as ONE persistent kernel launch (morph_batch), and puts
+consecutive micro-batches on different CUDA streams, so requests that arrive
+while others are on the GPU start without waiting for them.  Completions are
+found by polling CUDA events; a completed request frees its budget and its
+output buffer goes back to a pool for reuse.  Latency is arrival to
+completion.
+
+Inputs are pre-staged in device memory (requests point into a resident
+source pool), so host-to-device copies are not part of the latency; the
+budget still charges each request its input bytes as if staged.
+
+The scheduling logic is independent of CUDA: it talks to an executor
+(``GpuExecutor`` here; tests use a host-only fake).
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class ServeRequest:
+    rid: int
+    arrival_s: float
+    width: int
+    height: int
+    wx: int
+    wy: int
+    ax: int
+    ay: int
+    op: int
+    dtype_size: int = 1           # bytes per pixel (1: u8, 2: u16)
+    src: object = None            # executor-specific input handle (pre-staged)
+    origin: tuple = (0, 0)        # (x0, y0) of the input in its source pool
+    # filled by the server
+    admitted_s: float = -1.0
+    done_s: float = -1.0
+    out: object = None
+
+    @property
+    def nbytes(self) -> int:
+        """Input plus output image bytes (the default budget charge)."""
+        return 2 * self.width * self.height * self.dtype_size
+
+
+@dataclass
+class ServeStats:
+    completed: int = 0
+    rejected: int = 0
+    pixels: int = 0
+    wall_s: float = 0.0
+    latencies_ms: list = field(default_factory=list)
+    max_budget_used: int = 0
+    batches: int = 0
+    max_in_flight: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        return {"completed": self.completed, "rejected": self.rejected,
+                "throughput_req_s": self.completed / self.wall_s if self.wall_s else 0.0,
+                "gpix_s": self.pixels / self.wall_s / 1e9 if self.wall_s else 0.0,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_budget_used_bytes": self.max_budget_used, "batches": self.batches,
+                "max_batches_in_flight": self.max_in_flight}
+
+
+class Budget:
+    """Device-byte accounting for admission."""
+
+    def __init__(self, limit: int):
+        self.limit = int(limit)
+        self.used = 0
+
+    def try_take(self, n: int) -> bool:
+        if self.used + n > self.limit:
+            return False
+        self.used += n
+        return True
+
+    def give(self, n: int) -> None:
+        self.used -= n
+        assert self.used >= 0
+
+
+class Server:
+    """The scheduling loop.  ``executor`` provides: ``n_streams``;
+    ``alloc_out(req)`` -> output handle; ``launch(reqs, stream_index)`` ->
+    completion token; ``done(token)`` -> bool (non-blocking);
+    ``finish(req)``, called once per completed request (releases its output);
+    ``idle_wait()``, a short pause while work is in flight."""
+
+    def __init__(self, executor, budget_bytes: int = 4 << 30, max_batch: int = 128,
+                 max_in_flight: int = 8):
+        self.ex = executor
+        # bytes a request holds while admitted (executor's own rule if it has one)
+        self.charge = getattr(executor, "charge", lambda r: r.nbytes)
+        self.budget = Budget(budget_bytes)
+        self.max_batch = max_batch
+        self.max_in_flight = max_in_flight
+
+    def run(self, requests: list[ServeRequest], timeout_s: float = 600.0,
+            clock=time.perf_counter) -> ServeStats:
+        st = ServeStats()
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival_s))
+        waiting: collections.deque = collections.deque()
+        in_flight: list = []  # (token, reqs)
+        next_stream = 0
+        t0 = clock()
+        while pending or waiting or in_flight:
+            now = clock() - t0
+            if now > timeout_s:
+                raise TimeoutError("serving loop did not drain within %.0f s" % timeout_s)
+            while pending and pending[0].arrival_s <= now:
+                r = pending.popleft()
+                if self.charge(r) > self.budget.limit:  # can never fit: reject now
+                    st.rejected += 1
+                    continue
+                waiting.append(r)
+            # retire completed batches first: they free budget for admission
+            still = []
+            for token, reqs in in_flight:
+                if self.ex.done(token):
+                    tdone = clock() - t0
+                    for r in reqs:
+                        r.done_s = tdone
+                        st.latencies_ms.append((tdone - r.arrival_s) * 1e3)
+                        st.completed += 1
+                        st.pixels += r.width * r.height
+                        self.budget.give(self.charge(r))
+                        self.ex.finish(r)
+                else:
+                    still.append((token, reqs))
+            in_flight = still
+            # admit in arrival order while the budget allows
+            batch = []
+            if len(in_flight) < self.max_in_flight:
+                while waiting and len(batch) < self.max_batch and self.budget.try_take(self.charge(waiting[0])):
+                    r = waiting.popleft()
+                    r.admitted_s = now
+                    r.out = self.ex.alloc_out(r)
+                    batch.append(r)
+                st.max_budget_used = max(st.max_budget_used, self.budget.used)
+            if batch:
+                token = self.ex.launch(batch, next_stream)
+                next_stream = (next_stream + 1) % self.ex.n_streams
+                in_flight.append((token, batch))
+                st.batches += 1
+                st.max_in_flight = max(st.max_in_flight, len(in_flight))
+            elif in_flight or (waiting and not pending):
+                self.ex.idle_wait()
+            elif pending:
+                # nothing to do until the next arrival
+                dt = pending[0].arrival_s - (clock() - t0)
+                if dt > 0:
+                    time.sleep(min(dt, 0.0005))
+        st.wall_s = clock() - t0
+        return st
+
+
+class GpuExecutor:
+    """Runs micro-batches with morph_batch on ``n_streams`` CUDA streams.
+    Output buffers come from a pool of flat device buffers in power-of-two
+    size classes, so a warm server allocates nothing; the pool keeps at most
+    ``pool_cap`` idle bytes."""
+
+    def __init__(self, device="cuda", n_streams: int = 4, pool_cap: int = 4 << 30):
+        import torch
+
+        from paper_2002_09474_gb300 import morph
+        self.torch = torch
+        self.morph = morph
+        self.device = torch.device(device)
+        self.n_streams = n_streams
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_streams)]
+        self.free: dict = collections.defaultdict(list)
+        self.pool_cap = pool_cap
+        self.pooled = 0
+        self.keep = None  # when a dict, finish() stores a copy of every result by rid
+
+    @staticmethod
+    def size_class(nbytes: int) -> int:
+        return max(1 << 16, 1 << (int(nbytes) - 1).bit_length())
+
+    def charge(self, r: ServeRequest) -> int:
+        """Input bytes plus the output buffer's size class."""
+        n = r.width * r.height * r.dtype_size
+        return n + self.size_class(n)
+
+    def alloc_out(self, r: ServeRequest):
+        n = r.width * r.height * r.dtype_size
+        c = self.size_class(n)
+        if self.free[c]:
+            buf = self.free[c].pop()
+            self.pooled -= c
+        else:
+            buf = self.torch.empty(c, dtype=self.torch.uint8, device=self.device)
+        v = buf[:n]
+        if r.dtype_size == 2:
+            v = v.view(self.torch.uint16)
+        return v.view(r.height, r.width), buf
+
+    def finish(self, r: ServeRequest) -> None:
+        out, buf = r.out
+        if self.keep is not None:
+            self.keep[r.rid] = out.clone()
+        c = buf.numel()
+        if self.pooled + c <= self.pool_cap:
+            self.free[c].append(buf)
+            self.pooled += c
+        r.out = None
+
+    def launch(self, reqs, stream_index: int):
+        m = self.morph
+        descs = (m.MorphDesc * len(reqs))()
+        for d, r in zip(descs, reqs):
+            src, out = r.src, r.out[0]
+            d.src, d.dst = src.data_ptr(), out.data_ptr()
+            d.width, d.height = r.width, r.height
+            d.src_pitch = src.stride(0) * src.element_size()
+            d.dst_pitch = out.stride(0) * out.element_size()
+            d.wx, d.wy, d.anchor_x, d.anchor_y = r.wx, r.wy, r.ax, r.ay
+            d.op = r.op
+            d.dtype = m.MORPH_U8 if r.dtype_size == 1 else m.MORPH_U16
+        s = self.streams[stream_index]
+        rc = m.morph_batch(descs, len(reqs), s.cuda_stream)
+        if rc != 0:
+            raise m.MorphError("morph_batch", rc)
+        ev = self.torch.cuda.Event()
+        ev.record(s)
+        return ev
+
+    def done(self, ev) -> bool:
+        return ev.query()
+
+    def idle_wait(self) -> None:
+        time.sleep(0.00005)
+
+
+def source_pool(torch, width: int = 4096, height: int = 4096, seed: int = 6, device="cuda"):
+    """A resident uniform u8 image that requests take windows of (pre-staged
+    inputs)."""
+    from paper_2002_09474_gb300 import synth
+    img = synth.uniform_image(width, height, np.uint8, seed=seed)
+    return img, torch.from_numpy(img).to(device)
+
+
+def make_requests(rate_per_s: float, duration_s: float, pool_img, pool_dev, seed: int = 6,
+                  area_hi: int = 4096 * 4096) -> list[ServeRequest]:
+    """The serving workload: Poisson arrivals, log-uniform areas and aspect
+    ratios, windows 1..101, mixed ops; each request's input is a window of
+    the resident source pool at a seeded offset."""
+    from paper_2002_09474_gb300 import synth
+    specs = synth.serving_requests(rate_per_s, duration_s, seed=seed, area_hi=area_hi)
+    g = synth.rng(seed + 77)
+    H, W = pool_img.shape
+    out = []
+    for i, s in enumerate(specs):
+        w, h = min(s.width, W), min(s.height, H)
+        x0 = int(g.integers(0, W - w + 1))
+        y0 = int(g.integers(0, H - h + 1))
+        out.append(ServeRequest(i, s.arrival_s, w, h, s.wx, s.wy, s.ax, s.ay, s.op, 1,
+                                src=pool_dev[y0:y0 + h, x0:x0 + w], origin=(x0, y0)))
+    return out

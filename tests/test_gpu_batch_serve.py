@@ -1,0 +1,118 @@
+"""The batched and served forms at their full workload sizes: 2000 uneven
+images in one CUDA-graph launch, and a Poisson request stream through the
+continuous-batching server.  Each result must equal the same image filtered
+alone (one morph_apply call), and a seeded sample is checked against the
+oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_09474_gb300 import synth
+
+from gpu_util import need_cuda
+
+pytestmark = pytest.mark.gpu
+OPS = ("erode", "dilate")
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_cuda()
+    from paper_2002_09474_gb300 import morph
+    morph.morph_reset_tuning()
+    return torch, morph
+
+
+def check_sample(img, got, wx, wy, ax, ay, op, seed):
+    np.testing.assert_array_equal(got, oracle.sep_vhgw(img, wx, wy, ax, ay, OPS[op]))
+    g = synth.rng(seed)
+    h, w = img.shape
+    xs = np.concatenate([g.integers(0, w, 200), [0, w - 1]]).astype(np.int32)
+    ys = np.concatenate([g.integers(0, h, 200), [h - 1, 0]]).astype(np.int32)
+    np.testing.assert_array_equal(got[ys, xs], oracle.morph_points(img, wx, wy, ax, ay, OPS[op], xs, ys))
+
+
+def test_batch_2000_images_graph_plan(env):
+    torch, morph = env
+    specs = synth.batch_specs(2000, seed=5)
+    pix = synth.batch_pixels(specs, seed=5)
+    srcs = [torch.from_numpy(p).cuda() for p in pix]
+    outs = [torch.full_like(s, 0x5A) for s in srcs]
+    arr = (morph.MorphDesc * len(specs))()
+    for d, s, o, sp in zip(arr, srcs, outs, specs):
+        d.src, d.dst, d.width, d.height = s.data_ptr(), o.data_ptr(), sp.width, sp.height
+        d.src_pitch = d.dst_pitch = sp.width
+        d.wx, d.wy, d.anchor_x, d.anchor_y, d.op = sp.wx, sp.wy, sp.ax, sp.ay, sp.op
+        d.dtype = morph.MORPH_U8
+    plan = ctypes.c_void_p()
+    rc = morph.morph_batch_plan_create(arr, len(specs), ctypes.byref(plan))
+    assert rc == 0, morph.status_string(rc)
+    try:
+        for rep in range(2):  # the graph replays to the same result
+            rc = morph.morph_batch_plan_launch(plan, 0)
+            assert rc == 0, morph.status_string(rc)
+            torch.cuda.synchronize()
+            assert morph.morph_device_error() == 0
+            alone = torch.empty(2048 * 2048, dtype=torch.uint8, device="cuda")
+            for i, (s, o, sp) in enumerate(zip(srcs, outs, specs)):
+                a = alone[:sp.width * sp.height].view(sp.height, sp.width)
+                morph.apply(s, a, sp.wx, sp.wy, sp.ax, sp.ay, op=sp.op)
+                assert torch.equal(a, o), (i, sp)
+            for o in outs:
+                o.fill_(0x5A)
+    finally:
+        assert morph.morph_batch_plan_destroy(plan) == 0
+    # a seeded sample of 64 images against the oracle (after one more replay)
+    assert morph.morph_batch(arr, len(specs), 0) == 0
+    torch.cuda.synchronize()
+    for i in synth.rng(55).choice(len(specs), 64, replace=False):
+        sp = specs[i]
+        check_sample(pix[i], outs[i].cpu().numpy(), sp.wx, sp.wy, sp.ax, sp.ay, sp.op, 500 + int(i))
+
+
+def test_serving_results_equal_alone(env):
+    """Poisson stream at 5k req/s, full area range, 4 GB budget: every
+    request's result equals the same request run alone, and a sample equals
+    the oracle."""
+    torch, morph = env
+    from paper_2002_09474_gb300 import serve
+    pool_img, pool_dev = serve.source_pool(torch, seed=6)
+    rs = serve.make_requests(5000.0, 0.12, pool_img, pool_dev, seed=6)
+    assert len(rs) > 300
+    ex = serve.GpuExecutor(n_streams=4)
+    ex.keep = {}
+    st = serve.Server(ex, budget_bytes=4 << 30).run(rs, timeout_s=120)
+    torch.cuda.synchronize()
+    assert morph.morph_device_error() == 0
+    assert st.completed == len(rs) and st.rejected == 0 and st.batches > 1
+    assert st.max_budget_used <= 4 << 30
+    for r in rs:
+        alone = torch.empty((r.height, r.width), dtype=torch.uint8, device="cuda")
+        morph.apply(r.src, alone, r.wx, r.wy, r.ax, r.ay, op=r.op)
+        assert torch.equal(alone, ex.keep[r.rid]), r
+    for i in synth.rng(66).choice(len(rs), 24, replace=False):
+        r = rs[int(i)]
+        x0, y0 = r.origin
+        img = pool_img[y0:y0 + r.height, x0:x0 + r.width]
+        check_sample(img, ex.keep[r.rid].cpu().numpy(), r.wx, r.wy, r.ax, r.ay, r.op, 700 + int(i))
+
+
+def test_serving_budget_binds(env):
+    """A budget that holds only a few requests still drains the stream, never
+    holds more than it allows, and gives the same results."""
+    torch, morph = env
+    from paper_2002_09474_gb300 import serve
+    pool_img, pool_dev = serve.source_pool(torch, seed=7)
+    rs = serve.make_requests(20000.0, 0.01, pool_img, pool_dev, seed=7, area_hi=1024 * 1024)
+    ex = serve.GpuExecutor(n_streams=2)
+    ex.keep = {}
+    budget = 3 * ex.charge(max(rs, key=ex.charge))
+    st = serve.Server(ex, budget_bytes=budget).run(rs, timeout_s=60)
+    torch.cuda.synchronize()
+    assert st.completed == len(rs) and st.max_budget_used <= budget
+    for r in rs:
+        alone = torch.empty((r.height, r.width), dtype=torch.uint8, device="cuda")
+        morph.apply(r.src, alone, r.wx, r.wy, r.ax, r.ay, op=r.op)
+        assert torch.equal(alone, ex.keep[r.rid]), r
