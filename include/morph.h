@@ -219,6 +219,19 @@ int morph_reset_tuning(void);
  */
 int morph_set_split(int mode);
 
+/*
+ * Launch form of the fused kernel for single-image calls (no counterpart in
+ * the paper: a GPU scheduling choice).  mode 1: a persistent grid (resident
+ * CTAs x SMs) whose CTAs walk the tiles in turn, with two input buffers per
+ * CTA so that the TMA load of a CTA's next tile overlaps the computation of
+ * its current one; 0: one CTA per tile; -1 (default): the persistent form
+ * when the image has at least two tiles per resident CTA and its doubled
+ * input buffer fits in shared memory.  Images whose rows are not 16-byte
+ * aligned always take one CTA per tile.  The result never changes.
+ * Returns MORPH_ERR_ARG for another mode.
+ */
+int morph_set_pipeline(int mode);
+
 /* Text for a morph_status value (static storage). */
 const char *morph_status_string(int status);
 

@@ -379,6 +379,12 @@ int morph_set_split(int mode) {
   return MORPH_OK;
 }
 
+int morph_set_pipeline(int mode) {
+  if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
+  tuning().pipe_mode = mode;
+  return MORPH_OK;
+}
+
 int morph_reset_tuning(void) {
   reset_tuning_defaults();
   return MORPH_OK;

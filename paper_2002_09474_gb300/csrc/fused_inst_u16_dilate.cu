@@ -3,4 +3,5 @@
 
 namespace morph {
 FusedKernelFn fused_kernel_u16_dilate(int cfg) { return pick_fused_kernel<uint16_t, 1>(cfg); }
+FusedPipeKernelFn fused_pipe_kernel_u16_dilate(int cfg) { return pick_fused_pipe_kernel<uint16_t, 1>(cfg); }
 }  // namespace morph

@@ -3,4 +3,5 @@
 
 namespace morph {
 FusedKernelFn fused_kernel_u16_erode(int cfg) { return pick_fused_kernel<uint16_t, 0>(cfg); }
+FusedPipeKernelFn fused_pipe_kernel_u16_erode(int cfg) { return pick_fused_pipe_kernel<uint16_t, 0>(cfg); }
 }  // namespace morph

@@ -3,4 +3,5 @@
 
 namespace morph {
 FusedKernelFn fused_kernel_u8_dilate(int cfg) { return pick_fused_kernel<uint8_t, 1>(cfg); }
+FusedPipeKernelFn fused_pipe_kernel_u8_dilate(int cfg) { return pick_fused_pipe_kernel<uint8_t, 1>(cfg); }
 }  // namespace morph

@@ -22,6 +22,28 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(const __grid_constan
   run_tile<T, OP, TX, TY>(a, &tin, &tout, blockIdx.x * TX, blockIdx.y * TY, g, smem, &bar, phase, a.err);
 }
 
+// Persistent form: a grid of (SMs x resident CTAs) CTAs walks the tiles in
+// row-major order, tile blockIdx.x + i * gridDim.x on iteration i.  Two
+// copies of region A (see make_geom's `pipe` layout) let the TMA load of the
+// next tile run while the current one is computed, and the TMA store of a
+// tile stays in flight until the next tile begins.  Needs a.tma_ld.
+template <typename T, int OP, int TX, int TY>
+__global__ void __launch_bounds__(kThreads, 3) fused_pipe_kernel(const __grid_constant__ CUtensorMap tin,
+                                                                 const __grid_constant__ CUtensorMap tout,
+                                                                 const ImgArgs a, const Geom g, int ntx,
+                                                                 int ntiles) {
+  __shared__ __align__(8) uint64_t bar[2];
+  extern __shared__ __align__(128) uint4 smem[];
+  if (static_cast<int>(blockIdx.x) >= ntiles) return;  // whole CTA
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  run_tiles_pipelined<T, OP, TX, TY>(a, &tin, &tout, g, smem, bar, ntx, ntiles, blockIdx.x, gridDim.x);
+}
+
 template <typename T, int OP>
 FusedKernelFn pick_fused_kernel(int cfg) {
   switch (cfg) {
@@ -33,6 +55,21 @@ FusedKernelFn pick_fused_kernel(int cfg) {
     case kTile128x128: return fused_kernel<T, OP, 128, 128>;
     case kTile256x64: return fused_kernel<T, OP, 256, 64>;
     case kTile32x128: return fused_kernel<T, OP, 32, 128>;
+  }
+  return nullptr;
+}
+
+template <typename T, int OP>
+FusedPipeKernelFn pick_fused_pipe_kernel(int cfg) {
+  switch (cfg) {
+    case kTile128x64: return fused_pipe_kernel<T, OP, 128, 64>;
+    case kTile64x64: return fused_pipe_kernel<T, OP, 64, 64>;
+    case kTile64x128: return fused_pipe_kernel<T, OP, 64, 128>;
+    case kTile256x32: return fused_pipe_kernel<T, OP, 256, 32>;
+    case kTile32x32: return fused_pipe_kernel<T, OP, 32, 32>;
+    case kTile128x128: return fused_pipe_kernel<T, OP, 128, 128>;
+    case kTile256x64: return fused_pipe_kernel<T, OP, 256, 64>;
+    case kTile32x128: return fused_pipe_kernel<T, OP, 32, 128>;
   }
   return nullptr;
 }

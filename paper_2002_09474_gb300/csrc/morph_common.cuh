@@ -158,6 +158,7 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 #else
 // Host stand-ins with the same signatures, defined by the CPU emulator of the
@@ -173,6 +174,7 @@ void prefetch_tensormap(const CUtensorMap* map);
 void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y);
 void bulk_commit();
 void bulk_wait_read_all();
+void bulk_wait_all();
 
 #endif
 

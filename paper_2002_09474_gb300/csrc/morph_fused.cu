@@ -23,6 +23,43 @@ KernelFn kernel_for(int esz, int op, int cfg) {
   return op == 0 ? fused_kernel_u16_erode(cfg) : fused_kernel_u16_dilate(cfg);
 }
 
+FusedPipeKernelFn pipe_kernel_for(int esz, int op, int cfg) {
+  if (cfg < 0 || cfg >= kNumTileCfg) return nullptr;
+  if (esz == 1) return op == 0 ? fused_pipe_kernel_u8_erode(cfg) : fused_pipe_kernel_u8_dilate(cfg);
+  return op == 0 ? fused_pipe_kernel_u16_erode(cfg) : fused_pipe_kernel_u16_dilate(cfg);
+}
+
+// Raises a kernel's dynamic shared-memory limit once per device.
+cudaError_t allow_smem(const void* fn) {
+  static std::mutex mu;
+  static const void* done[64][64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const void** row = done[dev & 63];
+  for (int i = 0; i < 64; ++i) {
+    if (row[i] == fn) return cudaSuccess;
+    if (!row[i]) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
+      if (e == cudaSuccess) row[i] = fn;
+      return e;
+    }
+  }
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
+}
+
+// CTAs of a persistent launch: resident CTAs per SM x SMs, at most one per tile.
+int persistent_grid(const void* fn, int smem, int ntiles) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess) return 0;
+  if (per_sm < 1) return 0;
+  const long long n = static_cast<long long>(sms) * per_sm;
+  return static_cast<int>(n < ntiles ? n : ntiles);
+}
+
 // Address of g_fused_err on the current device (cached per device).
 int* fused_err_ptr() {
   static int* ptrs[64] = {};
@@ -106,26 +143,39 @@ int fused_smem_bytes(const FusedLaunch& L) {
   return make_geom(L.esz, tile_tx(L.cfg), tile_ty(L.cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row).smem_bytes;
 }
 
+int fused_pipe_smem_bytes(const FusedLaunch& L) {
+  if (L.cfg < 0 || L.cfg >= kNumTileCfg) return 0;
+  return make_geom(L.esz, tile_tx(L.cfg), tile_ty(L.cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row, true)
+      .smem_bytes;
+}
+
 cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int TX = tile_tx(L.cfg), TY = tile_ty(L.cfg);
   const Geom g = make_geom(L.esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
   if (g.smem_bytes > kMaxSmemBytes) return cudaErrorInvalidConfiguration;
-  KernelFn k = kernel_for(L.esz, L.op, L.cfg);
-  if (!k) return cudaErrorInvalidValue;
-  static bool opted[64][2][2][kNumTileCfg] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  bool& done = opted[dev & 63][L.esz - 1][L.op][L.cfg];
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
-    if (e != cudaSuccess) return e;
-    done = true;
-  }
   ImgArgs a;
   CUtensorMap tin, tout;
   fill_img_args(L, g, TX, TY, &a, &tin, &tout);
   if (!a.err) return cudaErrorInvalidDevice;
-  dim3 grid(cdiv(L.W, TX), cdiv(L.H, TY));
+  const int ntx = cdiv(L.W, TX), nty = cdiv(L.H, TY);
+  if (L.pipe && a.tma_ld) {
+    const Geom gp = make_geom(L.esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row, true);
+    FusedPipeKernelFn k = pipe_kernel_for(L.esz, L.op, L.cfg);
+    if (k && gp.smem_bytes <= kMaxSmemBytes && gp.bh == g.bh) {
+      cudaError_t e = allow_smem(reinterpret_cast<const void*>(k));
+      if (e != cudaSuccess) return e;
+      const int grid = persistent_grid(reinterpret_cast<const void*>(k), gp.smem_bytes, ntx * nty);
+      if (grid > 0) {
+        k<<<grid, kThreads, gp.smem_bytes, stream>>>(tin, tout, a, gp, ntx, ntx * nty);
+        return cudaGetLastError();
+      }
+    }
+  }
+  KernelFn k = kernel_for(L.esz, L.op, L.cfg);
+  if (!k) return cudaErrorInvalidValue;
+  cudaError_t e = allow_smem(reinterpret_cast<const void*>(k));
+  if (e != cudaSuccess) return e;
+  dim3 grid(ntx, nty);
   k<<<grid, kThreads, g.smem_bytes, stream>>>(tin, tout, a, g);
   return cudaGetLastError();
 }

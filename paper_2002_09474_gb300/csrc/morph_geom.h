@@ -33,12 +33,20 @@ struct Geom {
   int nchx;      // 8-column blocks of the x pass: ceil(nrx / 8)
   int t_rows;    // S1T rows allocated
   int off_s0, off_sy, off_py, off_ty, off_s1t, off_sx, off_px, off_tx, off_s2;
+  int a_slot;    // pipelined layout: 16-byte units between the two region-A slots (0 otherwise)
+  int in_a;      // bit mask of the buffers placed in region A (kInA* bits)
   int smem_bytes;
 };
 
+// Buffers of a tile, for Geom::in_a.
+constexpr int kInAS0 = 1, kInAY = 2, kInAS1T = 4, kInAX = 8, kInAS2 = 16;
+
 // blk_y / blk_x: the pass uses the blocked large-window method (needs scratch).
+// pipe: the persistent kernel's layout -- two copies of region A (S0 and the
+// buffers that share its space), so the next tile's input can land in one
+// while the current tile is computed in the other, then region B.
 __host__ __device__ inline Geom make_geom(int esz, int TX, int TY, int wx, int wy, int ax, bool blk_y,
-                                          bool blk_x) {
+                                          bool blk_x, bool pipe = false) {
   Geom g;
   g.esz = esz;
   const int al = 16 / esz;  // pixels per 16 bytes
@@ -118,7 +126,10 @@ __host__ __device__ inline Geom make_geom(int esz, int TX, int TY, int wx, int w
       where_s2 = oa;
     }
   }
-  const int offb = round_up(a, 8);
+  const int offb = pipe ? 2 * round_up(a, 8) : round_up(a, 8);
+  g.a_slot = pipe ? round_up(a, 8) : 0;
+  g.in_a = kInAS0 | (where_sy != B ? kInAY : 0) | (where_s1t != B ? kInAS1T : 0) | (where_sx != B ? kInAX : 0) |
+           (where_s2 != B ? kInAS2 : 0);
   auto place = [&](int where, int within) { return (where == B ? offb : 0) + within; };
   g.off_s0 = 0;
   g.off_sy = place(where_sy, 0);
@@ -131,6 +142,29 @@ __host__ __device__ inline Geom make_geom(int esz, int TX, int TY, int wx, int w
   g.off_s2 = place(where_s2, 0);
   g.smem_bytes = 16 * (offb + round_up(b, 8));
   return g;
+}
+
+// The geometry of slot 1 of a pipelined layout: region-A buffers moved to the
+// second copy of region A.
+__host__ __device__ inline Geom geom_slot(const Geom& g, int slot) {
+  Geom s = g;
+  if (slot) {
+    const int d = g.a_slot;
+    s.off_s0 += d;
+    if (g.in_a & kInAY) {
+      s.off_sy += d;
+      s.off_py += d;
+      s.off_ty += d;
+    }
+    if (g.in_a & kInAS1T) s.off_s1t += d;
+    if (g.in_a & kInAX) {
+      s.off_sx += d;
+      s.off_px += d;
+      s.off_tx += d;
+    }
+    if (g.in_a & kInAS2) s.off_s2 += d;
+  }
+  return s;
 }
 
 }  // namespace morph

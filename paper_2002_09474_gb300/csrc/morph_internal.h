@@ -45,11 +45,14 @@ struct FusedLaunch {
   int W, H;
   int wx, wy, ax, ay;  // clipped window
   bool vhgw_col, vhgw_row;
+  bool pipe;           // persistent input-prefetching kernel (set by the planner)
 };
 
 // Shared-memory bytes the fused kernel needs for this launch (0 if the
 // configuration is invalid).
 int fused_smem_bytes(const FusedLaunch& L);
+// The same for the persistent, prefetching form (two region-A slots).
+int fused_pipe_smem_bytes(const FusedLaunch& L);
 // Kernel entry of one (pixel type, op, tile configuration); defined in the
 // instantiation units fused_inst_*.cu.
 struct ImgArgs;
@@ -59,6 +62,12 @@ FusedKernelFn fused_kernel_u8_erode(int cfg);
 FusedKernelFn fused_kernel_u8_dilate(int cfg);
 FusedKernelFn fused_kernel_u16_erode(int cfg);
 FusedKernelFn fused_kernel_u16_dilate(int cfg);
+// The persistent, input-prefetching form (fused_pipe_kernel).
+using FusedPipeKernelFn = void (*)(const CUtensorMap, const CUtensorMap, const ImgArgs, const Geom, int, int);
+FusedPipeKernelFn fused_pipe_kernel_u8_erode(int cfg);
+FusedPipeKernelFn fused_pipe_kernel_u8_dilate(int cfg);
+FusedPipeKernelFn fused_pipe_kernel_u16_erode(int cfg);
+FusedPipeKernelFn fused_pipe_kernel_u16_dilate(int cfg);
 
 // Enqueues the fused kernel; returns a cudaError_t.
 cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream);

@@ -350,13 +350,47 @@ template <typename T> __device__ __forceinline__ uint32_t load_px(const uint8_t*
 }
 
 // ---------------------------------------------------------------------------
-// One tile.  `bar`/`phase` track the TMA barrier across tiles of a CTA.
-// Returns false when a bounded wait gave up (the error word is set).
+// One tile, in three parts: tile_issue_load (thread 0 starts the TMA copy of
+// the tile's input window into S0), the wait on its barrier, and tile_body
+// (identity fix-up or plain loads, both passes, store).  `shift` moves the
+// region-A buffers to the second slot of a pipelined layout (0 otherwise).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4* tile_buf(uint4* smem, const Geom& g, int off, int bit, int shift) {
+  return smem + off + ((g.in_a & bit) ? shift : 0);
+}
+
+// Thread 0 only.  The caller has ordered every earlier generic-proxy access
+// to this S0 before the call (barrier, and a proxy fence after writes).
+template <typename T>
+__device__ __forceinline__ void tile_issue_load(const ImgArgs& a, const CUtensorMap* tin, int x0, int y0,
+                                                const Geom& g, uint8_t* s0, uint64_t* bar) {
+  constexpr int E = sizeof(T);
+  const int xs = x0 - g.lead;
+  const int ys = y0 - a.ay;
+  mbar_arrive_expect_tx(bar, static_cast<uint32_t>(g.nbx * g.nby * g.box * g.bh));
+  for (int bx = 0; bx < g.nbx; ++bx)
+    for (int by = 0; by < g.nby; ++by)
+      tma_load_2d(s0 + (bx * g.ihp + by * g.bh) * g.box, tin, bar, xs + bx * (g.box / E), ys + by * g.bh);
+}
+
+// All threads: waits for the tile's input.  False when the bounded wait gave
+// up (the error word is set).
+__device__ __forceinline__ bool tile_wait_load(uint64_t* bar, uint32_t& phase, int* err) {
+  const bool ok = mbar_wait_bounded(bar, phase);
+  phase ^= 1u;
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(err, kDevErrTmaTimeout);
+    return false;
+  }
+  return true;
+}
+
+// async_store: a TMA store of S2 is left in flight (the caller waits for its
+// reads before S2's space is reused) and the tile ends with a proxy fence,
+// so the next TMA load may overwrite any buffer this tile wrote.
 template <typename T, int OP, int TX, int TY>
-__device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* tin, const CUtensorMap* tout,
-                                         int x0, int y0, const Geom& g, uint4* smem, uint64_t* bar,
-                                         uint32_t& phase, int* err) {
+__device__ __forceinline__ void tile_body(const ImgArgs& a, const CUtensorMap* tout, int x0, int y0,
+                                          const Geom& g, uint4* smem, int shift, bool async_store) {
   constexpr int E = sizeof(T);
   constexpr int PPW = 4 / E;   // pixels per 32-bit word of S0/S2
   constexpr int NTC = TY / 8;  // 8-row chunks per S1T row
@@ -367,26 +401,13 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
   const int tid = threadIdx.x;
   const int xs = x0 - g.lead;  // first loaded pixel column (16-byte aligned)
   const int ys = y0 - a.ay;    // first loaded row
-  uint8_t* s0 = reinterpret_cast<uint8_t*>(smem + g.off_s0);
+  uint8_t* s0 = reinterpret_cast<uint8_t*>(tile_buf(smem, g, g.off_s0, kInAS0, shift));
   const uint32_t IDW = ident_word<OP>();
 
-  // ---- 1. load ---------------------------------------------------------------
+  // ---- 1. load fix-up, or plain loads -------------------------------------------
   const int w_lo = g.k0 * 2 * E, w_hi = g.noct * 2 * E;  // S0 words the passes read
   const bool border = xs < 0 || ys < 0 || xs + g.noct * 8 > a.W || ys + g.ih > a.H;
   if (a.tma_ld) {
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(bar, static_cast<uint32_t>(g.nbx * g.nby * g.box * g.bh));
-      for (int bx = 0; bx < g.nbx; ++bx)
-        for (int by = 0; by < g.nby; ++by)
-          tma_load_2d(s0 + (bx * g.ihp + by * g.bh) * g.box, tin, bar, xs + bx * (g.box / E), ys + by * g.bh);
-    }
-    const bool ok = mbar_wait_bounded(bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicExch(err, kDevErrTmaTimeout);
-      return false;
-    }
     // TMA fills out-of-image pixels with 0: the identity of max, not of min.
     if (OP == 0 && border) {
       for (Strided2D i(w_hi - w_lo, tid, kThreads); i.r < g.ih; i.next()) {
@@ -433,8 +454,8 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     __syncthreads();
   }
 
-  uint8_t* s2 = reinterpret_cast<uint8_t*>(smem + g.off_s2);
-  uint4* s1t = smem + g.off_s1t;
+  uint8_t* s2 = reinterpret_cast<uint8_t*>(tile_buf(smem, g, g.off_s2, kInAS2, shift));
+  uint4* s1t = tile_buf(smem, g, g.off_s1t, kInAS1T, shift);
   const int nk = g.noct - g.k0;  // octet columns of S0 the pass along y covers
 
   // Emits the 8 y-pass outputs rows 8k..8k+7 of octet column c.
@@ -471,9 +492,9 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     }
   } else if (a.blk_y) {
     const BlkGeo bg = blk_geo(g.ih, TY, a.wy);
-    uint4* sy = smem + g.off_sy;
-    uint4* py = smem + g.off_py;
-    uint4* ty = smem + g.off_ty;
+    uint4* sy = tile_buf(smem, g, g.off_sy, kInAY, shift);
+    uint4* py = tile_buf(smem, g, g.off_py, kInAY, shift);
+    uint4* ty = tile_buf(smem, g, g.off_ty, kInAY, shift);
     const int pitch = g.noct;
     for (Strided2D i(nk, tid, kThreads); i.r < g.nchy; i.next()) {
       const int c = g.k0 + i.c, j = i.r;
@@ -511,9 +532,9 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     };
     if (a.blk_x) {
       const BlkGeo bg = blk_geo(g.nrx, TX, a.wx);
-      uint4* sx = smem + g.off_sx;
-      uint4* px = smem + g.off_px;
-      uint4* tx = smem + g.off_tx;
+      uint4* sx = tile_buf(smem, g, g.off_sx, kInAX, shift);
+      uint4* px = tile_buf(smem, g, g.off_px, kInAX, shift);
+      uint4* tx = tile_buf(smem, g, g.off_tx, kInAX, shift);
       for (int it = tid; it < NTC * g.nchx; it += kThreads) {
         const int c = it % NTC, j = it / NTC;
         const int cs = c ^ (j & MT);                 // S rows 8j.. (block-aligned)
@@ -549,7 +570,7 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
     if (tid == 0) {
       for (int bx = 0; bx < TX * E / SBOX; ++bx) tma_store_2d(tout, s2 + bx * TY * SBOX, x0 + bx * (SBOX / E), y0);
       bulk_commit();
-      bulk_wait_read_all();
+      if (!async_store) bulk_wait_read_all();
     }
     __syncthreads();
   } else {
@@ -583,9 +604,63 @@ __device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* ti
         }
       }
     }
+    if (async_store) fence_proxy_async_smem();
     __syncthreads();
   }
+}
+
+// A whole tile in one CTA with one S0 (the batched kernel's form).
+// `bar`/`phase` track the TMA barrier across tiles of a CTA.  Returns false
+// when a bounded wait gave up (the error word is set).
+template <typename T, int OP, int TX, int TY>
+__device__ __forceinline__ bool run_tile(const ImgArgs& a, const CUtensorMap* tin, const CUtensorMap* tout,
+                                         int x0, int y0, const Geom& g, uint4* smem, uint64_t* bar,
+                                         uint32_t& phase, int* err) {
+  if (a.tma_ld) {
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      tile_issue_load<T>(a, tin, x0, y0, g, reinterpret_cast<uint8_t*>(smem + g.off_s0), bar);
+    }
+    if (!tile_wait_load(bar, phase, err)) return false;
+  }
+  tile_body<T, OP, TX, TY>(a, tout, x0, y0, g, smem, 0, false);
   return true;
+}
+
+// The persistent form: this CTA computes tiles cta, cta + ncta, ... (row-major
+// over ntx tile columns) in a pipelined layout (make_geom with `pipe`).  The
+// TMA load of the next tile goes into the other region-A slot while the
+// current tile is computed; a tile's TMA store stays in flight until the
+// next tile begins.  Needs a.tma_ld; bar[0..1] initialised with count 1.
+template <typename T, int OP, int TX, int TY>
+__device__ __forceinline__ void run_tiles_pipelined(const ImgArgs& a, const CUtensorMap* tin,
+                                                    const CUtensorMap* tout, const Geom& g, uint4* smem,
+                                                    uint64_t* bar, int ntx, int ntiles, int cta, int ncta) {
+  const int tid = threadIdx.x;
+  int t = cta;
+  if (t >= ntiles) return;
+  uint8_t* s0a = reinterpret_cast<uint8_t*>(smem + g.off_s0);
+  uint8_t* s0b = s0a + 16 * g.a_slot;
+  if (tid == 0) tile_issue_load<T>(a, tin, (t % ntx) * TX, (t / ntx) * TY, g, s0a, &bar[0]);
+  uint32_t ph0 = 0, ph1 = 0;
+  for (int i = 0; t < ntiles; ++i, t += ncta) {
+    const int slot = i & 1;
+    const int next = t + ncta;
+    if (tid == 0) {
+      bulk_wait_read_all();  // the previous tile's TMA store has read its S2
+      if (next < ntiles)
+        tile_issue_load<T>(a, tin, (next % ntx) * TX, (next / ntx) * TY, g, slot ? s0a : s0b,
+                           slot ? &bar[0] : &bar[1]);
+    }
+    const bool ok = slot ? tile_wait_load(&bar[1], ph1, a.err) : tile_wait_load(&bar[0], ph0, a.err);
+    if (!ok) {
+      // let the other slot's copy land before the CTA's memory goes away
+      if (tid == 0 && next < ntiles) mbar_wait_bounded(slot ? &bar[0] : &bar[1], slot ? ph0 : ph1);
+      break;
+    }
+    tile_body<T, OP, TX, TY>(a, tout, (t % ntx) * TX, (t / ntx) * TY, g, smem, slot * g.a_slot, true);
+  }
+  if (tid == 0) bulk_wait_all();
 }
 
 }  // namespace morph

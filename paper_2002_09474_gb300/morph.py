@@ -75,6 +75,7 @@ _SIGS = {
     "morph_set_tuning": [_i32, _i32, _i32, _i32],
     "morph_reset_tuning": [],
     "morph_set_split": [_i32],
+    "morph_set_pipeline": [_i32],
     "morph_device_error": [],
 }
 for _name, _args in _SIGS.items():
@@ -179,6 +180,10 @@ def morph_set_tuning(dtype, cross_row, cross_col, tile_cfg):
 
 def morph_set_split(mode):
     return _lib.morph_set_split(mode)
+
+
+def morph_set_pipeline(mode):
+    return _lib.morph_set_pipeline(mode)
 
 
 def morph_reset_tuning():

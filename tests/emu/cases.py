@@ -1,7 +1,9 @@
 """Launch cases for the CPU emulator of the fused kernel (the same shapes,
 windows, anchors, methods, tile shapes and pitches as the GPU parity tests).
 Prints one case per line: esz op W H spad soff dpad doff wx wy ax ay cfg
-cross_x cross_y seed."""
+cross_x cross_y seed pipe.  Every case whose source is TMA-loadable (16-byte
+pitch and offset) appears twice: one CTA per tile, and the persistent
+two-slot form (pipe 1)."""
 import itertools
 import sys
 
@@ -58,7 +60,13 @@ def cases(full=True):
                     for (wx, wy) in ((3, 3), (1, 17), (17, 1), (21, 51)):
                         for op in (0, 1):
                             add(esz, op, 512, 256, 0, 0, 0, 0, wx, wy, wx // 2, wy // 2, cfg, c, c)
-    return out
+    both = []
+    for c in out:
+        both.append(c + (0,))
+        esz, w, spad, soff = c[0], c[2], c[4], c[5]
+        if (w * esz + spad) % 16 == 0 and soff % 16 == 0:
+            both.append(c + (1,))
+    return both
 
 
 if __name__ == "__main__":

@@ -13,12 +13,14 @@
 // bytes.  Results are compared with the brute-force oracle.
 //
 // Input, one case per line on stdin:
-//   esz op W H spad soff dpad doff wx wy ax ay cfg cross_x cross_y seed
-// (pads/offsets in bytes; cfg -1 = the planner's choice).  Output: one line
-// per case, "OK ..." or "FAIL ...".
+//   esz op W H spad soff dpad doff wx wy ax ay cfg cross_x cross_y seed pipe
+// (pads/offsets in bytes; cfg -1 = the planner's choice; pipe 1 = the
+// persistent two-slot kernel with 3 CTAs, when the input is TMA-loadable).
+// Output: one line per case, "OK ..." or "FAIL ...".
 #define MORPH_HOST_EMU 1
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <barrier>
 #include <chrono>
@@ -30,6 +32,8 @@
 #include <thread>
 #include <vector>
 
+#include <unistd.h>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -40,12 +44,15 @@ thread_local uint3 emu_threadIdx;
 struct EmuCta {
   std::barrier<>* bar = nullptr;
   std::atomic<int> orflag{0};
-  // mbarrier: a phase completes when its arrivals are in and its transaction
-  // count is back to zero; the phase bit then flips.
+  // mbarriers by address: a phase completes when its arrivals are in and
+  // its transaction count is back to zero; the phase bit then flips.
+  struct Mbar {
+    int count = 1, pending = 1;
+    long long tx = 0;
+    int phase_bit = 0;
+  };
   std::mutex mu;
-  int count = 1, pending = 1;
-  long long tx = 0;
-  int phase_bit = 0;
+  std::map<const void*, Mbar> mbars;
   const uint8_t* smem = nullptr;
   size_t smem_size = 0;
   std::atomic<int> errors{0};
@@ -112,43 +119,54 @@ static void check_smem(const void* p, size_t bytes, size_t align, const char* wh
 }
 
 namespace morph {
-static void mbar_check_complete() {  // caller holds g_cta->mu
-  if (g_cta->pending == 0 && g_cta->tx == 0) {
-    g_cta->phase_bit ^= 1;
-    g_cta->pending = g_cta->count;
+static void mbar_check_complete(EmuCta::Mbar& m) {  // caller holds g_cta->mu
+  if (m.pending == 0 && m.tx == 0) {
+    m.phase_bit ^= 1;
+    m.pending = m.count;
   }
 }
-void mbar_init(uint64_t*, uint32_t count) {
+void mbar_init(uint64_t* bar, uint32_t count) {
   std::lock_guard<std::mutex> l(g_cta->mu);
-  g_cta->count = g_cta->pending = static_cast<int>(count);
-  g_cta->tx = 0;
-  g_cta->phase_bit = 0;
+  EmuCta::Mbar& m = g_cta->mbars[bar];
+  m.count = m.pending = static_cast<int>(count);
+  m.tx = 0;
+  m.phase_bit = 0;
 }
 void fence_barrier_init() {}
-void mbar_arrive_expect_tx(uint64_t*, uint32_t bytes) {
+void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   std::lock_guard<std::mutex> l(g_cta->mu);
-  g_cta->tx += bytes;
-  g_cta->pending -= 1;
-  mbar_check_complete();
+  auto it = g_cta->mbars.find(bar);
+  if (it == g_cta->mbars.end()) {
+    emu_error("arrive on an uninitialised mbarrier");
+    return;
+  }
+  it->second.tx += bytes;
+  it->second.pending -= 1;
+  mbar_check_complete(it->second);
 }
-bool mbar_try_wait(uint64_t*, uint32_t parity) {
+bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   std::lock_guard<std::mutex> l(g_cta->mu);
-  return g_cta->phase_bit != static_cast<int>(parity);
+  auto it = g_cta->mbars.find(bar);
+  if (it == g_cta->mbars.end()) {
+    emu_error("wait on an uninitialised mbarrier");
+    return true;
+  }
+  return it->second.phase_bit != static_cast<int>(parity);
 }
 bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   const auto t0 = std::chrono::steady_clock::now();
   while (!mbar_try_wait(bar, parity)) {
     if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(5)) {
       std::lock_guard<std::mutex> l(g_cta->mu);
-      emu_error(g_cta->tx < 0 ? "TMA delivered more bytes than expected"
-                              : "TMA transfer count never reached the expected bytes (the wait times out)");
+      emu_error(g_cta->mbars[bar].tx < 0 ? "TMA delivered more bytes than expected"
+                                         : "TMA transfer count never reached the expected bytes (the wait times out)");
       return false;
     }
     std::this_thread::yield();
   }
   return true;
 }
-void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t*, int x, int y) {
+void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   const EmuMap* m = reinterpret_cast<const EmuMap*>(map);
   if ((static_cast<long long>(x) * m->esz) % 16) emu_error("TMA load x not 16-byte aligned");
   if (m->bw > m->W || m->bh > m->H) emu_error("TMA box larger than the tensor");
@@ -165,8 +183,9 @@ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t*, int x, int y) {
       }
     }
   std::lock_guard<std::mutex> l(g_cta->mu);
-  g_cta->tx -= static_cast<long long>(row) * m->bh;
-  mbar_check_complete();
+  EmuCta::Mbar& mb = g_cta->mbars[bar];
+  mb.tx -= static_cast<long long>(row) * m->bh;
+  mbar_check_complete(mb);
 }
 void fence_proxy_async_smem() {}
 void prefetch_tensormap(const CUtensorMap*) {}
@@ -189,6 +208,7 @@ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
 }
 void bulk_commit() {}
 void bulk_wait_read_all() {}
+void bulk_wait_all() {}
 }  // namespace morph
 
 // ---- host side: planner (linked from plan.cpp) ----------------------------------
@@ -198,6 +218,11 @@ namespace morph {
 int fused_smem_bytes(const FusedLaunch& L) {
   if (L.cfg < 0 || L.cfg >= kNumTileCfg) return 0;
   return make_geom(L.esz, tile_tx(L.cfg), tile_ty(L.cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row).smem_bytes;
+}
+int fused_pipe_smem_bytes(const FusedLaunch& L) {
+  if (L.cfg < 0 || L.cfg >= kNumTileCfg) return 0;
+  return make_geom(L.esz, tile_tx(L.cfg), tile_ty(L.cfg), L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row, true)
+      .smem_bytes;
 }
 }  // namespace morph
 
@@ -213,6 +238,30 @@ template <typename T, int OP, int TX, int TY>
 void cta_body(const ImgArgs& a, const CUtensorMap* tin, const CUtensorMap* tout, int x0, int y0, const Geom& g,
               uint4* smem, uint64_t* bar, uint32_t& phase, int* err) {
   run_tile<T, OP, TX, TY>(a, tin, tout, x0, y0, g, smem, bar, phase, err);
+}
+
+using PipeFn = void (*)(const ImgArgs&, const CUtensorMap*, const CUtensorMap*, const Geom&, uint4*, uint64_t*,
+                       int, int, int, int);
+
+template <typename T, int OP, int TX, int TY>
+void pipe_body(const ImgArgs& a, const CUtensorMap* tin, const CUtensorMap* tout, const Geom& g, uint4* smem,
+               uint64_t* bar, int ntx, int ntiles, int cta, int ncta) {
+  run_tiles_pipelined<T, OP, TX, TY>(a, tin, tout, g, smem, bar, ntx, ntiles, cta, ncta);
+}
+
+template <typename T, int OP>
+PipeFn pick_pipe(int cfg) {
+  switch (cfg) {
+    case kTile128x64: return pipe_body<T, OP, 128, 64>;
+    case kTile64x64: return pipe_body<T, OP, 64, 64>;
+    case kTile64x128: return pipe_body<T, OP, 64, 128>;
+    case kTile256x32: return pipe_body<T, OP, 256, 32>;
+    case kTile32x32: return pipe_body<T, OP, 32, 32>;
+    case kTile128x128: return pipe_body<T, OP, 128, 128>;
+    case kTile256x64: return pipe_body<T, OP, 256, 64>;
+    case kTile32x128: return pipe_body<T, OP, 32, 128>;
+  }
+  return nullptr;
 }
 
 template <typename T, int OP>
@@ -271,12 +320,12 @@ static uint64_t splitmix(uint64_t& s) {
 }
 
 int main() {
-  int esz, op, W, H, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, crx, cry;
+  int esz, op, W, H, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, crx, cry, pipe;
   unsigned long long seed;
   int failures = 0, cases = 0;
   pool_init();
-  while (scanf("%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %llu", &esz, &op, &W, &H, &spad, &soff, &dpad, &doff,
-               &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed) == 16) {
+  while (scanf("%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %llu %d", &esz, &op, &W, &H, &spad, &soff, &dpad,
+               &doff, &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed, &pipe) == 17) {
     ++cases;
     const long long sp = static_cast<long long>(W) * esz + spad, dp = static_cast<long long>(W) * esz + dpad;
     // Exact-size buffers: ASan flags any byte outside [offset, last pixel].
@@ -314,7 +363,8 @@ int main() {
       continue;
     }
     const int TX = tile_tx(L.cfg), TY = tile_ty(L.cfg);
-    const Geom g = make_geom(esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
+    const Geom g1 = make_geom(esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
+    const Geom gp = make_geom(esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row, true);
     ImgArgs a{};
     a.src = src;
     a.dst = dst;
@@ -339,39 +389,54 @@ int main() {
              bh <= 256 && (bw * esz) % 16 == 0 && bw <= W && bh <= H;
     };
     CUtensorMap tin{}, tout{};
-    EmuMap mi{src, nullptr, esz, W, H, sp, g.box / esz, g.bh};
+    EmuMap mi{src, nullptr, esz, W, H, sp, g1.box / esz, g1.bh};
     const int sbox = TX * esz < 128 ? TX * esz : 128;
     EmuMap mo{nullptr, dst, esz, W, H, dp, sbox / esz, TY};
     a.tma_ld = tma_ok(src, sp, mi.bw, mi.bh);
     a.tma_st = TX * esz >= 128 && tma_ok(dst, dp, mo.bw, mo.bh);
     memcpy(&tin, &mi, sizeof(mi));
     memcpy(&tout, &mo, sizeof(mo));
+    const bool use_pipe = pipe && a.tma_ld && gp.smem_bytes <= kMaxSmemBytes;
+    const Geom& g = use_pipe ? gp : g1;
     CtaFn fn = esz == 1 ? (op == 0 ? pick<uint8_t, 0>(L.cfg) : pick<uint8_t, 1>(L.cfg))
                         : (op == 0 ? pick<uint16_t, 0>(L.cfg) : pick<uint16_t, 1>(L.cfg));
+    PipeFn pfn = esz == 1 ? (op == 0 ? pick_pipe<uint8_t, 0>(L.cfg) : pick_pipe<uint8_t, 1>(L.cfg))
+                          : (op == 0 ? pick_pipe<uint16_t, 0>(L.cfg) : pick_pipe<uint16_t, 1>(L.cfg));
     const int gx = cdiv(W, TX), gy = cdiv(H, TY);
+    const int ntiles = gx * gy, ncta = use_pipe ? (ntiles < 3 ? ntiles : 3) : ntiles;
     int errors = 0, partial = 0;
     std::string first;
-    for (int by = 0; by < gy; ++by)
-      for (int bx = 0; bx < gx; ++bx) {
-        EmuCta cta;
-        std::barrier<> bar(kThreads);
-        cta.bar = &bar;
-        uint4* smem = static_cast<uint4*>(aligned_alloc(128, (g.smem_bytes + 127) / 128 * 128));
-        cta.smem = reinterpret_cast<const uint8_t*>(smem);
-        cta.smem_size = g.smem_bytes;
-        uint64_t mbar = 0;
-        pool_run([&](int tid) {
-          g_cta = &cta;
-          emu_threadIdx = make_uint3(tid, 0, 0);
-          uint32_t phase = 0;
+    for (int c = 0; c < ncta; ++c) {
+      const int bx = c % gx, by = c / gx;
+      EmuCta cta;
+      std::barrier<> bar(kThreads);
+      cta.bar = &bar;
+      uint4* smem = static_cast<uint4*>(aligned_alloc(128, (g.smem_bytes + 127) / 128 * 128));
+      cta.smem = reinterpret_cast<const uint8_t*>(smem);
+      cta.smem_size = g.smem_bytes;
+      uint64_t mbar[2] = {0, 0};
+      pool_run([&](int tid) {
+        g_cta = &cta;
+        emu_threadIdx = make_uint3(tid, 0, 0);
+        uint32_t phase = 0;
+        if (use_pipe) {
+          if (tid == 0) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+          }
           __syncthreads();
-          fn(a, &tin, &tout, bx * TX, by * TY, g, smem, &mbar, phase, a.err);
-        });
-        free(smem);
-        errors += cta.errors.load();
-        partial += cta.partial_stores.load();
-        if (cta.errors.load() && first.empty()) first = cta.first_error;
-      }
+          pfn(a, &tin, &tout, g, smem, mbar, gx, ntiles, c, ncta);
+        } else {
+          if (tid == 0) mbar_init(&mbar[0], 1);
+          __syncthreads();
+          fn(a, &tin, &tout, bx * TX, by * TY, g, smem, &mbar[0], phase, a.err);
+        }
+      });
+      free(smem);
+      errors += cta.errors.load();
+      partial += cta.partial_stores.load();
+      if (cta.errors.load() && first.empty()) first = cta.first_error;
+    }
     // compare with the oracle, and check the bytes between rows are untouched
     std::vector<uint8_t> want(static_cast<size_t>(W) * H * esz);
     oracle_morph(src, esz, W, H, sp, wx, wy, ax, ay, op, want.data(), static_cast<long long>(W) * esz);
@@ -386,14 +451,18 @@ int main() {
       if (dbuf[b] != 0xA5) ++guard;
     const bool ok = !errors && !bad && !guard && !errword;
     if (!ok) ++failures;
-    printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d partial_st %d "
-           "rows_bad %lld guard %lld dev_err %d %s\n",
+    printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d pipe %d "
+           "partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_pipe ? 1 : 0, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);
   }
   fprintf(stderr, "%d cases, %d failures\n", cases, failures);
-  return failures ? 1 : 0;
+  // The pool's threads still wait on a static barrier: leave without running
+  // static destructors under them.
+  fflush(stdout);
+  fflush(stderr);
+  _exit(failures ? 1 : 0);
 }

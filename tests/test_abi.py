@@ -113,4 +113,6 @@ def test_tuning_arguments():
     assert m.morph_set_tuning(5, 1, 1, -1) == -9
     assert m.morph_set_tuning(0, 1, 1, 99) == -10
     assert m.morph_set_tuning(0, -1, -1, -1) == 0
+    assert m.morph_set_pipeline(2) == -10 and m.morph_set_pipeline(-2) == -10
+    assert m.morph_set_pipeline(0) == 0 and m.morph_set_pipeline(-1) == 0
     assert m.morph_reset_tuning() == 0

@@ -62,11 +62,13 @@ WINDOWS = [(1, 1), (3, 3), (2, 5), (7, 1), (1, 9), (4, 4), (8, 8), (9, 16), (17,
            (64, 65), (61, 61)]
 
 
+@pytest.mark.parametrize("pipe", [0, 1])
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 @pytest.mark.parametrize("method", ["direct", "vhgw", "mixed"])
-def test_shapes_windows_methods(lib, dtype, method):
+def test_shapes_windows_methods(lib, dtype, method, pipe):
     torch = need_cuda()
     lib.morph_reset_tuning()
+    assert lib.morph_set_pipeline(pipe) == 0
     col, row = {"direct": (DIRECT, DIRECT), "vhgw": (VHGW, VHGW), "mixed": (DIRECT, VHGW)}[method]
     set_methods(lib, dtype, col, row)
     g = synth.rng(100 + (dtype == np.uint16))
@@ -82,11 +84,13 @@ def test_shapes_windows_methods(lib, dtype, method):
                 assert np.array_equal(got, want), (h, w, wx, wy, op, method)
 
 
+@pytest.mark.parametrize("pipe", [0, 1])
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 @pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5, 6, 7])
-def test_every_tile_shape(lib, dtype, cfg):
+def test_every_tile_shape(lib, dtype, cfg, pipe):
     torch = need_cuda()
     lib.morph_reset_tuning()
+    assert lib.morph_set_pipeline(pipe) == 0
     g = synth.rng(110 + cfg)
     img = synth.uniform_image(301, 177, dtype, gen=g)
     for method in ("direct", "vhgw"):
@@ -150,12 +154,14 @@ def test_windows_larger_than_image(lib, dtype):
             assert np.array_equal(got, want), (wx, wy, ax, ay, op)
 
 
+@pytest.mark.parametrize("pipe", [0, 1])
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
-def test_tma_paths_on_whole_tiles(lib, dtype):
+def test_tma_paths_on_whole_tiles(lib, dtype, pipe):
     """Sizes that are whole multiples of every tile shape with 16-byte
     pitches: every tile loads and stores through TMA."""
     torch = need_cuda()
     lib.morph_reset_tuning()
+    assert lib.morph_set_pipeline(pipe) == 0
     g = synth.rng(150)
     img = synth.uniform_image(512, 256, dtype, gen=g)
     for cfg in range(8):
@@ -199,3 +205,32 @@ def test_fused_and_two_launch_forms_agree(lib, dtype):
                             assert np.array_equal(got, want[op]), (h, w, wx, wy, mode, op, pad)
     finally:
         lib.morph_set_split(-1)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_persistent_form_many_tiles_per_cta(lib, dtype):
+    """Images with several tiles per resident CTA, so each CTA of the
+    persistent form uses both input slots many times; every tile shape,
+    ragged right and bottom edges, against the separable checker and the
+    one-CTA-per-tile form."""
+    torch = need_cuda()
+    g = synth.rng(170)
+    h, w = 1900, 2501
+    img = synth.uniform_image(w, h, dtype, gen=g)
+    pad = aligned_pad(w, dtype)
+    wins = ((3, 3), (1, 101), (101, 1), (21, 51), (127, 127), (9, 16))
+    want = {(wx, wy, op): oracle.sep_vhgw(img, wx, wy, wx // 2, wy // 2, op)
+            for (wx, wy) in wins for op in ("erode", "dilate")}
+    try:
+        for cfg in range(8):
+            for (wx, wy) in wins:
+                lib.morph_reset_tuning()
+                set_methods(lib, dtype, 9, 9, cfg)
+                for op in ("erode", "dilate"):
+                    for pipe in (1, 0):
+                        assert lib.morph_set_pipeline(pipe) == 0
+                        assert lib.morph_set_split(0) == 0
+                        got = run(lib, torch, img, wx, wy, wx // 2, wy // 2, op, pad=pad, dst_pad=pad)
+                        assert np.array_equal(got, want[(wx, wy, op)]), (cfg, wx, wy, op, pipe)
+    finally:
+        lib.morph_reset_tuning()
