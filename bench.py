@@ -360,6 +360,14 @@ def run_gpu(args):
     libbuild.build()
     from paper_2002_09474_gb300 import morph
 
+    # the library's autotuner (crossovers, form of the pass along x), as a
+    # user would run it once per device; its cache lives outside the repo
+    import tempfile
+    tune_path = os.path.join(tempfile.gettempdir(), "morph_tune_%d.json" % local)
+    rc = morph.morph_autotune(tune_path)
+    if rc != 0:
+        raise morph.MorphError("morph_autotune", rc)
+
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream

@@ -38,8 +38,9 @@
  *  - wx, wy >= 1; 0 <= anchor < w.  A window may be larger than the image
  *    (the window is clipped to the image).
  *  - Single-image calls allocate nothing, except the two-launch form of very
- *    large 2-D windows (see morph_set_split), which takes its intermediate
- *    image from the stream-ordered allocator.
+ *    large 2-D windows (see morph_set_split) and the transpose form of the
+ *    pass along x (see morph_set_xpass), which take their intermediate
+ *    images from the stream-ordered allocator.
  */
 #ifndef MORPH_H
 #define MORPH_H
@@ -231,6 +232,19 @@ int morph_set_split(int mode);
  * Returns MORPH_ERR_ARG for another mode.
  */
 int morph_set_pipeline(int mode);
+
+/*
+ * Form of the pass along x for dtype (MORPH_U8/MORPH_U16).  mode 0 (default):
+ * inside the fused kernel, whose 8x8-pixel register transposes turn it into a
+ * pass along y (section 1's "transpose, pass, transpose" without leaving the
+ * chip); 1: the paper's baseline form of section 5.2.1 through HBM --
+ * transpose_u8/u16 into a scratch image, the pass along y, transpose back --
+ * with a 2-D window's 1 x wy pass run first.  Scratch images come from the
+ * stream-ordered allocator.  morph_autotune measures both and keeps the
+ * faster.  The result never changes.  MORPH_ERR_DTYPE / MORPH_ERR_ARG for a
+ * bad dtype or mode.
+ */
+int morph_set_xpass(int dtype, int mode);
 
 /* Text for a morph_status value (static storage). */
 const char *morph_status_string(int status);

@@ -55,11 +55,103 @@ void clip_window(int n, int w, int a, int* w_out, int* a_out) {
   *w_out = before + after + 1;
 }
 
+namespace {
+
+// Stream-ordered scratch image of `rows` rows of `row_bytes` (pitch rounded
+// to 16 bytes so that TMA can describe it).
+struct Scratch {
+  void* p = nullptr;
+  size_t pitch = 0;
+  cudaStream_t st = nullptr;
+  bool alloc(size_t row_bytes, int rows, cudaStream_t s) {
+    st = s;
+    pitch = (row_bytes + 15) / 16 * 16;
+    return cudaMallocAsync(&p, pitch * static_cast<size_t>(rows), s) == cudaSuccess;
+  }
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, st);
+  }
+};
+
+int launch_one(FusedLaunch L, cudaStream_t stream) {
+  if (!plan_single(&L)) return MORPH_ERR_WINDOW;
+  return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+}
+
+// The pass along x in the paper's baseline form (section 5.2.1): transpose,
+// the same pass along y, transpose back -- here through the standalone
+// transpose kernels and HBM, where the fused kernel transposes 8x8 blocks in
+// registers.  A 2-D window first runs its 1 x wy pass into a scratch image.
+int launch_transposed_x(const FusedLaunch& L, cudaStream_t stream) {
+  const int W = L.W, H = L.H, e = L.esz;
+  const void* xs = L.src;
+  long long xsp = L.sp;
+  Scratch ya, tb, tc;
+  if (L.wy > 1) {
+    if (!ya.alloc(static_cast<size_t>(W) * e, H, stream)) return MORPH_ERR_NOMEM;
+    FusedLaunch A = L;
+    A.wx = 1;
+    A.ax = 0;
+    A.dst = ya.p;
+    A.dp = static_cast<long long>(ya.pitch);
+    const int rc = launch_one(A, stream);
+    if (rc != MORPH_OK) return rc;
+    xs = ya.p;
+    xsp = A.dp;
+  }
+  // tb, tc: H pixels per row, W rows (the transposed image)
+  if (!tb.alloc(static_cast<size_t>(H) * e, W, stream) || !tc.alloc(static_cast<size_t>(H) * e, W, stream))
+    return MORPH_ERR_NOMEM;
+  if (transpose_launch(xs, xsp, tb.p, static_cast<long long>(tb.pitch), W, H, e, stream) != cudaSuccess)
+    return MORPH_ERR_CUDA;
+  FusedLaunch B = L;
+  B.W = H;
+  B.H = W;
+  B.wx = 1;
+  B.ax = 0;
+  B.wy = L.wx;
+  B.ay = L.ax;
+  B.src = tb.p;
+  B.sp = static_cast<long long>(tb.pitch);
+  B.dst = tc.p;
+  B.dp = static_cast<long long>(tc.pitch);
+  const int rc = launch_one(B, stream);
+  if (rc != MORPH_OK) return rc;
+  return transpose_launch(tc.p, static_cast<long long>(tc.pitch), L.dst, L.dp, H, W, e, stream) == cudaSuccess
+             ? MORPH_OK
+             : MORPH_ERR_CUDA;
+}
+
+}  // namespace
+
+int launch_planned(FusedLaunch L, cudaStream_t stream) {
+  if (L.wx > 1 && tuning().xpass_transpose[L.esz - 1]) return launch_transposed_x(L, stream);
+  if (!plan_split(L)) return launch_one(L, stream);
+  // Split form (section 5's separability): the 1 x wy pass into an
+  // intermediate image, then the wx x 1 pass from it.  The intermediate is a
+  // stream-ordered allocation (16-byte rows, so both launches can use TMA).
+  Scratch tmp;
+  if (!tmp.alloc(static_cast<size_t>(L.W) * L.esz, L.H, stream)) return MORPH_ERR_NOMEM;
+  FusedLaunch A = L, B = L;
+  A.wx = 1;
+  A.ax = 0;
+  A.dst = tmp.p;
+  A.dp = static_cast<long long>(tmp.pitch);
+  B.wy = 1;
+  B.ay = 0;
+  B.src = tmp.p;
+  B.sp = static_cast<long long>(tmp.pitch);
+  int rc = launch_one(A, stream);
+  if (rc == MORPH_OK) rc = launch_one(B, stream);
+  return rc;
+}
+
 int run_single(const void* src, size_t sp, void* dst, size_t dp, int W, int H, int dtype, int op, int wx,
                int wy, int ax, int ay, cudaStream_t stream) {
   int rc = validate(src, sp, dst, dp, W, H, dtype, op, wx, wy, ax, ay);
   if (rc != MORPH_OK) return rc;
   FusedLaunch L;
+  memset(&L, 0, sizeof(L));
   L.esz = esz_of(dtype);
   L.op = op;
   L.src = src;
@@ -70,31 +162,7 @@ int run_single(const void* src, size_t sp, void* dst, size_t dp, int W, int H, i
   L.H = H;
   clip_window(W, wx, ax, &L.wx, &L.ax);
   clip_window(H, wy, ay, &L.wy, &L.ay);
-  if (!plan_split(L)) {
-    if (!plan_single(&L)) return MORPH_ERR_WINDOW;
-    return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
-  }
-  // Split form (section 5's separability): the 1 x wy pass into an
-  // intermediate image, then the wx x 1 pass from it.  The intermediate is a
-  // stream-ordered allocation (16-byte rows, so both launches can use TMA).
-  const size_t tp = (static_cast<size_t>(W) * L.esz + 15) / 16 * 16;
-  void* tmp = nullptr;
-  if (cudaMallocAsync(&tmp, tp * static_cast<size_t>(H), stream) != cudaSuccess) return MORPH_ERR_NOMEM;
-  FusedLaunch A = L, B = L;
-  A.wx = 1;
-  A.ax = 0;
-  A.dst = tmp;
-  A.dp = static_cast<long long>(tp);
-  B.wy = 1;
-  B.ay = 0;
-  B.src = tmp;
-  B.sp = static_cast<long long>(tp);
-  rc = MORPH_OK;
-  if (!plan_single(&A) || !plan_single(&B)) rc = MORPH_ERR_WINDOW;
-  if (rc == MORPH_OK && fused_launch(A, stream) != cudaSuccess) rc = MORPH_ERR_CUDA;
-  if (rc == MORPH_OK && fused_launch(B, stream) != cudaSuccess) rc = MORPH_ERR_CUDA;
-  cudaFreeAsync(tmp, stream);
-  return rc;
+  return launch_planned(L, stream);
 }
 
 // Device staging buffers of morph_apply_host: one input/output pair per
@@ -376,6 +444,14 @@ int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg) {
 int morph_set_split(int mode) {
   if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
   tuning().split_mode = mode;
+  return MORPH_OK;
+}
+
+int morph_set_xpass(int dtype, int mode) {
+  const int esz = esz_of(dtype);
+  if (!esz) return MORPH_ERR_DTYPE;
+  if (mode < 0 || mode > 1) return MORPH_ERR_ARG;
+  tuning().xpass_transpose[esz - 1] = mode;
   return MORPH_OK;
 }
 

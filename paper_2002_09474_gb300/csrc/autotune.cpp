@@ -2,7 +2,9 @@
 // direct method beats the blocked van Herk/Gil-Werman method, per pixel type
 // and per pass -- the crossovers w_x^0 / w_y^0 of the paper's section 5.3,
 // which the paper measured on an ARM CPU (59 and 69) and which differ on a
-// GPU.  Results persist as a small JSON file keyed by the device.
+// GPU -- and, per pixel type, whether the pass along x runs faster inside the
+// fused kernel or through the standalone transpose kernels (section 5.2.1's
+// form).  Results persist as a small JSON file keyed by the device.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -49,6 +51,22 @@ float time_launch(FusedLaunch L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1
   return t[t.size() / 2];
 }
 
+// Median time (ms) of one call in the planned form under the current tuning.
+float time_planned(const FusedLaunch& L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  std::vector<float> t;
+  for (int r = 0; r < kReps + 1; ++r) {
+    cudaEventRecord(e0, st);
+    if (launch_planned(L, st) != MORPH_OK) return 1e30f;
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r) t.push_back(ms);
+  }
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+
 bool load_cache(const char* path, const std::string& key, Tuning* t) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
@@ -68,14 +86,23 @@ bool load_cache(const char* path, const std::string& key, Tuning* t) {
   t->cross_col[0] = v[1];
   t->cross_row[1] = v[2];
   t->cross_col[1] = v[3];
+  int xp[2] = {0, 0};
+  const char* q = strstr(buf, "\"xpass\": [");
+  if (q && sscanf(q, "\"xpass\": [%d, %d]", &xp[0], &xp[1]) == 2) {
+    t->xpass_transpose[0] = xp[0] == 1;
+    t->xpass_transpose[1] = xp[1] == 1;
+  }
   return true;
 }
 
 bool save_cache(const char* path, const std::string& key, const Tuning& t) {
   FILE* f = fopen(path, "w");
   if (!f) return false;
-  fprintf(f, "{\"device\": \"%s\", \"cross\": [%d, %d, %d, %d], \"order\": \"u8 x, u8 y, u16 x, u16 y\"}\n",
-          key.c_str(), t.cross_row[0], t.cross_col[0], t.cross_row[1], t.cross_col[1]);
+  fprintf(f,
+          "{\"device\": \"%s\", \"cross\": [%d, %d, %d, %d], \"order\": \"u8 x, u8 y, u16 x, u16 y\", "
+          "\"xpass\": [%d, %d]}\n",
+          key.c_str(), t.cross_row[0], t.cross_col[0], t.cross_row[1], t.cross_col[1], t.xpass_transpose[0],
+          t.xpass_transpose[1]);
   return fclose(f) == 0;
 }
 
@@ -146,6 +173,30 @@ extern "C" int morph_autotune(const char* cache_path) {
   }
   t.forced_cfg[0] = forced0;
   t.forced_cfg[1] = forced1;
+  // The pass along x: fused (register transposes) or through the transpose
+  // kernels, timed on a small and a large 1-D window along x.
+  for (int e = 0; e < 2 && rc == MORPH_OK; ++e) {
+    float tf = 0, tt = 0;
+    for (int w : {15, 101}) {
+      FusedLaunch L;
+      memset(&L, 0, sizeof(L));
+      L.esz = e + 1;
+      L.src = src;
+      L.dst = dst;
+      L.sp = L.dp = static_cast<long long>(pitch);
+      L.W = kTuneW;
+      L.H = kTuneH;
+      L.wx = w;
+      L.ax = w / 2;
+      L.wy = 1;
+      t.xpass_transpose[e] = 0;
+      tf += time_planned(L, st, e0, e1);
+      t.xpass_transpose[e] = 1;
+      tt += time_planned(L, st, e0, e1);
+    }
+    if (tf >= 1e29f || tt >= 1e29f) rc = MORPH_ERR_CUDA;
+    t.xpass_transpose[e] = tt < tf ? 1 : 0;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(st);

@@ -72,6 +72,7 @@ void reset_tuning_defaults() {
     g_tuning.cross_col[e] = 9;
     g_tuning.cross_row[e] = 9;
     g_tuning.forced_cfg[e] = -1;
+    g_tuning.xpass_transpose[e] = 0;
   }
   g_tuning.split_mode = -1;
   g_tuning.pipe_mode = -1;

@@ -14,6 +14,7 @@ struct Tuning {
   int forced_cfg[2];              // [esz-1]: tile configuration to use when it fits (-1: cost model)
   int split_mode;                 // 2-D windows as two 1-D launches: -1 auto, 0 never, 1 always
   int pipe_mode;                  // persistent input-prefetching kernel: -1 auto, 0 never, 1 always
+  int xpass_transpose[2];         // [esz-1]: pass along x through the transpose kernels (1) or fused (0)
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 
@@ -30,5 +31,10 @@ bool plan_single(FusedLaunch* L);
 bool plan_split(const FusedLaunch& L);
 double tile_cost(const FusedLaunch& L, int cfg);
 int ctas_per_sm(int smem_bytes);
+
+// Runs one clipped single-image launch by the planned form (fused, two
+// launches, or the pass along x through the transpose kernels); returns a
+// morph_status.  Defined with the C ABI.
+int launch_planned(FusedLaunch L, cudaStream_t stream);
 
 }  // namespace morph

@@ -234,3 +234,27 @@ def test_persistent_form_many_tiles_per_cta(lib, dtype):
                         assert np.array_equal(got, want[(wx, wy, op)]), (cfg, wx, wy, op, pipe)
     finally:
         lib.morph_reset_tuning()
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_pass_along_x_through_transpose_kernels(lib, dtype):
+    """Section 5.2.1's baseline form of the pass along x (transpose kernels,
+    pass along y, transpose back) gives the same result as the fused form."""
+    torch = need_cuda()
+    lib.morph_reset_tuning()
+    code = lib.MORPH_U8 if dtype == np.uint8 else lib.MORPH_U16
+    g = synth.rng(180)
+    try:
+        for (h, w) in ((1, 1), (37, 300), (257, 129), (200, 513), (64, 64)):
+            img = synth.uniform_image(w, h, dtype, gen=g)
+            for (wx, wy, ax, ay) in ((5, 1, 2, 0), (64, 1, 10, 0), (127, 1, 63, 0), (9, 17, 4, 8),
+                                     (40, 3, 39, 0), (2, 2, 1, 0)):
+                for op in ("erode", "dilate"):
+                    want = oracle.morph(img, wx, wy, ax, ay, op)
+                    for mode in (1, 0):
+                        assert lib.morph_set_xpass(code, mode) == 0
+                        for pad in (0, aligned_pad(w, dtype)):
+                            got = run(lib, torch, img, wx, wy, ax, ay, op, pad=pad, dst_pad=pad)
+                            assert np.array_equal(got, want), (h, w, wx, wy, ax, ay, op, mode, pad)
+    finally:
+        lib.morph_reset_tuning()
