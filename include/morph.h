@@ -234,6 +234,16 @@ int morph_set_split(int mode);
 int morph_set_pipeline(int mode);
 
 /*
+ * Kernel for single-image calls whose window is 1 x wy (wy > 1), including
+ * the first launch of the two-launch form: mode -1 (default) or 1: the
+ * column kernel (one pass along y per CTA tile 128 bytes wide and as tall as
+ * fills whole waves of the GPU; outputs stored from registers); 0: the
+ * fused two-pass tile kernel.  The result never changes.  MORPH_ERR_ARG for
+ * another mode.
+ */
+int morph_set_column_kernel(int mode);
+
+/*
  * Form of the pass along x for dtype (MORPH_U8/MORPH_U16).  mode 0 (default):
  * inside the fused kernel, whose 8x8-pixel register transposes turn it into a
  * pass along y (section 1's "transpose, pass, transpose" without leaving the

@@ -75,6 +75,8 @@ struct Scratch {
 
 int launch_one(FusedLaunch L, cudaStream_t stream) {
   if (!plan_single(&L)) return MORPH_ERR_WINDOW;
+  if (L.wx == 1 && L.wy > 1 && tuning().col_mode != 0)
+    return col_launch(L, L.vhgw_col && L.wy >= 9, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
 }
 
@@ -452,6 +454,12 @@ int morph_set_xpass(int dtype, int mode) {
   if (!esz) return MORPH_ERR_DTYPE;
   if (mode < 0 || mode > 1) return MORPH_ERR_ARG;
   tuning().xpass_transpose[esz - 1] = mode;
+  return MORPH_OK;
+}
+
+int morph_set_column_kernel(int mode) {
+  if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
+  tuning().col_mode = mode;
   return MORPH_OK;
 }
 

@@ -36,11 +36,10 @@ std::string device_key() {
 
 // Median time (ms) of one forced configuration.
 float time_launch(FusedLaunch L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-  if (!plan_single(&L)) return 1e30f;
   std::vector<float> t;
   for (int r = 0; r < kReps + 1; ++r) {
     cudaEventRecord(e0, st);
-    if (fused_launch(L, st) != cudaSuccess) return 1e30f;
+    if (launch_planned(L, st) != MORPH_OK) return 1e30f;
     cudaEventRecord(e1, st);
     cudaEventSynchronize(e1);
     float ms = 0;

@@ -180,6 +180,8 @@ cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+int* device_error_word() { return fused_err_ptr(); }
+
 int fused_take_device_error() {
   int v = 0, z = 0;
   if (cudaMemcpyFromSymbol(&v, g_fused_err, sizeof(int)) != cudaSuccess) return -1;

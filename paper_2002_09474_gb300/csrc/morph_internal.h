@@ -73,6 +73,12 @@ FusedPipeKernelFn fused_pipe_kernel_u16_dilate(int cfg);
 cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream);
 // Reads and clears the fused kernels' device error word.
 int fused_take_device_error();
+// Device address of that word on the current device (nullptr on failure).
+int* device_error_word();
+
+// The column-pass kernel for 1 x wy windows (blocked: van Herk/Gil-Werman
+// blocks, needs wy >= 9; else the direct method).
+cudaError_t col_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream);
 
 // Enqueues the tiled transpose kernel: dst (W rows of H pixels) = src^T.
 cudaError_t transpose_launch(const void* src, long long sp, void* dst, long long dp, int W, int H, int esz,

@@ -15,6 +15,7 @@ struct Tuning {
   int split_mode;                 // 2-D windows as two 1-D launches: -1 auto, 0 never, 1 always
   int pipe_mode;                  // persistent input-prefetching kernel: -1 auto, 0 never, 1 always
   int xpass_transpose[2];         // [esz-1]: pass along x through the transpose kernels (1) or fused (0)
+  int col_mode;                   // 1 x wy windows by the column kernel: -1 auto (yes), 0 never, 1 always
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 

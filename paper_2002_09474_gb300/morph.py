@@ -76,6 +76,7 @@ _SIGS = {
     "morph_reset_tuning": [],
     "morph_set_split": [_i32],
     "morph_set_pipeline": [_i32],
+    "morph_set_column_kernel": [_i32],
     "morph_set_xpass": [_i32, _i32],
     "morph_device_error": [],
 }
@@ -185,6 +186,10 @@ def morph_set_split(mode):
 
 def morph_set_pipeline(mode):
     return _lib.morph_set_pipeline(mode)
+
+
+def morph_set_column_kernel(mode):
+    return _lib.morph_set_column_kernel(mode)
 
 
 def morph_set_xpass(dtype, mode):

@@ -1,9 +1,9 @@
 """Launch cases for the CPU emulator of the fused kernel (the same shapes,
 windows, anchors, methods, tile shapes and pitches as the GPU parity tests).
 Prints one case per line: esz op W H spad soff dpad doff wx wy ax ay cfg
-cross_x cross_y seed pipe.  Every case whose source is TMA-loadable (16-byte
-pitch and offset) appears twice: one CTA per tile, and the persistent
-two-slot form (pipe 1)."""
+cross_x cross_y seed kern.  Every case whose source is TMA-loadable (16-byte
+pitch and offset) also appears in the persistent two-slot form (kern 1), and
+every 1 x wy case (wy > 1) also through the column kernel (kern 2)."""
 import itertools
 import sys
 
@@ -63,9 +63,22 @@ def cases(full=True):
     both = []
     for c in out:
         both.append(c + (0,))
-        esz, w, spad, soff = c[0], c[2], c[4], c[5]
+        esz, w, spad, soff, wx, wy = c[0], c[2], c[4], c[5], c[8], c[9]
         if (w * esz + spad) % 16 == 0 and soff % 16 == 0:
             both.append(c + (1,))
+    # the column kernel: every 1 x wy case, plus tall images and long windows
+    col = [c for c in out if c[8] == 1 and c[9] > 1]
+    seed = 100000
+    for esz in (1, 2):
+        for (w, h) in ((128, 1000), (300, 2100), (64, 700), (1, 900), (257, 33)):
+            for wy in (2, 7, 8, 9, 10, 16, 17, 31, 63, 101, 255, 700):
+                for op in (0, 1):
+                    for cross in (0, 1000000):
+                        pad = aligned_pad(w, esz) if (wy + op) % 2 else 0
+                        col.append((esz, op, w, h, pad, 0, pad, 0, 1, wy, 0, wy // 2, -1, cross, cross, seed))
+                        seed += 1
+    for c in col:
+        both.append(c + (2,))
     return both
 
 

@@ -13,9 +13,11 @@
 // bytes.  Results are compared with the brute-force oracle.
 //
 // Input, one case per line on stdin:
-//   esz op W H spad soff dpad doff wx wy ax ay cfg cross_x cross_y seed pipe
-// (pads/offsets in bytes; cfg -1 = the planner's choice; pipe 1 = the
-// persistent two-slot kernel with 3 CTAs, when the input is TMA-loadable).
+//   esz op W H spad soff dpad doff wx wy ax ay cfg cross_x cross_y seed kern
+// (pads/offsets in bytes; cfg -1 = the planner's choice; kern 0 = one CTA
+// per tile, 1 = the persistent two-slot kernel with 3 CTAs when the input is
+// TMA-loadable, 2 = the column kernel for 1 x wy windows, its tile height
+// planned for 152 SMs on odd seeds and 3 SMs on even ones).
 // Output: one line per case, "OK ..." or "FAIL ...".
 #define MORPH_HOST_EMU 1
 
@@ -101,6 +103,7 @@ static inline unsigned int __byte_perm(unsigned int x, unsigned int y, unsigned 
 static inline int atomicExch(int* p, int v) { return __atomic_exchange_n(p, v, __ATOMIC_SEQ_CST); }
 
 #include "morph_tile.cuh"
+#include "morph_col.cuh"
 
 // ---- TMA / mbarrier model ------------------------------------------------------
 struct EmuMap {
@@ -292,24 +295,32 @@ static std::function<void(int)> g_job;
 static std::barrier<>* g_start = nullptr;
 static std::barrier<>* g_done = nullptr;
 static bool g_quit = false;
+static int g_active = kThreads;  // threads of the current CTA
 static void pool_init() {
-  static std::barrier<> start(kThreads + 1), done(kThreads + 1);
+  static std::barrier<> start(kColThreads + 1), done(kColThreads + 1);
   g_start = &start;
   g_done = &done;
-  for (int t = 0; t < kThreads; ++t)
+  for (int t = 0; t < kColThreads; ++t)
     std::thread([t] {
       for (;;) {
         g_start->arrive_and_wait();
         if (g_quit) return;
-        g_job(t);
+        if (t < g_active) g_job(t);
         g_done->arrive_and_wait();
       }
     }).detach();
 }
-static void pool_run(std::function<void(int)> job) {
+static void pool_run(std::function<void(int)> job, int nthreads = kThreads) {
   g_job = std::move(job);
+  g_active = nthreads;
   g_start->arrive_and_wait();
   g_done->arrive_and_wait();
+}
+
+using ColFnE = bool (*)(const ColArgs&, const CUtensorMap*, int, uint8_t*, uint32_t*, uint64_t*);
+template <typename T, int OP>
+ColFnE pick_col(bool blk) {
+  return blk ? col_tile<T, OP, true> : col_tile<T, OP, false>;
 }
 
 static uint64_t splitmix(uint64_t& s) {
@@ -320,12 +331,13 @@ static uint64_t splitmix(uint64_t& s) {
 }
 
 int main() {
-  int esz, op, W, H, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, crx, cry, pipe;
+  int esz, op, W, H, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, crx, cry, kern;
   unsigned long long seed;
   int failures = 0, cases = 0;
   pool_init();
   while (scanf("%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %llu %d", &esz, &op, &W, &H, &spad, &soff, &dpad,
-               &doff, &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed, &pipe) == 17) {
+               &doff, &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed, &kern) == 17) {
+    const int pipe = kern == 1;
     ++cases;
     const long long sp = static_cast<long long>(W) * esz + spad, dp = static_cast<long long>(W) * esz + dpad;
     // Exact-size buffers: ASan flags any byte outside [offset, last pixel].
@@ -396,7 +408,8 @@ int main() {
     a.tma_st = TX * esz >= 128 && tma_ok(dst, dp, mo.bw, mo.bh);
     memcpy(&tin, &mi, sizeof(mi));
     memcpy(&tout, &mo, sizeof(mo));
-    const bool use_pipe = pipe && a.tma_ld && gp.smem_bytes <= kMaxSmemBytes;
+    const bool use_col = kern == 2 && L.wx == 1 && L.wy > 1;
+    const bool use_pipe = !use_col && pipe && a.tma_ld && gp.smem_bytes <= kMaxSmemBytes;
     const Geom& g = use_pipe ? gp : g1;
     CtaFn fn = esz == 1 ? (op == 0 ? pick<uint8_t, 0>(L.cfg) : pick<uint8_t, 1>(L.cfg))
                         : (op == 0 ? pick<uint16_t, 0>(L.cfg) : pick<uint16_t, 1>(L.cfg));
@@ -406,7 +419,62 @@ int main() {
     const int ntiles = gx * gy, ncta = use_pipe ? (ntiles < 3 ? ntiles : 3) : ntiles;
     int errors = 0, partial = 0;
     std::string first;
-    for (int c = 0; c < ncta; ++c) {
+    int col_ty = 0;
+    if (use_col) {
+      // the column kernel, planned and launched as col_launch does
+      const bool blk = L.vhgw_col && L.wy >= 9;
+      const int ty = col_pick_ty(esz, W, H, L.wy, (seed & 1) ? 152 : 3, kMaxSmemBytes);
+      const ColGeom cg = col_geom(esz, ty, L.wy);
+      col_ty = ty;
+      ColArgs c{};
+      c.src = src;
+      c.dst = dst;
+      c.sp = sp;
+      c.dp = dp;
+      c.W = W;
+      c.H = H;
+      c.w = L.wy;
+      c.a = L.ay;
+      c.ty = cg.ty;
+      c.ih = cg.ih;
+      c.ihp = cg.ihp;
+      c.ntx = cdiv(W * esz, kColBytes);
+      c.ntiles = c.ntx * cdiv(H, cg.ty);
+      c.blocked = blk;
+      c.ld_vec = a.ld_vec;
+      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
+      c.err = &errword;
+      c.tma_ld = tma_ok(src, sp, kColBytes / esz, kColBox);
+      EmuMap mc{src, nullptr, esz, W, H, sp, kColBytes / esz, kColBox};
+      CUtensorMap tc{};
+      memcpy(&tc, &mc, sizeof(mc));
+      ColFnE cf = esz == 1 ? (op == 0 ? pick_col<uint8_t, 0>(blk) : pick_col<uint8_t, 1>(blk))
+                           : (op == 0 ? pick_col<uint16_t, 0>(blk) : pick_col<uint16_t, 1>(blk));
+      for (int t = 0; t < c.ntiles; ++t) {
+        EmuCta cta;
+        std::barrier<> bar(kColThreads);
+        cta.bar = &bar;
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (cg.smem + 127) / 128 * 128));
+        cta.smem = sm;
+        cta.smem_size = cg.smem;
+        uint64_t mbars[kColMaxBoxes] = {};
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              if (tid == 0)
+                for (int b = 0; b < kColMaxBoxes; ++b) mbar_init(&mbars[b], 1);
+              __syncthreads();
+              cf(c, &tc, t, sm, reinterpret_cast<uint32_t*>(sm + kColBytes * cg.ihp), mbars);
+            },
+            kColThreads);
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+      a.tma_ld = c.tma_ld;
+    }
+    for (int c = 0; c < (use_col ? 0 : ncta); ++c) {
       const int bx = c % gx, by = c / gx;
       EmuCta cta;
       std::barrier<> bar(kThreads);
@@ -451,10 +519,10 @@ int main() {
       if (dbuf[b] != 0xA5) ++guard;
     const bool ok = !errors && !bad && !guard && !errword;
     if (!ok) ++failures;
-    printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d pipe %d "
-           "partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
+    printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
+           "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_pipe ? 1 : 0, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);
