@@ -244,6 +244,17 @@ int morph_set_pipeline(int mode);
 int morph_set_column_kernel(int mode);
 
 /*
+ * Kernel for single-image calls whose window is wx x 1 (wx > 1), including
+ * the second launch of the two-launch form: mode -1 (default) or 1: the row
+ * kernel (tiles 256 bytes wide; 8 x 8-pixel blocks transposed once in
+ * registers into a column-major shared-memory copy, the pass along x run on
+ * it, outputs transposed back and stored from registers) when its tile fits
+ * in shared memory; 0: the fused two-pass tile kernel.  The result never
+ * changes.  MORPH_ERR_ARG for another mode.
+ */
+int morph_set_row_kernel(int mode);
+
+/*
  * Form of the pass along x for dtype (MORPH_U8/MORPH_U16).  mode 0 (default):
  * inside the fused kernel, whose 8x8-pixel register transposes turn it into a
  * pass along y (section 1's "transpose, pass, transpose" without leaving the

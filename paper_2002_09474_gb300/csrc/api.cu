@@ -77,6 +77,8 @@ int launch_one(FusedLaunch L, cudaStream_t stream) {
   if (!plan_single(&L)) return MORPH_ERR_WINDOW;
   if (L.wx == 1 && L.wy > 1 && tuning().col_mode != 0)
     return col_launch(L, L.vhgw_col && L.wy >= 9, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+  if (L.wy == 1 && L.wx > 1 && tuning().row_mode != 0 && row_fits(L))
+    return row_launch(L, L.vhgw_row && L.wx >= 9, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
 }
 
@@ -460,6 +462,12 @@ int morph_set_xpass(int dtype, int mode) {
 int morph_set_column_kernel(int mode) {
   if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
   tuning().col_mode = mode;
+  return MORPH_OK;
+}
+
+int morph_set_row_kernel(int mode) {
+  if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
+  tuning().row_mode = mode;
   return MORPH_OK;
 }
 

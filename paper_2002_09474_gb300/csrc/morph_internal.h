@@ -80,6 +80,11 @@ int* device_error_word();
 // blocks, needs wy >= 9; else the direct method).
 cudaError_t col_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream);
 
+// The row-pass kernel for wx x 1 windows (blocked needs wx >= 9), when its
+// tile fits in shared memory (row_fits).
+bool row_fits(const FusedLaunch& L);
+cudaError_t row_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream);
+
 // Enqueues the tiled transpose kernel: dst (W rows of H pixels) = src^T.
 cudaError_t transpose_launch(const void* src, long long sp, void* dst, long long dp, int W, int H, int esz,
                              cudaStream_t stream);

@@ -77,6 +77,7 @@ void reset_tuning_defaults() {
   g_tuning.split_mode = -1;
   g_tuning.pipe_mode = -1;
   g_tuning.col_mode = -1;
+  g_tuning.row_mode = -1;
   g_tuning.from_autotune = 0;
   g_init = true;
 }

@@ -16,6 +16,7 @@ struct Tuning {
   int pipe_mode;                  // persistent input-prefetching kernel: -1 auto, 0 never, 1 always
   int xpass_transpose[2];         // [esz-1]: pass along x through the transpose kernels (1) or fused (0)
   int col_mode;                   // 1 x wy windows by the column kernel: -1 auto (yes), 0 never, 1 always
+  int row_mode;                   // wx x 1 windows by the row kernel: -1 auto (yes), 0 never, 1 always
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 

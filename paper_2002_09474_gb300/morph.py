@@ -77,6 +77,7 @@ _SIGS = {
     "morph_set_split": [_i32],
     "morph_set_pipeline": [_i32],
     "morph_set_column_kernel": [_i32],
+    "morph_set_row_kernel": [_i32],
     "morph_set_xpass": [_i32, _i32],
     "morph_device_error": [],
 }
@@ -190,6 +191,10 @@ def morph_set_pipeline(mode):
 
 def morph_set_column_kernel(mode):
     return _lib.morph_set_column_kernel(mode)
+
+
+def morph_set_row_kernel(mode):
+    return _lib.morph_set_row_kernel(mode)
 
 
 def morph_set_xpass(dtype, mode):

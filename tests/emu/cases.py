@@ -3,7 +3,8 @@ windows, anchors, methods, tile shapes and pitches as the GPU parity tests).
 Prints one case per line: esz op W H spad soff dpad doff wx wy ax ay cfg
 cross_x cross_y seed kern.  Every case whose source is TMA-loadable (16-byte
 pitch and offset) also appears in the persistent two-slot form (kern 1), and
-every 1 x wy case (wy > 1) also through the column kernel (kern 2)."""
+every 1 x wy case (wy > 1) also through the column kernel (kern 2), every
+wx x 1 case (wx > 1) also through the row kernel (kern 3)."""
 import itertools
 import sys
 
@@ -79,6 +80,26 @@ def cases(full=True):
                         seed += 1
     for c in col:
         both.append(c + (2,))
+    # the row kernel: every wx x 1 case, plus wide images, long windows, all
+    # anchor extremes, unaligned pitches and offsets
+    row = [c for c in out if c[9] == 1 and c[8] > 1]
+    for esz in (1, 2):
+        for (w, h) in ((256, 64), (257, 65), (1000, 70), (2100, 9), (7, 130), (513, 128)):
+            for wx in (2, 3, 8, 9, 10, 17, 31, 63, 101, 255, 700):
+                for ax in sorted({0, wx // 2, wx - 1}):
+                    for op in (0, 1):
+                        for cross in (0, 1000000):
+                            n = len(row)
+                            if n % 3 == 0:
+                                pad, off, dpad, doff = aligned_pad(w, esz), 0, aligned_pad(w, esz), 0
+                            elif n % 3 == 1:
+                                pad, off, dpad, doff = 0, 0, 0, 0
+                            else:
+                                pad, off, dpad, doff = 3 * esz, esz, 5 * esz, 2 * esz
+                            row.append((esz, op, w, h, pad, off, dpad, doff, wx, 1, ax, 0, -1, cross, cross, seed))
+                            seed += 1
+    for c in row:
+        both.append(c + (3,))
     return both
 
 

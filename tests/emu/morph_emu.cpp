@@ -17,7 +17,8 @@
 // (pads/offsets in bytes; cfg -1 = the planner's choice; kern 0 = one CTA
 // per tile, 1 = the persistent two-slot kernel with 3 CTAs when the input is
 // TMA-loadable, 2 = the column kernel for 1 x wy windows, its tile height
-// planned for 152 SMs on odd seeds and 3 SMs on even ones).
+// planned for 152 SMs on odd seeds and 3 SMs on even ones, 3 = the row
+// kernel for wx x 1 windows).
 // Output: one line per case, "OK ..." or "FAIL ...".
 #define MORPH_HOST_EMU 1
 
@@ -101,9 +102,14 @@ static inline unsigned int __byte_perm(unsigned int x, unsigned int y, unsigned 
   return r;
 }
 static inline int atomicExch(int* p, int v) { return __atomic_exchange_n(p, v, __ATOMIC_SEQ_CST); }
+static inline unsigned int __funnelshift_r(unsigned int lo, unsigned int hi, unsigned int s) {
+  const uint64_t v = (static_cast<uint64_t>(hi) << 32) | lo;
+  return static_cast<unsigned int>(v >> (s & 31));
+}
 
 #include "morph_tile.cuh"
 #include "morph_col.cuh"
+#include "morph_row.cuh"
 
 // ---- TMA / mbarrier model ------------------------------------------------------
 struct EmuMap {
@@ -323,6 +329,12 @@ ColFnE pick_col(bool blk) {
   return blk ? col_tile<T, OP, true> : col_tile<T, OP, false>;
 }
 
+using RowFnE = bool (*)(const RowArgs&, const CUtensorMap*, int, const RowGeom&, uint8_t*, uint64_t*, uint32_t&);
+template <typename T, int OP>
+RowFnE pick_row(bool blk) {
+  return blk ? row_tile<T, OP, true> : row_tile<T, OP, false>;
+}
+
 static uint64_t splitmix(uint64_t& s) {
   uint64_t z = (s += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -409,7 +421,9 @@ int main() {
     memcpy(&tin, &mi, sizeof(mi));
     memcpy(&tout, &mo, sizeof(mo));
     const bool use_col = kern == 2 && L.wx == 1 && L.wy > 1;
-    const bool use_pipe = !use_col && pipe && a.tma_ld && gp.smem_bytes <= kMaxSmemBytes;
+    const RowGeom rg = row_geom(esz, L.wx, L.ax);
+    const bool use_row = kern == 3 && L.wy == 1 && L.wx > 1 && rg.smem <= kMaxSmemBytes;
+    const bool use_pipe = !use_col && !use_row && pipe && a.tma_ld && gp.smem_bytes <= kMaxSmemBytes;
     const Geom& g = use_pipe ? gp : g1;
     CtaFn fn = esz == 1 ? (op == 0 ? pick<uint8_t, 0>(L.cfg) : pick<uint8_t, 1>(L.cfg))
                         : (op == 0 ? pick<uint16_t, 0>(L.cfg) : pick<uint16_t, 1>(L.cfg));
@@ -474,7 +488,55 @@ int main() {
       }
       a.tma_ld = c.tma_ld;
     }
-    for (int c = 0; c < (use_col ? 0 : ncta); ++c) {
+    if (use_row) {
+      // the row kernel, launched as row_launch does
+      const bool blk = L.vhgw_row && L.wx >= 9;
+      RowArgs ra{};
+      ra.src = src;
+      ra.dst = dst;
+      ra.sp = sp;
+      ra.dp = dp;
+      ra.W = W;
+      ra.H = H;
+      ra.w = L.wx;
+      ra.a = L.ax;
+      ra.ntx = cdiv(W, rg.txp);
+      ra.nty = cdiv(H, rg.ty);
+      ra.blocked = blk;
+      ra.ld_vec = a.ld_vec;
+      ra.st_vec = (reinterpret_cast<uintptr_t>(dst) % (8 * esz) == 0) && (dp % (8 * esz) == 0);
+      ra.err = &errword;
+      ra.tma_ld = tma_ok(src, sp, 128 / esz, rg.ty);
+      EmuMap mr{src, nullptr, esz, W, H, sp, 128 / esz, rg.ty};
+      CUtensorMap tr{};
+      memcpy(&tr, &mr, sizeof(mr));
+      RowFnE rf = esz == 1 ? (op == 0 ? pick_row<uint8_t, 0>(blk) : pick_row<uint8_t, 1>(blk))
+                           : (op == 0 ? pick_row<uint16_t, 0>(blk) : pick_row<uint16_t, 1>(blk));
+      for (int t = 0; t < ra.ntx * ra.nty; ++t) {
+        EmuCta cta;
+        std::barrier<> bar(kRowThreads);
+        cta.bar = &bar;
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (rg.smem + 127) / 128 * 128));
+        cta.smem = sm;
+        cta.smem_size = rg.smem;
+        uint64_t mbar = 0;
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              uint32_t phase = 0;
+              if (tid == 0) mbar_init(&mbar, 1);
+              __syncthreads();
+              rf(ra, &tr, t, rg, sm, &mbar, phase);
+            },
+            kRowThreads);
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+      a.tma_ld = ra.tma_ld;
+    }
+    for (int c = 0; c < (use_col || use_row ? 0 : ncta); ++c) {
       const int bx = c % gx, by = c / gx;
       EmuCta cta;
       std::barrier<> bar(kThreads);
@@ -522,7 +584,7 @@ int main() {
     printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
            "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);
