@@ -244,6 +244,36 @@ int morph_set_pipeline(int mode);
 int morph_set_column_kernel(int mode);
 
 /*
+ * Kernel of the pass along y (1 x wy windows, and the first launch of the
+ * two-launch form): van Herk/Gil-Werman with blocks of wy rows (section
+ * 5.1.1), one warp per tile 128 bytes wide and `rows` output rows tall, the
+ * block suffix kept in place of the input rows it replaces.  mode 1: this
+ * kernel for every wy >= 2 whose warp tile fits in shared memory; -1
+ * (default): the library's choice, at present the column kernel of
+ * morph_set_column_kernel (measured faster on the GB300); 0: never.  rows:
+ * output rows per warp tile, 1 to 1024 (rounded up to a multiple of 8), or 0
+ * for the launch-shape model's choice.  The result never changes.
+ * MORPH_ERR_ARG for another mode or rows.
+ */
+int morph_set_colv(int mode, int rows);
+
+/*
+ * Kernel of the pass along x (wx x 1 windows, and the second launch of the
+ * two-launch form): van Herk/Gil-Werman with blocks of 8 pixels (section
+ * 5.1.1's decomposition; the whole blocks inside a window folded from their
+ * totals), one warp per 8 rows and a segment of `seg` output columns, each
+ * lane's block transposed in registers (section 4) so that one packed
+ * min/max handles 8 rows.  Accepts 9 <= wx <= 256 when the source rows are
+ * aligned to 8 bytes (u8) or 16 bytes (u16).  mode 1: this kernel wherever
+ * it accepts the call; -1 (default): the library's choice, at present the
+ * row kernel of morph_set_row_kernel (measured faster on the GB300); 0:
+ * never.  seg: output columns per warp task, rounded up to a multiple of
+ * 256, or 0 for the launch-shape model's choice.  The result never changes.
+ * MORPH_ERR_ARG for another mode or seg.
+ */
+int morph_set_rowv(int mode, int seg);
+
+/*
  * Kernel for single-image calls whose window is wx x 1 (wx > 1), including
  * the second launch of the two-launch form: mode -1 (default) or 1: the row
  * kernel (tiles 256 bytes wide; 8 x 8-pixel blocks transposed once in
@@ -269,6 +299,15 @@ int morph_set_xpass(int dtype, int mode);
 
 /* Text for a morph_status value (static storage). */
 const char *morph_status_string(int status);
+
+/*
+ * Number of kernel launches the library has enqueued since it was loaded, on
+ * every device and stream (a launch captured into a CUDA graph counts once,
+ * when captured).  For accounting: a caller can read it before and after a
+ * call to learn how many kernels the call launched.  Never fails.  The paper
+ * has no counterpart.
+ */
+long long morph_launch_count(void);
 
 /*
  * Reads and clears the device error word that kernels set when a bounded wait

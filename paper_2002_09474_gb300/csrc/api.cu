@@ -1,6 +1,7 @@
 // C ABI (include/morph.h): argument checks, exact window clipping, method and
 // tile choice (section 5.3's crossover), launches, host staging.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -73,10 +74,21 @@ struct Scratch {
   }
 };
 
+// The warp-tiled pass along y and the register-blocked pass along x: used
+// when forced (mode 1) and they accept the launch; in auto mode (-1) only
+// where they were measured faster than the column and row kernels on the
+// GB300 -- at present nowhere.
+bool use_colv(const FusedLaunch& L) { return tuning().colv_mode == 1 && colv_fits(L); }
+bool use_rowv(const FusedLaunch& L) { return tuning().rowv_mode == 1 && rowv_fits(L); }
+
 int launch_one(FusedLaunch L, cudaStream_t stream) {
   if (!plan_single(&L)) return MORPH_ERR_WINDOW;
+  if (L.wx == 1 && L.wy > 1 && use_colv(L))
+    return colv_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   if (L.wx == 1 && L.wy > 1 && tuning().col_mode != 0)
     return col_launch(L, L.vhgw_col && L.wy >= 9, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+  if (L.wy == 1 && L.wx > 1 && use_rowv(L))
+    return rowv_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   if (L.wy == 1 && L.wx > 1 && tuning().row_mode != 0 && row_fits(L))
     return row_launch(L, L.vhgw_row && L.wx >= 9, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   return fused_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
@@ -149,6 +161,12 @@ int launch_planned(FusedLaunch L, cudaStream_t stream) {
   if (rc == MORPH_OK) rc = launch_one(B, stream);
   return rc;
 }
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int run_single(const void* src, size_t sp, void* dst, size_t dp, int W, int H, int dtype, int op, int wx,
                int wy, int ax, int ay, cudaStream_t stream) {
@@ -471,6 +489,20 @@ int morph_set_row_kernel(int mode) {
   return MORPH_OK;
 }
 
+int morph_set_colv(int mode, int rows) {
+  if (mode < -1 || mode > 1 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
+  tuning().colv_mode = mode;
+  tuning().colv_rows = rows;
+  return MORPH_OK;
+}
+
+int morph_set_rowv(int mode, int seg) {
+  if (mode < -1 || mode > 1 || seg < 0 || seg > (1 << 20)) return MORPH_ERR_ARG;
+  tuning().rowv_mode = mode;
+  tuning().rowv_seg = seg;
+  return MORPH_OK;
+}
+
 int morph_set_pipeline(int mode) {
   if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
   tuning().pipe_mode = mode;
@@ -537,6 +569,8 @@ const char* morph_status_string(int status) {
   }
   return "unknown status";
 }
+
+long long morph_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int morph_device_error(void) {
   if (cudaDeviceSynchronize() != cudaSuccess) return MORPH_ERR_CUDA;

@@ -174,6 +174,7 @@ cudaError_t batch_enqueue(const BatchHost& h, const BatchImage* d_imgs, const CU
   if (!k || h.grid < 1 || !h.err) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
+  note_launch();
   k<<<h.grid, kThreads, h.smem, stream>>>(d_imgs, d_maps, static_cast<int>(h.imgs.size()), h.ntiles, d_counter,
                                           h.err);
   return cudaGetLastError();
@@ -186,6 +187,7 @@ cudaError_t batch_enqueue_raw(int cfg, int smem, int grid, int* err, int nimg, i
   if (!k || grid < 1 || !err) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), stream);
   if (e != cudaSuccess) return e;
+  note_launch();
   k<<<grid, kThreads, smem, stream>>>(d_imgs, d_maps, nimg, ntiles, d_counter, err);
   return cudaGetLastError();
 }

@@ -89,6 +89,7 @@ cudaError_t col_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream) 
       opted[dev & 63][slot] = reinterpret_cast<const void*>(k);
     }
   }
+  note_launch();
   k<<<a.ntiles, kColThreads, g.smem, stream>>>(tin, a);
   return cudaGetLastError();
 }

@@ -166,6 +166,7 @@ cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
       if (e != cudaSuccess) return e;
       const int grid = persistent_grid(reinterpret_cast<const void*>(k), gp.smem_bytes, ntx * nty);
       if (grid > 0) {
+        note_launch();
         k<<<grid, kThreads, gp.smem_bytes, stream>>>(tin, tout, a, gp, ntx, ntx * nty);
         return cudaGetLastError();
       }
@@ -176,6 +177,7 @@ cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
   cudaError_t e = allow_smem(reinterpret_cast<const void*>(k));
   if (e != cudaSuccess) return e;
   dim3 grid(ntx, nty);
+  note_launch();
   k<<<grid, kThreads, g.smem_bytes, stream>>>(tin, tout, a, g);
   return cudaGetLastError();
 }

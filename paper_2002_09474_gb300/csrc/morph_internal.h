@@ -69,6 +69,9 @@ FusedPipeKernelFn fused_pipe_kernel_u8_dilate(int cfg);
 FusedPipeKernelFn fused_pipe_kernel_u16_erode(int cfg);
 FusedPipeKernelFn fused_pipe_kernel_u16_dilate(int cfg);
 
+// Counts one kernel launch enqueued by the library (morph_launch_count).
+void note_launch();
+
 // Enqueues the fused kernel; returns a cudaError_t.
 cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream);
 // Reads and clears the fused kernels' device error word.
@@ -79,6 +82,16 @@ int* device_error_word();
 // The column-pass kernel for 1 x wy windows (blocked: van Herk/Gil-Werman
 // blocks, needs wy >= 9; else the direct method).
 cudaError_t col_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream);
+
+// The warp-tiled van Herk/Gil-Werman kernel of the pass along y (any wy >= 2),
+// when its warp tile fits in shared memory (colv_fits).
+bool colv_fits(const FusedLaunch& L);
+cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream);
+
+// The register-blocked van Herk/Gil-Werman kernel of the pass along x
+// (9 <= wx <= 256, rows aligned to 8 * esz bytes; rowv_fits).
+bool rowv_fits(const FusedLaunch& L);
+cudaError_t rowv_launch(const FusedLaunch& L, cudaStream_t stream);
 
 // The row-pass kernel for wx x 1 windows (blocked needs wx >= 9), when its
 // tile fits in shared memory (row_fits).

@@ -1,0 +1,292 @@
+// Pass along x (a w x 1 element; the paper's "vertical pass", section 5.2) by
+// van Herk/Gil-Werman with 8-pixel blocks, one warp per 8 rows and a segment
+// of columns, the block data in registers.
+//
+// The warp walks its segment in chunks of 256 pixels.  In a chunk, lane l
+// owns block k = 32c + l: the 8 input columns whose pixels start the windows
+// of outputs x = xs + 8k .. xs + 8k + 7 (xs the segment's first output, so
+// the block starts at input column xs - a + 8k).  It loads the block's 8 rows
+// straight from global memory (each warp load reads 256 contiguous bytes of
+// one row) and transposes them in registers into 8 "octets", one per pixel
+// column, each four 32-bit words holding the 8 rows in 16-bit lanes -- the
+// paper's transpose of section 4, so that the pass along x becomes a pass
+// over registers, 8 rows per instruction pair.
+//
+// With q = (w - 1) div 8 and r = (w - 1) mod 8, output 8k + i takes the
+// window from offset i of block k to offset r + i of block k + q:
+//    out = op( S_k[i], T_{k+1} .. T_{k+q-1}, P_{k+q}[r + i] )
+// with S the suffix within block k, T a block's total and P_j[n] the prefix
+// of block j up to offset n (for n > 7: op(T_j, P_{j+1}[n - 8])).  This is
+// van Herk/Gil-Werman's suffix/prefix decomposition (section 5.1.1) with
+// blocks of 8 and the whole blocks between folded from their totals.  Every
+// lane writes its block's prefixes (the last one is its total) to a ring in
+// shared memory; the outputs of chunk c are made once chunk c + 1's
+// prefixes are there.  The suffix is scanned in registers, seeded with the
+// fold of the whole blocks.
+//
+// 8-bit pixels are widened by duplicating each byte into both halves of its
+// 16-bit lane (p * 257), which min/max.u16x2 preserve; the transposes do the
+// widening for free.  Needs w >= 9 (q >= 1) and w <= 256 (the window ends
+// within the next chunk), rows aligned to 8 bytes (u8) or 16 bytes (u16).
+#pragma once
+
+#include "morph_common.cuh"
+
+namespace morph {
+
+constexpr int kRvChunk = 256;  // pixels per chunk (32 lanes x 8)
+constexpr int kRvRing = 64;    // prefix ring: two chunks of blocks
+// Shared memory per warp: 8 prefix slots x kRvRing blocks x 16 bytes.
+constexpr int kRvWarpSmem = 8 * kRvRing * 16;
+
+struct RowvArgs {
+  const uint8_t* src;
+  uint8_t* dst;
+  long long sp, dp;  // pitches in bytes
+  int W, H;          // pixels
+  int w, a;          // window along x and its anchor, clipped to the image (9 <= w <= 256)
+  int seg;           // output columns per segment (multiple of 256)
+  int nseg;          // segments across: ceil(W / seg)
+  int ntask;         // warp tasks: ceil(H / 8) * nseg
+  int st_vec;        // 1: output rows allow aligned 8 * esz-byte stores
+};
+
+template <int OP>
+__device__ __forceinline__ uint4 rv_op(uint4 a, uint4 b) {
+  return OP == 0 ? make_uint4(__vminu2(a.x, b.x), __vminu2(a.y, b.y), __vminu2(a.z, b.z), __vminu2(a.w, b.w))
+                 : make_uint4(__vmaxu2(a.x, b.x), __vmaxu2(a.y, b.y), __vmaxu2(a.z, b.z), __vmaxu2(a.w, b.w));
+}
+__device__ __forceinline__ uint32_t rv_word(const uint4& v, int j) {
+  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+// 8 pixels of one row starting at pixel column B (any integer), as 8 * E
+// bytes in the low words of `o` (u8: o[0..1], u16: o[0..3]); pixels outside
+// [0, W) take the identity.  dl = B mod 8 (the same for every lane).
+template <typename T, int OP>
+__device__ __forceinline__ void rv_load_row(const uint8_t* row, int B, int dl, int W, uint32_t (&o)[4]) {
+  constexpr int E = sizeof(T);
+  const uint32_t IDW = ident_word<OP>();
+  const int B8 = B - dl;  // multiple of 8 pixels
+  if (B8 >= 0 && B8 + 16 <= W) {
+    if (E == 1) {
+      const uint2 x = *reinterpret_cast<const uint2*>(row + B8);
+      uint2 y = make_uint2(0u, 0u);
+      if (dl) y = *reinterpret_cast<const uint2*>(row + B8 + 8);
+      const int s = 8 * (dl & 3);
+      const uint32_t a0 = dl < 4 ? x.x : x.y, a1 = dl < 4 ? x.y : y.x, a2 = dl < 4 ? y.x : y.y;
+      o[0] = __funnelshift_r(a0, a1, s);
+      o[1] = __funnelshift_r(a1, a2, s);
+      o[2] = o[3] = 0u;
+    } else {
+      const uint4 x = *reinterpret_cast<const uint4*>(row + 2 * B8);
+      uint4 y = make_uint4(0u, 0u, 0u, 0u);
+      if (dl) y = *reinterpret_cast<const uint4*>(row + 2 * B8 + 16);
+      const int s = 16 * (dl & 1);
+      uint32_t v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+      // shift by dl/2 words (uniform), then by s bits
+      switch (dl >> 1) {
+        case 0:
+#pragma unroll
+          for (int h = 0; h < 4; ++h) o[h] = __funnelshift_r(v[h], v[h + 1], s);
+          break;
+        case 1:
+#pragma unroll
+          for (int h = 0; h < 4; ++h) o[h] = __funnelshift_r(v[h + 1], v[h + 2], s);
+          break;
+        case 2:
+#pragma unroll
+          for (int h = 0; h < 4; ++h) o[h] = __funnelshift_r(v[h + 2], v[h + 3], s);
+          break;
+        default:
+#pragma unroll
+          for (int h = 0; h < 4; ++h) o[h] = __funnelshift_r(v[h + 3], v[h + 4], s);
+          break;
+      }
+    }
+  } else {
+    o[0] = o[1] = o[2] = o[3] = IDW;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int x = B + t;
+      if (x >= 0 && x < W) {
+        const uint32_t v = reinterpret_cast<const T*>(row)[x];
+        const int wi = t * E / 4, sh = 8 * ((t * E) & 3);
+        const uint32_t m = (E == 1 ? 0xFFu : 0xFFFFu) << sh;
+        o[wi] = (o[wi] & ~m) | (v << sh);
+      }
+    }
+  }
+}
+
+// Loads block k (8 rows from y0, 8 pixels from column B) and transposes it:
+// V[p] = pixel column p, word j = rows 2j (low lane) and 2j+1 (high lane).
+template <typename T, int OP>
+__device__ __forceinline__ void rv_load_block(const RowvArgs& a, int y0, int B, int dl, uint4 (&V)[8]) {
+  constexpr int E = sizeof(T);
+  uint32_t R[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    if (y0 + r < a.H) {
+      rv_load_row<T, OP>(a.src + static_cast<long long>(y0 + r) * a.sp, B, dl, a.W, R[r]);
+    } else {
+      R[r][0] = R[r][1] = R[r][2] = R[r][3] = ident_word<OP>();
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    uint32_t wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (E == 1) {
+        // bytes p%4 of rows 2j and 2j+1, each duplicated into its 16-bit lane
+        const uint32_t sel = (p & 3) * 0x11u + (4 + (p & 3)) * 0x1100u;
+        wv[j] = __byte_perm(R[2 * j][p >> 2], R[2 * j + 1][p >> 2], sel);
+      } else {
+        wv[j] = __byte_perm(R[2 * j][p >> 1], R[2 * j + 1][p >> 1], (p & 1) ? 0x7632u : 0x5410u);
+      }
+    }
+    V[p] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+  }
+}
+
+// Writes the 8 x 8 output block (octets O) at rows y0.., columns x..
+// (columns < xe), transposed back to rows.
+template <typename T>
+__device__ __forceinline__ void rv_store_block(const RowvArgs& a, int y0, int x, int xe, const uint4 (&O)[8]) {
+  constexpr int E = sizeof(T);
+  uint32_t Rw[8][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (E == 1) {
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const uint32_t A = __byte_perm(rv_word(O[4 * g], j), rv_word(O[4 * g + 1], j), 0x6240);
+        const uint32_t Bq = __byte_perm(rv_word(O[4 * g + 2], j), rv_word(O[4 * g + 3], j), 0x6240);
+        Rw[2 * j][g] = __byte_perm(A, Bq, 0x5410);
+        Rw[2 * j + 1][g] = __byte_perm(A, Bq, 0x7632);
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        Rw[2 * j][h] = __byte_perm(rv_word(O[2 * h], j), rv_word(O[2 * h + 1], j), 0x5410);
+        Rw[2 * j + 1][h] = __byte_perm(rv_word(O[2 * h], j), rv_word(O[2 * h + 1], j), 0x7632);
+      }
+    }
+  }
+  const bool full = a.st_vec && x + 8 <= xe;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    if (y0 + r >= a.H) break;
+    uint8_t* row = a.dst + static_cast<long long>(y0 + r) * a.dp;
+    if (full) {
+      if (E == 1)
+        *reinterpret_cast<uint2*>(row + x) = make_uint2(Rw[r][0], Rw[r][1]);
+      else
+        *reinterpret_cast<uint4*>(row + 2 * x) = make_uint4(Rw[r][0], Rw[r][1], Rw[r][2], Rw[r][3]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (x + t < xe)
+          reinterpret_cast<T*>(row)[x + t] = static_cast<T>(Rw[r][t * E / 4] >> (8 * ((t * E) & 3)));
+    }
+  }
+}
+
+// One warp task: rows 8 * (task / nseg) .. +7, output columns of segment
+// task % nseg.  pb: this warp's prefix ring (8 x kRvRing uint4, slot n of
+// block b at pb[n * kRvRing + b]).
+template <typename T, int OP>
+__device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane, uint4* pb) {
+  const int y0 = 8 * (task / a.nseg);
+  const int xs = (task % a.nseg) * a.seg;
+  const int xe = xs + a.seg < a.W ? xs + a.seg : a.W;
+  const int nck = (xe - xs + kRvChunk - 1) / kRvChunk;  // output chunks
+  const int X0 = xs - a.a;                                // input column of block 0
+  const int dl = ((X0 % 8) + 8) % 8;
+  const int q = (a.w - 1) >> 3, r = (a.w - 1) & 7;
+  const uint32_t IDW = ident_word<OP>();
+  const uint4 ID4 = make_uint4(IDW, IDW, IDW, IDW);
+
+  uint4 Vc[8], Vn[8];
+  auto prefixes = [&](const uint4 (&V)[8], int k) {
+    const int b = k & (kRvRing - 1);
+    uint4 P = V[0];
+    pb[b] = P;
+#pragma unroll
+    for (int n = 1; n < 8; ++n) {
+      P = rv_op<OP>(P, V[n]);
+      pb[n * kRvRing + b] = P;
+    }
+  };
+  rv_load_block<T, OP>(a, y0, X0 + 8 * lane, dl, Vc);
+  prefixes(Vc, lane);
+  for (int c = 0; c < nck; ++c) {
+    const int k = 32 * c + lane;
+    // the next chunk (its prefixes close the windows of this one)
+    rv_load_block<T, OP>(a, y0, X0 + 8 * (k + 32), dl, Vn);
+    prefixes(Vn, k + 32);
+    __syncwarp();
+    // fold of the whole blocks k+1 .. k+q-1
+    uint4 m = ID4;
+    for (int j = 1; j < q; ++j) m = rv_op<OP>(m, pb[7 * kRvRing + ((k + j) & (kRvRing - 1))]);
+    // suffixes of block k, seeded with m
+    uint4 S[8];
+    S[7] = rv_op<OP>(Vc[7], m);
+#pragma unroll
+    for (int i = 6; i >= 0; --i) S[i] = rv_op<OP>(Vc[i], S[i + 1]);
+    const int bq = (k + q) & (kRvRing - 1), bq1 = (k + q + 1) & (kRvRing - 1);
+    const uint4 Tq = pb[7 * kRvRing + bq];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int n = r + i;
+      const uint4 Pv = n < 8 ? pb[n * kRvRing + bq] : rv_op<OP>(Tq, pb[(n - 8) * kRvRing + bq1]);
+      S[i] = rv_op<OP>(S[i], Pv);
+    }
+    const int x = xs + 8 * k;
+    if (x < xe) rv_store_block<T>(a, y0, x, xe, S);
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 8; ++p) Vc[p] = Vn[p];
+  }
+}
+
+// Launch shape: segment length (a multiple of 256) and warp tasks.  Each task
+// costs its output chunks plus one look-ahead chunk (loads, transposes and
+// prefixes only: about 0.45 of an output chunk); tasks run in waves of
+// (SMs x resident warps); an SM issues at full rate only with about 8 warps.
+struct RowvPlan {
+  int seg, nseg, ntask;
+  bool ok;
+};
+inline RowvPlan rowv_plan(int W, int H, int sms, int wps, int forced_seg) {
+  RowvPlan best{0, 0, 0, false};
+  if (W < 1 || H < 1 || sms < 1) return best;
+  const int wmax = (W + kRvChunk - 1) / kRvChunk * kRvChunk;
+  int want = 0;  // a forced segment length, at most the image's width
+  if (forced_seg > 0) {
+    want = (forced_seg + kRvChunk - 1) / kRvChunk * kRvChunk;
+    if (want > wmax) want = wmax;
+  }
+  double best_cost = 1e300;
+  for (int seg = kRvChunk; seg <= wmax; seg += kRvChunk) {
+    if (want > 0 && seg != want) continue;
+    const int nseg = (W + seg - 1) / seg;
+    const long long ntask = static_cast<long long>((H + 7) / 8) * nseg;
+    if (ntask > (1ll << 30)) continue;
+    const double per_sm = static_cast<double>(ntask) / sms;
+    const double waves = static_cast<double>(static_cast<long long>((per_sm + wps - 1) / wps));
+    const double busy = per_sm < wps ? per_sm : wps;
+    const double chunks = (seg < W ? seg : W) / static_cast<double>(kRvChunk);
+    const double work = chunks + 0.45 + 0.1;
+    const double eff = busy >= 8 ? 1.0 : busy / 8.0;
+    const double cost = waves * work / eff;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = RowvPlan{seg, nseg, static_cast<int>(ntask), true};
+    }
+  }
+  return best;
+}
+
+}  // namespace morph

@@ -78,6 +78,10 @@ void reset_tuning_defaults() {
   g_tuning.pipe_mode = -1;
   g_tuning.col_mode = -1;
   g_tuning.row_mode = -1;
+  g_tuning.colv_mode = -1;
+  g_tuning.colv_rows = 0;
+  g_tuning.rowv_mode = -1;
+  g_tuning.rowv_seg = 0;
   g_tuning.from_autotune = 0;
   g_init = true;
 }

@@ -17,6 +17,10 @@ struct Tuning {
   int xpass_transpose[2];         // [esz-1]: pass along x through the transpose kernels (1) or fused (0)
   int col_mode;                   // 1 x wy windows by the column kernel: -1 auto (yes), 0 never, 1 always
   int row_mode;                   // wx x 1 windows by the row kernel: -1 auto (yes), 0 never, 1 always
+  int colv_mode;                  // 1 x wy passes by the warp-tiled vHGW kernel: -1 auto, 0 never, 1 always
+  int colv_rows;                  // its output rows per warp tile (0: launch-shape model)
+  int rowv_mode;                  // wx x 1 passes by the register-blocked vHGW kernel: -1 auto, 0 never, 1 always
+  int rowv_seg;                   // its output columns per warp segment (0: launch-shape model)
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 

@@ -77,6 +77,7 @@ cudaError_t row_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream) 
       opted[dev & 63][slot] = reinterpret_cast<const void*>(k);
     }
   }
+  note_launch();
   k<<<a.ntx * a.nty, kRowThreads, g.smem, stream>>>(tin, a, g);
   return cudaGetLastError();
 }

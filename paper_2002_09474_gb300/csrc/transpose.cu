@@ -134,10 +134,12 @@ cudaError_t transpose_launch(const void* src, long long sp, void* dst, long long
   if (esz == 1) {
     TrArgs<uint8_t> a{static_cast<const uint8_t*>(src), static_cast<uint8_t*>(dst), sp, dp, W, H,
                       (s % 16 == 0) && (sp % 16 == 0), (d % 4 == 0) && (dp % 4 == 0)};
+    note_launch();
     transpose_kernel<uint8_t><<<grid, kTThreads, 0, stream>>>(a);
   } else {
     TrArgs<uint16_t> a{static_cast<const uint8_t*>(src), static_cast<uint8_t*>(dst), sp, dp, W, H,
                        (s % 16 == 0) && (sp % 16 == 0), (d % 8 == 0) && (dp % 8 == 0)};
+    note_launch();
     transpose_kernel<uint16_t><<<grid, kTThreads, 0, stream>>>(a);
   }
   return cudaGetLastError();

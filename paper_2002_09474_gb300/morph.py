@@ -78,22 +78,26 @@ _SIGS = {
     "morph_set_pipeline": [_i32],
     "morph_set_column_kernel": [_i32],
     "morph_set_row_kernel": [_i32],
+    "morph_set_colv": [_i32, _i32],
+    "morph_set_rowv": [_i32, _i32],
     "morph_set_xpass": [_i32, _i32],
     "morph_device_error": [],
+    "morph_launch_count": [],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name, None)
     if _f is None:
         continue
     _f.argtypes = _args
-    _f.restype = ctypes.c_char_p if _name == "morph_status_string" else ctypes.c_int
+    _f.restype = (ctypes.c_char_p if _name == "morph_status_string" else
+                  ctypes.c_longlong if _name == "morph_launch_count" else ctypes.c_int)
 
 
 def declared_functions() -> list[str]:
     """Names of the functions include/morph.h declares."""
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(",
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:long\s+long|[a-z_0-9]+)\s*\*?\s*([a-z_0-9]+)\s*\(",
                                  text, flags=re.M)))
 
 
@@ -195,6 +199,18 @@ def morph_set_column_kernel(mode):
 
 def morph_set_row_kernel(mode):
     return _lib.morph_set_row_kernel(mode)
+
+
+def morph_set_colv(mode, rows=0):
+    return _lib.morph_set_colv(mode, rows)
+
+
+def morph_launch_count():
+    return _lib.morph_launch_count()
+
+
+def morph_set_rowv(mode, seg=0):
+    return _lib.morph_set_rowv(mode, seg)
 
 
 def morph_set_xpass(dtype, mode):

@@ -4,7 +4,9 @@ Prints one case per line: esz op W H spad soff dpad doff wx wy ax ay cfg
 cross_x cross_y seed kern.  Every case whose source is TMA-loadable (16-byte
 pitch and offset) also appears in the persistent two-slot form (kern 1), and
 every 1 x wy case (wy > 1) also through the column kernel (kern 2), every
-wx x 1 case (wx > 1) also through the row kernel (kern 3)."""
+wx x 1 case (wx > 1) also through the row kernel (kern 3), and every 1 x wy
+case also through the warp-tiled van Herk/Gil-Werman kernel of the pass
+along y (kern 4).  --only K keeps the cases of kernel K."""
 import itertools
 import sys
 
@@ -100,9 +102,45 @@ def cases(full=True):
                             seed += 1
     for c in row:
         both.append(c + (3,))
+    # the warp-tiled pass along y: every 1 x wy case, plus tall images, long
+    # windows, anchor extremes, unaligned pitches and offsets
+    colv = [c for c in out if c[8] == 1 and c[9] > 1]
+    for esz in (1, 2):
+        for (w, h) in ((128, 1000), (300, 2100), (64, 700), (1, 900), (257, 33), (190, 41)):
+            for wy in (2, 3, 7, 8, 9, 16, 17, 31, 63, 101, 255, 700):
+                for ay in sorted({0, wy // 2, wy - 1}):
+                    for op in (0, 1):
+                        n = len(colv)
+                        if n % 3 == 0:
+                            pad, off, dpad, doff = aligned_pad(w, esz), 0, aligned_pad(w, esz), 0
+                        elif n % 3 == 1:
+                            pad, off, dpad, doff = 0, 0, 0, 0
+                        else:
+                            pad, off, dpad, doff = 3 * esz, esz, 5 * esz, 2 * esz
+                        colv.append((esz, op, w, h, pad, off, dpad, doff, 1, wy, 0, ay, -1, -1, -1, seed))
+                        seed += 1
+    for c in colv:
+        both.append(c + (4,))
+    # the register-blocked pass along x: the row kernel's cases, plus aligned
+    # rows (so that the kernel takes them) of ragged widths and heights
+    rowv = [c for c in row if 9 <= c[8] <= 256]
+    for esz in (1, 2):
+        for (w, h) in ((256, 64), (257, 65), (1000, 70), (2100, 9), (1500, 130), (513, 13), (40, 20)):
+            for wx in (9, 10, 16, 17, 31, 63, 101, 127, 255, 256):
+                for ax in sorted({0, wx // 2, wx - 1}):
+                    for op in (0, 1):
+                        n = len(rowv)
+                        pad = (16 - (w * esz) % 16) % 16
+                        dpad, doff = (pad, 0) if n % 2 else (esz, 3 * esz)
+                        rowv.append((esz, op, w, h, pad, 0, dpad, doff, wx, 1, ax, 0, -1, -1, -1, seed))
+                        seed += 1
+    for c in rowv:
+        both.append(c + (5,))
     return both
 
 
 if __name__ == "__main__":
+    only = int(sys.argv[sys.argv.index("--only") + 1]) if "--only" in sys.argv else None
     for c in cases(full="--quick" not in sys.argv):
-        print(*c)
+        if only is None or c[-1] == only:
+            print(*c)

@@ -18,12 +18,18 @@
 // per tile, 1 = the persistent two-slot kernel with 3 CTAs when the input is
 // TMA-loadable, 2 = the column kernel for 1 x wy windows, its tile height
 // planned for 152 SMs on odd seeds and 3 SMs on even ones, 3 = the row
-// kernel for wx x 1 windows).
+// kernel for wx x 1 windows, 4 = the warp-tiled van Herk/Gil-Werman kernel
+// of the pass along y for 1 x wy windows, its tile height planned for 152
+// SMs on odd seeds and 3 SMs on even ones, 5 = the register-blocked van
+// Herk/Gil-Werman kernel of the pass along x for wx x 1 windows, when the
+// source rows allow it, its segment planned for 152 SMs on odd seeds and 3
+// SMs on even ones).
 // Output: one line per case, "OK ..." or "FAIL ...".
 #define MORPH_HOST_EMU 1
 
 #include <atomic>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <barrier>
 #include <chrono>
@@ -46,6 +52,7 @@ thread_local uint3 emu_threadIdx;
 
 struct EmuCta {
   std::barrier<>* bar = nullptr;
+  std::barrier<>* wbar[8] = {};  // one per warp (__syncwarp)
   std::atomic<int> orflag{0};
   // mbarriers by address: a phase completes when its arrivals are in and
   // its transaction count is back to zero; the phase bit then flips.
@@ -69,6 +76,7 @@ static void emu_error(const char* what) {
 }
 
 static inline void __syncthreads() { g_cta->bar->arrive_and_wait(); }
+static inline void __syncwarp() { g_cta->wbar[threadIdx.x >> 5]->arrive_and_wait(); }
 static inline int __syncthreads_or(int p) {
   if (p) g_cta->orflag.store(1);
   g_cta->bar->arrive_and_wait();
@@ -110,6 +118,8 @@ static inline unsigned int __funnelshift_r(unsigned int lo, unsigned int hi, uns
 #include "morph_tile.cuh"
 #include "morph_col.cuh"
 #include "morph_row.cuh"
+#include "morph_colv.cuh"
+#include "morph_rowv.cuh"
 
 // ---- TMA / mbarrier model ------------------------------------------------------
 struct EmuMap {
@@ -488,6 +498,128 @@ int main() {
       }
       a.tma_ld = c.tma_ld;
     }
+    const bool use_colv = kern == 4 && L.wx == 1 && L.wy > 1;
+    if (use_colv) {
+      // the warp-tiled pass along y, planned and launched as colv_launch does
+      const ColvPlan p = colv_plan(esz, W, H, L.wy, (seed & 1) ? 152 : 3, kMaxSmemBytes, 0);
+      if (!p.ok) {
+        printf("FAIL case %d: no colv plan\n", cases);
+        ++failures;
+        continue;
+      }
+      col_ty = p.L;
+      ColvArgs c{};
+      c.src = src;
+      c.dst = dst;
+      c.sp = sp;
+      c.dp = dp;
+      c.W = W;
+      c.H = H;
+      c.w = L.wy;
+      c.a = L.ay;
+      c.L = p.L;
+      c.nbox = p.nbox;
+      c.ns = cdiv(W * esz, kCvBytes);
+      c.ntask = p.ntask;
+      c.wpc = p.wpc;
+      c.ld_vec = a.ld_vec;
+      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
+      c.err = &errword;
+      c.tma_ld = tma_ok(src, sp, kCvBytes / esz, kCvBox);
+      EmuMap mc{src, nullptr, esz, W, H, sp, kCvBytes / esz, kCvBox};
+      CUtensorMap tc{};
+      memcpy(&tc, &mc, sizeof(mc));
+      using VFn = bool (*)(const ColvArgs&, const CUtensorMap*, int, int, uint8_t*, uint64_t*);
+      VFn vf = esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0> : colv_tile<uint8_t, 1>)
+                        : (op == 0 ? colv_tile<uint16_t, 0> : colv_tile<uint16_t, 1>);
+      const int nthr = 32 * c.wpc;
+      for (int blk = 0; blk < cdiv(c.ntask, c.wpc); ++blk) {
+        EmuCta cta;
+        std::barrier<> bar(nthr);
+        cta.bar = &bar;
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (p.smem + 127) / 128 * 128));
+        cta.smem = sm;
+        cta.smem_size = p.smem;
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              const int warp = tid >> 5, lane = tid & 31, task = blk * c.wpc + warp;
+              if (task >= c.ntask) return;
+              uint8_t* tile = sm + warp * colv_tile_bytes(c.nbox);
+              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.wpc * colv_tile_bytes(c.nbox)) + warp * kCvMaxBox;
+              if (c.tma_ld && lane == 0)
+                for (int b = 0; b < c.nbox; ++b) mbar_init(&bars[b], 1);
+              // lanes wait on the barriers only after lane 0 initialised them
+              // (a warp-wide __syncwarp in the kernel)
+              while (c.tma_ld && lane != 0) {
+                bool ready;
+                {
+                  std::lock_guard<std::mutex> l(g_cta->mu);
+                  ready = g_cta->mbars.count(&bars[c.nbox - 1]) != 0;
+                }
+                if (ready) break;
+                std::this_thread::yield();
+              }
+              vf(c, &tc, task, lane, tile, bars);
+            },
+            nthr);
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+      a.tma_ld = c.tma_ld;
+    }
+    const int ral = 8 * esz;
+    const bool use_rowv = kern == 5 && L.wy == 1 && L.wx >= 9 && L.wx <= 256 &&
+                          reinterpret_cast<uintptr_t>(src) % ral == 0 && sp % ral == 0;
+    if (use_rowv) {
+      const RowvPlan p = rowv_plan(W, H, (seed & 1) ? 152 : 3, 16, 0);
+      col_ty = p.seg;
+      RowvArgs ra{};
+      ra.src = src;
+      ra.dst = dst;
+      ra.sp = sp;
+      ra.dp = dp;
+      ra.W = W;
+      ra.H = H;
+      ra.w = L.wx;
+      ra.a = L.ax;
+      ra.seg = p.seg;
+      ra.nseg = p.nseg;
+      ra.ntask = p.ntask;
+      ra.st_vec = (reinterpret_cast<uintptr_t>(dst) % ral == 0) && (dp % ral == 0);
+      using RvFn = void (*)(const RowvArgs&, int, int, uint4*);
+      RvFn rf = esz == 1 ? (op == 0 ? rowv_task<uint8_t, 0> : rowv_task<uint8_t, 1>)
+                         : (op == 0 ? rowv_task<uint16_t, 0> : rowv_task<uint16_t, 1>);
+      const int wpc = 4;
+      for (int blk = 0; blk < cdiv(p.ntask, wpc); ++blk) {
+        EmuCta cta;
+        std::barrier<> bar(32 * wpc);
+        std::vector<std::unique_ptr<std::barrier<>>> wb;
+        for (int w = 0; w < wpc; ++w) {
+          wb.emplace_back(new std::barrier<>(32));
+          cta.wbar[w] = wb.back().get();
+        }
+        cta.bar = &bar;
+        const size_t smb = static_cast<size_t>(wpc) * kRvWarpSmem;
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, smb));
+        cta.smem = sm;
+        cta.smem_size = smb;
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              const int warp = tid >> 5, lane = tid & 31, task = blk * wpc + warp;
+              if (task >= p.ntask) return;
+              rf(ra, task, lane, reinterpret_cast<uint4*>(sm + warp * kRvWarpSmem));
+            },
+            32 * wpc);
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+    }
     if (use_row) {
       // the row kernel, launched as row_launch does
       const bool blk = L.vhgw_row && L.wx >= 9;
@@ -536,7 +668,7 @@ int main() {
       }
       a.tma_ld = ra.tma_ld;
     }
-    for (int c = 0; c < (use_col || use_row ? 0 : ncta); ++c) {
+    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv ? 0 : ncta); ++c) {
       const int bx = c % gx, by = c / gx;
       EmuCta cta;
       std::barrier<> bar(kThreads);
@@ -584,7 +716,7 @@ int main() {
     printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
            "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_rowv ? 5 : use_colv ? 4 : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);
