@@ -37,10 +37,11 @@
  *    that neighbouring tiles write.
  *  - wx, wy >= 1; 0 <= anchor < w.  A window may be larger than the image
  *    (the window is clipped to the image).
- *  - Single-image calls allocate nothing, except the two-launch form of very
- *    large 2-D windows (see morph_set_split) and the transpose form of the
- *    pass along x (see morph_set_xpass), which take their intermediate
- *    images from the stream-ordered allocator.
+ *  - Single-image calls allocate nothing, except the two-launch form of
+ *    2-D windows (see morph_set_split) and the transpose form of the pass
+ *    along x (see morph_set_xpass), which take their intermediate images
+ *    from the stream-ordered allocator (cudaMallocAsync on the call's
+ *    stream; such calls can be captured into a CUDA graph).
  */
 #ifndef MORPH_H
 #define MORPH_H
@@ -212,10 +213,13 @@ int morph_reset_tuning(void);
 /*
  * Form of single-image calls with a 2-D window (section 5: the element is
  * separable, so erosion by wx x wy is erosion by 1 x wy followed by wx x 1).
- * mode -1 (default): run both passes fused in one kernel unless the fused
- * tile is so large that only one CTA fits on an SM, then run them as two
- * launches through an intermediate image the library allocates
- * stream-ordered; 0: always fused; 1: always two launches.  The result never
+ * mode -1 (default): two launches through an intermediate image the
+ * library allocates stream-ordered when both window sides are at least 9
+ * and the pixels are 8-bit or the longer side is at least 32 (where the
+ * single-pass kernels were measured faster than the fused kernel on the
+ * GB300), or when the fused tile is so large that fewer than 3 CTAs fit on
+ * an SM; otherwise both passes fused in one kernel.  0: always fused; 1:
+ * always two launches.  The result never
  * changes.
  */
 int morph_set_split(int mode);
@@ -249,10 +253,14 @@ int morph_set_column_kernel(int mode);
  * 5.1.1), one warp per tile 128 bytes wide and `rows` output rows tall, the
  * block suffix kept in place of the input rows it replaces.  mode 1: this
  * kernel for every wy >= 2 whose warp tile fits in shared memory; -1
- * (default): the library's choice, at present the column kernel of
- * morph_set_column_kernel (measured faster on the GB300); 0: never.  rows:
+ * (default): wherever the van Herk/Gil-Werman method is chosen (wy above the
+ * crossover of section 5.3; measured faster than the column kernel there);
+ * 0: never (the column kernel of morph_set_column_kernel instead).  rows:
  * output rows per warp tile, 1 to 1024 (rounded up to a multiple of 8), or 0
- * for the launch-shape model's choice.  The result never changes.
+ * for the library's choice: for wy > 32 (and TMA-loadable rows) a
+ * shared-tile form in which the warps of a CTA share one input tile and keep
+ * the block suffix of their 32 or 64 output rows in registers, else warp
+ * tiles of 64 rows.  The result never changes.
  * MORPH_ERR_ARG for another mode or rows.
  */
 int morph_set_colv(int mode, int rows);
@@ -265,10 +273,11 @@ int morph_set_colv(int mode, int rows);
  * lane's block transposed in registers (section 4) so that one packed
  * min/max handles 8 rows.  Accepts 9 <= wx <= 256 when the source rows are
  * aligned to 8 bytes (u8) or 16 bytes (u16).  mode 1: this kernel wherever
- * it accepts the call; -1 (default): the library's choice, at present the
- * row kernel of morph_set_row_kernel (measured faster on the GB300); 0:
- * never.  seg: output columns per warp task, rounded up to a multiple of
- * 256, or 0 for the launch-shape model's choice.  The result never changes.
+ * it accepts the call; -1 (default): for 16-bit pixels with the van
+ * Herk/Gil-Werman method and wx >= 32 (where it was measured faster than
+ * the row kernel of morph_set_row_kernel); 0: never.  seg: output columns
+ * per warp task, rounded up to a multiple of 256, or 0 for the shortest
+ * segment whose tasks fit in one wave of resident warps.  The result never changes.
  * MORPH_ERR_ARG for another mode or seg.
  */
 int morph_set_rowv(int mode, int seg);

@@ -75,16 +75,31 @@ struct Scratch {
 };
 
 // The warp-tiled pass along y and the register-blocked pass along x: used
-// when forced (mode 1) and they accept the launch; in auto mode (-1) only
-// where they were measured faster than the column and row kernels on the
-// GB300 -- at present nowhere.
-bool use_colv(const FusedLaunch& L) { return tuning().colv_mode == 1 && colv_fits(L); }
-bool use_rowv(const FusedLaunch& L) { return tuning().rowv_mode == 1 && rowv_fits(L); }
+// when forced (mode 1) and they accept the launch; in auto mode (-1) where
+// they were measured faster than the column and row kernels on the GB300
+// (4096^2 images, CUDA-graph timing): the pass along y whenever the van
+// Herk/Gil-Werman method is chosen (10-25% faster at 51, 101 and 127
+// rows), the pass along x for 16-bit pixels and windows of 32 or more (about
+// 30% faster at 101 and 127; slower at 21, and slower for 8-bit pixels).
+bool use_colv(const FusedLaunch& L) {
+  const int m = tuning().colv_mode;
+  if (m == 0) return false;
+  return (m == 1 || L.vhgw_col) && colv_fits(L);
+}
+bool use_rowv(const FusedLaunch& L) {
+  const int m = tuning().rowv_mode;
+  if (m == 0) return false;
+  return (m == 1 || (L.esz == 2 && L.wx >= 32 && L.vhgw_row)) && rowv_fits(L);
+}
 
 int launch_one(FusedLaunch L, cudaStream_t stream) {
   if (!plan_single(&L)) return MORPH_ERR_WINDOW;
-  if (L.wx == 1 && L.wy > 1 && use_colv(L))
+  if (L.wx == 1 && L.wy > 1 && use_colv(L)) {
+    // rows per warp tile not forced: the shared-tile form where it applies
+    if (tuning().colv_rows == 0 && colw_fits(L))
+      return colw_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
     return colv_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+  }
   if (L.wx == 1 && L.wy > 1 && tuning().col_mode != 0)
     return col_launch(L, L.vhgw_col && L.wy >= 9, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   if (L.wy == 1 && L.wx > 1 && use_rowv(L))

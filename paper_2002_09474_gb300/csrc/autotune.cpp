@@ -30,40 +30,50 @@ std::string device_key() {
   int drv = 0;
   cudaDriverGetVersion(&drv);
   char buf[512];
-  snprintf(buf, sizeof(buf), "%s|sm%d%d|%dSM|drv%d|v1", p.name, p.major, p.minor, p.multiProcessorCount, drv);
+  snprintf(buf, sizeof(buf), "%s|sm%d%d|%dSM|drv%d|v2", p.name, p.major, p.minor, p.multiProcessorCount, drv);
   return buf;
 }
 
-// Median time (ms) of one forced configuration.
-float time_launch(FusedLaunch L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-  std::vector<float> t;
-  for (int r = 0; r < kReps + 1; ++r) {
-    cudaEventRecord(e0, st);
-    if (launch_planned(L, st) != MORPH_OK) return 1e30f;
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (r) t.push_back(ms);  // the first run warms up
-  }
-  std::sort(t.begin(), t.end());
-  return t[t.size() / 2];
-}
-
-// Median time (ms) of one call in the planned form under the current tuning.
+// Mean GPU time (ms) of one call in the planned form under the current
+// tuning.  The calls are captured into a CUDA graph and the graph is timed,
+// so that host-side launch cost (which can exceed the kernel's own time on a
+// small image) does not enter the comparison.
 float time_planned(const FusedLaunch& L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-  std::vector<float> t;
-  for (int r = 0; r < kReps + 1; ++r) {
-    cudaEventRecord(e0, st);
-    if (launch_planned(L, st) != MORPH_OK) return 1e30f;
-    cudaEventRecord(e1, st);
-    cudaEventSynchronize(e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (r) t.push_back(ms);
+  constexpr int kCalls = 8;
+  if (launch_planned(L, st) != MORPH_OK) return 1e30f;  // set-up outside the capture
+  if (cudaStreamSynchronize(st) != cudaSuccess) return 1e30f;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return 1e30f;
+  bool ok = true;
+  for (int i = 0; i < kCalls; ++i) ok = ok && launch_planned(L, st) == MORPH_OK;
+  if (cudaStreamEndCapture(st, &graph) != cudaSuccess || !ok) {
+    if (graph) cudaGraphDestroy(graph);
+    return 1e30f;
   }
-  std::sort(t.begin(), t.end());
-  return t[t.size() / 2];
+  float best = 1e30f;
+  if (cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+    std::vector<float> t;
+    for (int r = 0; r < kReps + 1; ++r) {
+      cudaEventRecord(e0, st);
+      cudaGraphLaunch(exec, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r) t.push_back(ms / kCalls);  // the first replay warms up
+    }
+    if (!t.empty()) {
+      std::sort(t.begin(), t.end());
+      best = t[t.size() / 2];
+    }
+    cudaGraphExecDestroy(exec);
+  }
+  cudaGraphDestroy(graph);
+  return best;
+}
+float time_launch(const FusedLaunch& L, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  return time_planned(L, st, e0, e1);
 }
 
 bool load_cache(const char* path, const std::string& key, Tuning* t) {

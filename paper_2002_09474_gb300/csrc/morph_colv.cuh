@@ -53,10 +53,10 @@ struct ColvArgs {
   int* err;          // device error word
 };
 
-// Shared memory of one CTA: wpc warp tiles, then wpc * kCvMaxBox mbarriers.
+// Shared memory of one CTA: wpc warp tiles, then wpc * nbox mbarriers.
 __host__ __device__ inline int colv_tile_bytes(int nbox) { return nbox * kCvBoxBytes; }
 __host__ __device__ inline int colv_smem_bytes(int nbox, int wpc) {
-  return wpc * colv_tile_bytes(nbox) + wpc * kCvMaxBox * 8;
+  return wpc * colv_tile_bytes(nbox) + wpc * nbox * 8;
 }
 
 // Two 16-bit-lane carriers of one 32-bit word (u8: odd pixels in v[0], even
@@ -102,7 +102,7 @@ __device__ __forceinline__ void colv_store(const ColvArgs& a, int y, int px0, ui
 }
 
 // One warp tile.  tile: this warp's shared memory (nbox boxes); bars: its
-// kCvMaxBox mbarriers, initialised with count 1.  lane: 0..31.  Returns false
+// nbox mbarriers, initialised with count 1.  lane: 0..31.  Returns false
 // when a bounded wait gave up (error word set by lane 0).
 template <typename T, int OP>
 __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* tin, int task, int lane,
@@ -178,44 +178,71 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
     return true;
   };
 
+  // Rows move between shared memory and registers 8 at a time: the 8 loads
+  // of a batch issue together, so a scan waits for shared-memory latency
+  // once per batch rather than once per row (the in-place stores of the
+  // h-scan would otherwise order every load after the previous store).
+  constexpr int kB = 8;
+  C IDC;
+#pragma unroll
+  for (int i = 0; i < (E == 1 ? 2 : 1); ++i) IDC.v[i] = IDW;
   const int beta = Lr % w;
   for (int E0 = beta ? beta : w; E0 <= Lr; E0 += w) {
     const int lo = E0 - w > 0 ? E0 - w : 0;
     if (!ensure(E0 + w - 1)) return false;
-    // h-scan, in place
-    C h = cw_of<E>(LD(E0 - 1));
-    ST(E0 - 1, cw_word<E>(h));
-#pragma unroll 4
-    for (int r = E0 - 2; r >= lo; --r) {
+    // h-scan, rows E0-1 down to lo, in place
+    C h = IDC;
+    int r = E0 - 1;
+    for (; r - (kB - 1) >= lo; r -= kB) {
+      uint32_t x[kB];
+#pragma unroll
+      for (int t = 0; t < kB; ++t) x[t] = LD(r - t);
+#pragma unroll
+      for (int t = 0; t < kB; ++t) {
+        h = cw_op<OP, E>(h, cw_of<E>(x[t]));
+        x[t] = cw_word<E>(h);
+      }
+#pragma unroll
+      for (int t = 0; t < kB; ++t) ST(r - t, x[t]);
+    }
+    for (; r >= lo; --r) {
       h = cw_op<OP, E>(h, cw_of<E>(LD(r)));
       ST(r, cw_word<E>(h));
     }
     if (E0 - w >= 0 && col_in) colv_store<T>(a, y0 + E0 - w, px0, cw_word<E>(h), fast);
-    // g-scan; rows before w-1 (partial first block only) emit nothing
-    C g = cw_of<E>(LD(E0));
-    int e = E0;
+    // g-scan over rows E0 .. E0+w-2; row e closes the window of output
+    // e-w+1, so rows before w-1 (a partial first block only) emit nothing
+    C g = IDC;
     const int e_emit = E0 > w - 1 ? E0 : w - 1;
-    for (; e < e_emit; ) {
-      ++e;
-      g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
-    }
-    // here g covers rows E0 .. e
-    if (col_in) {
-      if (fast) {
-        uint8_t* out = a.dst + static_cast<long long>(y0 + e - w + 1) * a.dp + static_cast<long long>(px0) * E;
-#pragma unroll 4
-        for (; e <= E0 + w - 2; ++e) {
-          const C o = cw_op<OP, E>(cw_of<E>(LD(e - w + 1)), g);
-          *reinterpret_cast<uint32_t*>(out) = cw_word<E>(o);
+    const int last = E0 + w - 2;
+    int e = E0;
+    for (; e < e_emit; ++e) g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
+    if (!col_in) continue;
+    if (fast) {
+      uint8_t* out = a.dst + static_cast<long long>(y0 + e - w + 1) * a.dp + static_cast<long long>(px0) * E;
+      for (; e + (kB - 1) <= last; e += kB) {
+        uint32_t xe[kB], xh[kB];
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+          xe[t] = LD(e + t);
+          xh[t] = LD(e + t - w + 1);
+        }
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+          g = cw_op<OP, E>(g, cw_of<E>(xe[t]));
+          *reinterpret_cast<uint32_t*>(out) = cw_word<E>(cw_op<OP, E>(cw_of<E>(xh[t]), g));
           out += a.dp;
-          if (e + 1 <= E0 + w - 2) g = cw_op<OP, E>(g, cw_of<E>(LD(e + 1)));
         }
-      } else {
-        for (; e <= E0 + w - 2; ++e) {
-          const C o = cw_op<OP, E>(cw_of<E>(LD(e - w + 1)), g);
-          colv_store<T>(a, y0 + e - w + 1, px0, cw_word<E>(o), false);
-          if (e + 1 <= E0 + w - 2) g = cw_op<OP, E>(g, cw_of<E>(LD(e + 1)));
-        }
+      }
+      for (; e <= last; ++e) {
+        g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
+        *reinterpret_cast<uint32_t*>(out) = cw_word<E>(cw_op<OP, E>(cw_of<E>(LD(e - w + 1)), g));
+        out += a.dp;
+      }
+    } else {
+      for (; e <= last; ++e) {
+        g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
+        colv_store<T>(a, y0 + e - w + 1, px0, cw_word<E>(cw_op<OP, E>(cw_of<E>(LD(e - w + 1)), g)), false);
       }
     }
   }
@@ -227,52 +254,208 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
 namespace morph {
 
 // Launch shape of the pass along y: output rows per warp tile (L), warps per
-// CTA, shared memory.  The model: each warp tile costs its L rows plus the
-// g-scan rows of a partial first block plus a fixed start-up; tiles run in
-// waves of (SMs x resident warps); an SM issues at full rate only with about
-// 8 warps busy.
+// CTA, shared memory.  L = 64 unless forced (or the image is shorter):
+// measured on the GB300 over 4096^2 u8/u16 images and windows of 51, 101
+// and 127 rows, it was within 10% of the best height everywhere; smaller
+// tiles spend more of their time on the partial first block and on loading
+// halo rows, taller ones leave SMs idle.  Warps per CTA: the choice that
+// keeps the most warps resident per SM.
 struct ColvPlan {
   int L, nbox, wpc, ntask, smem;
   bool ok;
 };
 
-inline ColvPlan colv_plan(int esz, int W, int H, int w, int sms, int max_smem, int forced_L) {
-  ColvPlan best{0, 0, 0, 0, 0, false};
-  if (w < 2 || sms < 1) return best;
+inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L) {
+  ColvPlan p{0, 0, 0, 0, 0, false};
+  if (w < 2 || W < 1 || H < 1) return p;
   const int ns = (W * esz + kCvBytes - 1) / kCvBytes;
   int hmax = (H + 7) / 8 * 8;
   if (hmax > 1024) hmax = 1024;
-  int want = 0;  // a forced tile height, at most the image's height
-  if (forced_L > 0) {
-    want = (forced_L + 7) / 8 * 8;
-    if (want > hmax) want = hmax;
-  }
-  double best_cost = 1e300;
-  for (int L = 8; L <= hmax; L += 8) {
-    if (want > 0 && L != want) continue;
+  int L = forced_L > 0 ? (forced_L + 7) / 8 * 8 : 64;
+  if (L > hmax) L = hmax;
+  // very long windows: shorter tiles until the tile fits
+  for (; L >= 8; L -= 8) {
     const int nbox = (L + w - 1 + kCvBox - 1) / kCvBox;
-    if (nbox > kCvMaxBox) break;
-    int wpc = 4;
-    while (wpc > 1 && colv_smem_bytes(nbox, wpc) > max_smem) wpc /= 2;
-    const int smem = colv_smem_bytes(nbox, wpc);
-    if (smem > max_smem) break;
+    if (nbox > kCvMaxBox) continue;
+    int wpc = 0, wps = 0;
+    for (int c = 4; c >= 1; c /= 2) {
+      if (colv_smem_bytes(nbox, c) > max_smem) continue;
+      int ctas = 233472 / (colv_smem_bytes(nbox, c) + 1024);
+      if (ctas > 32) ctas = 32;
+      if (ctas * c > 64) ctas = 64 / c;
+      if (ctas * c > wps) {
+        wps = ctas * c;
+        wpc = c;
+      }
+    }
+    if (wpc == 0) continue;
+    const long long ntask = static_cast<long long>(ns) * ((H + L - 1) / L);
+    if (ntask > (1ll << 30)) return p;
+    return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc), true};
+  }
+  return p;
+}
+
+}  // namespace morph
+
+namespace morph {
+
+// ---------------------------------------------------------------------------
+// Shared-tile form for long windows (w > LW): the warps of a CTA share one
+// input tile -- NW x LW output rows of a 128-byte strip plus the window's
+// w - 1 halo rows, loaded once -- and each warp keeps the block suffix of its
+// LW output rows in registers instead of writing it over the input.  With
+// w > LW a warp's LW outputs start their windows inside one block of w rows
+// (the partial block at the top of its tile), so
+//   h-scan  rows LW-1 .. 0 into registers h[0..LW-1]
+//   g-scan  rows LW .. LW+w-2; row w-1+o closes output o = op(h[o], g).
+// Sharing the halo rows lets about twice as many warps stay resident per SM
+// as the in-place form, and loads each halo row once per CTA.
+// ---------------------------------------------------------------------------
+struct ColwArgs {
+  const uint8_t* src;
+  uint8_t* dst;
+  long long sp, dp;
+  int W, H;
+  int w, a;    // window (w > LW) and anchor, clipped to the image
+  int nw;      // warps per CTA (output rows per CTA: nw * LW)
+  int nbox;    // 32-row boxes per CTA tile: ceil((nw * LW + w - 1) / 32)
+  int ns;      // strips across
+  int ntile;   // CTA tiles: ns * ceil(H / (nw * LW))
+  int st_vec;  // 1: rows allow aligned 32-bit stores
+  int* err;
+};
+
+__host__ __device__ inline int colw_smem_bytes(int nbox) { return nbox * kCvBoxBytes + nbox * 8; }
+
+// One warp of a CTA tile.  tile: the CTA's input tile; bars: its nbox
+// mbarriers (count 1), the boxes issued by the CTA's thread 0.  False when a
+// bounded wait gave up.
+template <typename T, int OP, int LW>
+__device__ __forceinline__ bool colw_warp(const ColwArgs& a, int ctile, int warp, int lane, const uint8_t* tile,
+                                          uint64_t* bars) {
+  constexpr int E = sizeof(T), PPW = 4 / E;
+  using C = Cw<E>;
+  const uint32_t IDW = ident_word<OP>();
+  const int s = ctile % a.ns;
+  const int yc = (ctile / a.ns) * (a.nw * LW);  // first output row of the CTA tile
+  const int y0 = yc + warp * LW;                // this warp's first output row
+  if (y0 >= a.H) return true;
+  const int w = a.w;
+  const int ysc = yc - a.a;                     // image row of CTA tile row 0
+  const int r0 = warp * LW;                     // this warp's tile row 0
+  const int px0 = s * (kCvBytes / E) + lane * PPW;
+  const bool col_in = px0 < a.W;
+  const bool fast = a.st_vec && px0 + PPW <= a.W;
+  const uint8_t* col = tile + 4 * lane;
+  // rows outside the image read as the identity (TMA fills them with 0)
+  const bool edge = ysc + r0 < 0 || ysc + r0 + LW + w - 1 > a.H;
+  auto LD = [&](int r) -> uint32_t {  // r: row of this warp's tile
+    const uint32_t v = *reinterpret_cast<const uint32_t*>(col + (r0 + r) * kCvBytes);
+    if (!edge) return v;
+    const int y = ysc + r0 + r;
+    return (y < 0 || y >= a.H) ? IDW : v;
+  };
+  int have = 0;
+  auto ensure = [&](int rows) -> bool {  // this warp's tile rows [0, rows) landed
+    const int need = (r0 + rows + kCvBox - 1) / kCvBox;
+    for (; have < need; ++have)
+      if (!mbar_wait_bounded(&bars[have], 0)) {
+        if (lane == 0) atomicExch(a.err, kDevErrTmaTimeout);
+        return false;
+      }
+    return true;
+  };
+  C IDC;
+#pragma unroll
+  for (int i = 0; i < (E == 1 ? 2 : 1); ++i) IDC.v[i] = IDW;
+
+  // h-scan into registers
+  if (!ensure(LW)) return false;
+  uint32_t h[LW];
+  {
+    C acc = IDC;
+#pragma unroll
+    for (int t = LW - 1; t >= 0; --t) {
+      acc = cw_op<OP, E>(acc, cw_of<E>(LD(t)));
+      h[t] = cw_word<E>(acc);
+    }
+  }
+  // g-scan: rows LW .. w-2 emit nothing
+  C g = IDC;
+  int e = LW;
+  constexpr int kB = 8;
+  for (; e + kB <= w - 1; e += kB) {
+    if (!ensure(e + kB)) return false;
+    uint32_t x[kB];
+#pragma unroll
+    for (int t = 0; t < kB; ++t) x[t] = LD(e + t);
+#pragma unroll
+    for (int t = 0; t < kB; ++t) g = cw_op<OP, E>(g, cw_of<E>(x[t]));
+  }
+  for (; e < w - 1; ++e) {
+    if (!ensure(e + 1)) return false;
+    g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
+  }
+  // rows w-1 .. w-2+LW close outputs 0 .. LW-1
+  const int nout = a.H - y0 < LW ? a.H - y0 : LW;
+  if (!ensure(w - 1 + LW)) return false;
+  uint8_t* out = a.dst + static_cast<long long>(y0) * a.dp + static_cast<long long>(px0) * E;
+#pragma unroll
+  for (int o0 = 0; o0 < LW; o0 += kB) {
+    uint32_t x[kB];
+#pragma unroll
+    for (int t = 0; t < kB; ++t) x[t] = LD(w - 1 + o0 + t);
+#pragma unroll
+    for (int t = 0; t < kB; ++t) {
+      const int o = o0 + t;
+      g = cw_op<OP, E>(g, cw_of<E>(x[t]));
+      const uint32_t v = cw_word<E>(cw_op<OP, E>(cw_of<E>(h[o]), g));
+      if (col_in && o < nout) {
+        if (fast) {
+          *reinterpret_cast<uint32_t*>(out + static_cast<long long>(o) * a.dp) = v;
+        } else {
+          T* row = reinterpret_cast<T*>(a.dst + static_cast<long long>(y0 + o) * a.dp);
+#pragma unroll
+          for (int q = 0; q < PPW; ++q)
+            if (px0 + q < a.W) row[px0 + q] = static_cast<T>(v >> (8 * E * q));
+        }
+      }
+    }
+  }
+  return true;
+}
+
+// Launch shape of the shared-tile form: warps per CTA (1..8) so that the
+// CTA tiles come closest to filling whole waves of resident CTAs, preferring
+// more warps (fewer halo rows per output).
+struct ColwPlan {
+  int nw, nbox, ntile, smem;
+  bool ok;
+};
+inline ColwPlan colw_plan(int esz, int W, int H, int w, int LW, int sms, int max_smem, int max_warps) {
+  ColwPlan best{0, 0, 0, 0, false};
+  if (w <= LW || sms < 1) return best;
+  const int ns = (W * esz + kCvBytes - 1) / kCvBytes;
+  double best_cost = 1e300;
+  for (int nw = 8; nw >= 1; --nw) {
+    const int rows = nw * LW + w - 1;
+    const int nbox = (rows + kCvBox - 1) / kCvBox;
+    const int smem = colw_smem_bytes(nbox);
+    if (smem > max_smem) continue;
     int ctas = 233472 / (smem + 1024);
     if (ctas > 32) ctas = 32;
-    if (ctas * wpc > 64) ctas = 64 / wpc;
-    if (ctas < 1) ctas = 1;
-    const int wps = ctas * wpc;
-    const long long ntask = static_cast<long long>(ns) * ((H + L - 1) / L);
-    const double per_sm = static_cast<double>(ntask) / sms;
-    const double waves = static_cast<double>(static_cast<long long>((per_sm + wps - 1) / wps));
-    const double busy = per_sm < wps ? per_sm : wps;
-    const int beta = L % w;
-    const double extra = beta ? (w - 1 - beta) : 0;
-    const double work = L + 0.25 * extra + 32.0;
-    const double eff = busy >= 8 ? 1.0 : busy / 8.0;
-    const double cost = waves * work / eff;
+    if (ctas * nw > max_warps) ctas = max_warps / nw;  // registers
+    if (ctas < 1) continue;
+    const long long ntile = static_cast<long long>(ns) * ((H + nw * LW - 1) / (nw * LW));
+    const double waves = static_cast<double>((ntile + static_cast<long long>(sms) * ctas - 1) /
+                                             (static_cast<long long>(sms) * ctas));
+    // per-CTA time ~ its warps' scans (LW + w - 1 rows each, in parallel)
+    // plus its load (rows) spread over the SM; prefer fewer waves
+    const double cost = waves * (LW + w - 1 + 0.25 * rows / nw * ctas / 4.0);
     if (cost < best_cost) {
       best_cost = cost;
-      best = ColvPlan{L, nbox, wpc, static_cast<int>(ntask), smem, true};
+      best = ColwPlan{nw, nbox, static_cast<int>(ntile), smem, true};
     }
   }
   return best;

@@ -160,6 +160,21 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Per-thread asynchronous copies global -> shared (8 or 16 bytes, both
+// addresses aligned to the size), grouped by commit; wait_group<N> returns
+// once at most N of this thread's groups are still in flight.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 #else
 // Host stand-ins with the same signatures, defined by the CPU emulator of the
 // kernels (tests/emu); only compiled when MORPH_HOST_EMU is set.
@@ -175,6 +190,11 @@ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y);
 void bulk_commit();
 void bulk_wait_read_all();
 void bulk_wait_all();
+void cp_async8(void* smem, const void* gmem);
+void cp_async16(void* smem, const void* gmem);
+void cp_async_commit();
+template <int N>
+void cp_async_wait() {}
 
 #endif
 

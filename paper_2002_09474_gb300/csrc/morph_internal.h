@@ -87,6 +87,10 @@ cudaError_t col_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream);
 // when its warp tile fits in shared memory (colv_fits).
 bool colv_fits(const FusedLaunch& L);
 cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream);
+// Its shared-tile form for wy > 32 (warps of a CTA share one TMA-loaded tile
+// and keep the block suffix in registers; colw_fits).
+bool colw_fits(const FusedLaunch& L);
+cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream);
 
 // The register-blocked van Herk/Gil-Werman kernel of the pass along x
 // (9 <= wx <= 256, rows aligned to 8 * esz bytes; rowv_fits).

@@ -36,8 +36,13 @@ namespace morph {
 
 constexpr int kRvChunk = 256;  // pixels per chunk (32 lanes x 8)
 constexpr int kRvRing = 64;    // prefix ring: two chunks of blocks
-// Shared memory per warp: 8 prefix slots x kRvRing blocks x 16 bytes.
-constexpr int kRvWarpSmem = 8 * kRvRing * 16;
+// Input chunks in flight or in use per warp: 3 for u8 (copies run two
+// chunks ahead), 2 for u16 (one chunk ahead; each chunk is twice the bytes).
+__host__ __device__ constexpr int rv_slots(int esz) { return esz == 1 ? 3 : 2; }
+// Shared memory per warp: the prefix ring (8 prefixes x kRvRing blocks x 16
+// bytes), then the input slots of 8 rows x 33 entries of 8 pixels.
+__host__ __device__ constexpr int rv_raw_off() { return 8 * kRvRing * 16; }
+__host__ __device__ constexpr int rv_warp_smem(int esz) { return rv_raw_off() + rv_slots(esz) * 8 * 33 * 8 * esz; }
 
 struct RowvArgs {
   const uint8_t* src;
@@ -119,20 +124,12 @@ __device__ __forceinline__ void rv_load_row(const uint8_t* row, int B, int dl, i
   }
 }
 
-// Loads block k (8 rows from y0, 8 pixels from column B) and transposes it:
-// V[p] = pixel column p, word j = rows 2j (low lane) and 2j+1 (high lane).
-template <typename T, int OP>
-__device__ __forceinline__ void rv_load_block(const RowvArgs& a, int y0, int B, int dl, uint4 (&V)[8]) {
+// Transposes 8 rows of 8 pixels (R[r]: u8 words 0..1 or u16 words 0..3) into
+// octets: V[p] = pixel column p, word j = rows 2j (low lane) and 2j+1 (high
+// lane); u8 bytes are duplicated into their 16-bit lane.
+template <typename T>
+__device__ __forceinline__ void rv_transpose_in(const uint32_t (&R)[8][4], uint4 (&V)[8]) {
   constexpr int E = sizeof(T);
-  uint32_t R[8][4];
-#pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    if (y0 + r < a.H) {
-      rv_load_row<T, OP>(a.src + static_cast<long long>(y0 + r) * a.sp, B, dl, a.W, R[r]);
-    } else {
-      R[r][0] = R[r][1] = R[r][2] = R[r][3] = ident_word<OP>();
-    }
-  }
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
     uint32_t wv[4];
@@ -148,6 +145,22 @@ __device__ __forceinline__ void rv_load_block(const RowvArgs& a, int y0, int B, 
     }
     V[p] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
+}
+
+// Loads block k (8 rows from y0, 8 pixels from column B) and transposes it:
+// V[p] = pixel column p, word j = rows 2j (low lane) and 2j+1 (high lane).
+template <typename T, int OP>
+__device__ __forceinline__ void rv_load_block(const RowvArgs& a, int y0, int B, int dl, uint4 (&V)[8]) {
+  uint32_t R[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    if (y0 + r < a.H) {
+      rv_load_row<T, OP>(a.src + static_cast<long long>(y0 + r) * a.sp, B, dl, a.W, R[r]);
+    } else {
+      R[r][0] = R[r][1] = R[r][2] = R[r][3] = ident_word<OP>();
+    }
+  }
+  rv_transpose_in<T>(R, V);
 }
 
 // Writes the 8 x 8 output block (octets O) at rows y0.., columns x..
@@ -194,10 +207,22 @@ __device__ __forceinline__ void rv_store_block(const RowvArgs& a, int y0, int x,
 }
 
 // One warp task: rows 8 * (task / nseg) .. +7, output columns of segment
-// task % nseg.  pb: this warp's prefix ring (8 x kRvRing uint4, slot n of
-// block b at pb[n * kRvRing + b]).
+// task % nseg.  ws: this warp's shared memory (rv_warp_smem bytes): the
+// prefix ring (slot n of block b at uint4 index n * kRvRing + b), then the
+// input slots.
+//
+// Input chunks travel by per-lane asynchronous copies one (u16) or two (u8)
+// chunks ahead of use: lane l copies the 8 pixels at the aligned column of its block start
+// (entry l of each row), lane 31 also the 8 after the chunk (entry 32); a
+// block's pixels are entries l and l+1 shifted by the uniform B mod 8.
+// Chunks that reach outside the image (or rows past its bottom) are loaded
+// directly instead, pixel by pixel where needed.
 template <typename T, int OP>
-__device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane, uint4* pb) {
+__device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane, uint8_t* ws) {
+  constexpr int E = sizeof(T), EB = 8 * E;  // bytes per entry
+  constexpr int NS = rv_slots(E), D = NS - 1;  // input slots, chunks copied ahead
+  uint4* pb = reinterpret_cast<uint4*>(ws);
+  uint8_t* raw = ws + rv_raw_off();
   const int y0 = 8 * (task / a.nseg);
   const int xs = (task % a.nseg) * a.seg;
   const int xe = xs + a.seg < a.W ? xs + a.seg : a.W;
@@ -207,8 +232,74 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
   const int q = (a.w - 1) >> 3, r = (a.w - 1) & 7;
   const uint32_t IDW = ident_word<OP>();
   const uint4 ID4 = make_uint4(IDW, IDW, IDW, IDW);
+  const bool rows_in = y0 + 8 <= a.H;
 
-  uint4 Vc[8], Vn[8];
+  auto entry = [&](int slot, int row, int e) { return raw + ((slot * 8 + row) * 33 + e) * EB; };
+  auto fast_chunk = [&](int j) {
+    const int cs = X0 + kRvChunk * j - dl;
+    return rows_in && cs >= 0 && cs + kRvChunk + 8 <= a.W;
+  };
+  auto issue = [&](int j) {
+    if (j <= nck && fast_chunk(j)) {
+      const int slot = j % NS, cs = X0 + kRvChunk * j - dl;
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const uint8_t* row = a.src + static_cast<long long>(y0 + rr) * a.sp;
+        const uint8_t* g = row + static_cast<long long>(cs + 8 * lane) * E;
+        if (E == 1) cp_async8(entry(slot, rr, lane), g); else cp_async16(entry(slot, rr, lane), g);
+        if (lane == 31) {
+          const uint8_t* t = row + static_cast<long long>(cs + kRvChunk) * E;
+          if (E == 1) cp_async8(entry(slot, rr, 32), t); else cp_async16(entry(slot, rr, 32), t);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // Block data of chunk j from its input slot: V[p] = pixel column p.
+  auto build = [&](int j, uint4 (&V)[8]) {
+    if (!fast_chunk(j)) {
+      rv_load_block<T, OP>(a, y0, X0 + kRvChunk * j + 8 * lane, dl, V);
+      return;
+    }
+    const int slot = j % NS;
+    uint32_t R[8][4];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+      const uint8_t* p0 = entry(slot, rr, lane);
+      const uint8_t* p1 = entry(slot, rr, lane + 1);
+      if (E == 1) {
+        const uint2 x = *reinterpret_cast<const uint2*>(p0), y = *reinterpret_cast<const uint2*>(p1);
+        const int sh = 8 * (dl & 3);
+        const uint32_t a0 = dl < 4 ? x.x : x.y, a1 = dl < 4 ? x.y : y.x, a2 = dl < 4 ? y.x : y.y;
+        R[rr][0] = __funnelshift_r(a0, a1, sh);
+        R[rr][1] = __funnelshift_r(a1, a2, sh);
+        R[rr][2] = R[rr][3] = 0u;
+      } else {
+        const uint4 x = *reinterpret_cast<const uint4*>(p0), y = *reinterpret_cast<const uint4*>(p1);
+        const uint32_t v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+        const int sh = 16 * (dl & 1);
+        switch (dl >> 1) {
+          case 0:
+#pragma unroll
+            for (int h = 0; h < 4; ++h) R[rr][h] = __funnelshift_r(v[h], v[h + 1], sh);
+            break;
+          case 1:
+#pragma unroll
+            for (int h = 0; h < 4; ++h) R[rr][h] = __funnelshift_r(v[h + 1], v[h + 2], sh);
+            break;
+          case 2:
+#pragma unroll
+            for (int h = 0; h < 4; ++h) R[rr][h] = __funnelshift_r(v[h + 2], v[h + 3], sh);
+            break;
+          default:
+#pragma unroll
+            for (int h = 0; h < 4; ++h) R[rr][h] = __funnelshift_r(v[h + 3], v[h + 4], sh);
+            break;
+        }
+      }
+    }
+    rv_transpose_in<T>(R, V);
+  };
   auto prefixes = [&](const uint4 (&V)[8], int k) {
     const int b = k & (kRvRing - 1);
     uint4 P = V[0];
@@ -219,42 +310,53 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
       pb[n * kRvRing + b] = P;
     }
   };
-  rv_load_block<T, OP>(a, y0, X0 + 8 * lane, dl, Vc);
-  prefixes(Vc, lane);
-  for (int c = 0; c < nck; ++c) {
-    const int k = 32 * c + lane;
-    // the next chunk (its prefixes close the windows of this one)
-    rv_load_block<T, OP>(a, y0, X0 + 8 * (k + 32), dl, Vn);
-    prefixes(Vn, k + 32);
+
+  // One step: chunk j's block data into Vnew (and its prefixes into the
+  // ring), then the outputs of chunk j-1 from Vold.  Steps alternate the two
+  // arrays, so no block data is copied between them.
+  auto step = [&](int j, const uint4 (&Vold)[8], uint4 (&Vnew)[8]) {
+    issue(j + D);
+    cp_async_wait<D>();
     __syncwarp();
-    // fold of the whole blocks k+1 .. k+q-1
-    uint4 m = ID4;
-    for (int j = 1; j < q; ++j) m = rv_op<OP>(m, pb[7 * kRvRing + ((k + j) & (kRvRing - 1))]);
-    // suffixes of block k, seeded with m
-    uint4 S[8];
-    S[7] = rv_op<OP>(Vc[7], m);
+    build(j, Vnew);
+    prefixes(Vnew, kRvChunk / 8 * j + lane);
+    __syncwarp();
+    if (j >= 1) {
+      // outputs of chunk j-1: block k
+      const int k = 32 * (j - 1) + lane;
+      uint4 m = ID4;  // fold of the whole blocks k+1 .. k+q-1
+      for (int t = 1; t < q; ++t) m = rv_op<OP>(m, pb[7 * kRvRing + ((k + t) & (kRvRing - 1))]);
+      uint4 S[8];  // suffixes of block k, seeded with m
+      S[7] = rv_op<OP>(Vold[7], m);
 #pragma unroll
-    for (int i = 6; i >= 0; --i) S[i] = rv_op<OP>(Vc[i], S[i + 1]);
-    const int bq = (k + q) & (kRvRing - 1), bq1 = (k + q + 1) & (kRvRing - 1);
-    const uint4 Tq = pb[7 * kRvRing + bq];
+      for (int i = 6; i >= 0; --i) S[i] = rv_op<OP>(Vold[i], S[i + 1]);
+      const int bq = (k + q) & (kRvRing - 1), bq1 = (k + q + 1) & (kRvRing - 1);
+      const uint4 Tq = pb[7 * kRvRing + bq];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int n = r + i;
-      const uint4 Pv = n < 8 ? pb[n * kRvRing + bq] : rv_op<OP>(Tq, pb[(n - 8) * kRvRing + bq1]);
-      S[i] = rv_op<OP>(S[i], Pv);
+      for (int i = 0; i < 8; ++i) {
+        const int n = r + i;
+        const uint4 Pv = n < 8 ? pb[n * kRvRing + bq] : rv_op<OP>(Tq, pb[(n - 8) * kRvRing + bq1]);
+        S[i] = rv_op<OP>(S[i], Pv);
+      }
+      const int x = xs + 8 * k;
+      if (x < xe) rv_store_block<T>(a, y0, x, xe, S);
     }
-    const int x = xs + 8 * k;
-    if (x < xe) rv_store_block<T>(a, y0, x, xe, S);
     __syncwarp();
-#pragma unroll
-    for (int p = 0; p < 8; ++p) Vc[p] = Vn[p];
+  };
+  uint4 VA[8], VB[8];
+  for (int j = 0; j < D; ++j) issue(j);
+  for (int j = 0; j <= nck; j += 2) {
+    step(j, VB, VA);
+    if (j + 1 <= nck) step(j + 1, VA, VB);
   }
+  cp_async_wait<0>();
 }
 
 // Launch shape: segment length (a multiple of 256) and warp tasks.  Each task
-// costs its output chunks plus one look-ahead chunk (loads, transposes and
-// prefixes only: about 0.45 of an output chunk); tasks run in waves of
-// (SMs x resident warps); an SM issues at full rate only with about 8 warps.
+// walks its segment chunk by chunk, one chunk ahead, so a task's time is
+// about (its chunks + 1) chunk latencies; a second wave of tasks costs a
+// whole task time.  So: the shortest segment whose tasks all fit in one
+// wave of (SMs x resident warps), else the longest (one segment per row).
 struct RowvPlan {
   int seg, nseg, ntask;
   bool ok;
@@ -263,30 +365,23 @@ inline RowvPlan rowv_plan(int W, int H, int sms, int wps, int forced_seg) {
   RowvPlan best{0, 0, 0, false};
   if (W < 1 || H < 1 || sms < 1) return best;
   const int wmax = (W + kRvChunk - 1) / kRvChunk * kRvChunk;
-  int want = 0;  // a forced segment length, at most the image's width
+  const long long slots = static_cast<long long>(sms) * wps;
+  const long long octets = (H + 7) / 8;
+  int seg = wmax;
   if (forced_seg > 0) {
-    want = (forced_seg + kRvChunk - 1) / kRvChunk * kRvChunk;
-    if (want > wmax) want = wmax;
+    seg = (forced_seg + kRvChunk - 1) / kRvChunk * kRvChunk;
+    if (seg > wmax) seg = wmax;
+  } else {
+    for (int s = kRvChunk; s <= wmax; s += kRvChunk)
+      if (octets * ((W + s - 1) / s) <= slots) {
+        seg = s;
+        break;
+      }
   }
-  double best_cost = 1e300;
-  for (int seg = kRvChunk; seg <= wmax; seg += kRvChunk) {
-    if (want > 0 && seg != want) continue;
-    const int nseg = (W + seg - 1) / seg;
-    const long long ntask = static_cast<long long>((H + 7) / 8) * nseg;
-    if (ntask > (1ll << 30)) continue;
-    const double per_sm = static_cast<double>(ntask) / sms;
-    const double waves = static_cast<double>(static_cast<long long>((per_sm + wps - 1) / wps));
-    const double busy = per_sm < wps ? per_sm : wps;
-    const double chunks = (seg < W ? seg : W) / static_cast<double>(kRvChunk);
-    const double work = chunks + 0.45 + 0.1;
-    const double eff = busy >= 8 ? 1.0 : busy / 8.0;
-    const double cost = waves * work / eff;
-    if (cost < best_cost) {
-      best_cost = cost;
-      best = RowvPlan{seg, nseg, static_cast<int>(ntask), true};
-    }
-  }
-  return best;
+  const int nseg = (W + seg - 1) / seg;
+  const long long ntask = octets * nseg;
+  if (ntask > (1ll << 30)) return best;
+  return RowvPlan{seg, nseg, static_cast<int>(ntask), true};
 }
 
 }  // namespace morph

@@ -2,6 +2,7 @@
 // windows, 9 <= w <= 256): instantiations, launch shape and launch.  Device
 // code in morph_rowv.cuh.
 #include <cstring>
+#include <mutex>
 
 #include "morph_geom.h"
 #include "morph_internal.h"
@@ -13,12 +14,12 @@ namespace morph {
 constexpr int kRvWarps = 4;  // warps per CTA
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(32 * kRvWarps) rowv_kernel(const RowvArgs a) {
-  __shared__ uint4 pbuf[kRvWarps * 8 * kRvRing];
+__global__ void __launch_bounds__(32 * kRvWarps, 4) rowv_kernel(const RowvArgs a) {
+  extern __shared__ __align__(128) uint8_t rvsmem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int task = blockIdx.x * kRvWarps + warp;
   if (task >= a.ntask) return;
-  rowv_task<T, OP>(a, task, lane, pbuf + warp * 8 * kRvRing);
+  rowv_task<T, OP>(a, task, lane, rvsmem + warp * rv_warp_smem(sizeof(T)));
 }
 
 namespace {
@@ -39,8 +40,6 @@ int sm_count_r() {
 
 }  // namespace
 
-// Resident warps per SM assumed by the launch-shape model.
-constexpr int kRvWarpsPerSm = 16;
 
 bool rowv_fits(const FusedLaunch& L) {
   const int al = 8 * L.esz;  // row alignment the vector loads and stores need
@@ -52,7 +51,29 @@ cudaError_t rowv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int sms = sm_count_r();
   if (sms <= 0) return cudaErrorInvalidDevice;
   if (!rowv_fits(L)) return cudaErrorInvalidConfiguration;
-  const RowvPlan p = rowv_plan(L.W, L.H, sms, kRvWarpsPerSm, tuning().rowv_seg);
+  const int smem = kRvWarps * rv_warp_smem(L.esz);
+  RowvFn k = rowv_kernel_for(L.esz, L.op);
+  static std::mutex mu;
+  static const void* opted[64][4] = {};
+  static int resident[64][4] = {};  // CTAs per SM
+  int wps = 0;                        // resident warps per SM
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    const int slot = (L.esz - 1) * 2 + L.op;
+    if (opted[dev & 63][slot] != reinterpret_cast<const void*>(k)) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      int n = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 32 * kRvWarps, smem);
+      if (e != cudaSuccess) return e;
+      resident[dev & 63][slot] = n > 0 ? n : 1;
+      opted[dev & 63][slot] = reinterpret_cast<const void*>(k);
+    }
+    wps = kRvWarps * resident[dev & 63][slot];
+  }
+  const RowvPlan p = rowv_plan(L.W, L.H, sms, wps, tuning().rowv_seg);
   if (!p.ok) return cudaErrorInvalidConfiguration;
   RowvArgs a;
   a.src = static_cast<const uint8_t*>(L.src);
@@ -69,7 +90,7 @@ cudaError_t rowv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int al = 8 * L.esz;
   a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % al == 0) && (L.dp % al == 0);
   note_launch();
-  rowv_kernel_for(L.esz, L.op)<<<cdiv(p.ntask, kRvWarps), 32 * kRvWarps, 0, stream>>>(a);
+  k<<<cdiv(p.ntask, kRvWarps), 32 * kRvWarps, smem, stream>>>(a);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,10 @@ def main(argv=None):
     ap.add_argument("--cross-row", type=int, default=-1, help="force the x-pass crossover")
     ap.add_argument("--cross-col", type=int, default=-1, help="force the y-pass crossover")
     ap.add_argument("--tile", type=int, default=-1, help="force a tile configuration first")
+    ap.add_argument("--colv", type=int, default=-1,
+                    help="force the warp-tiled pass along y with this many rows per tile (0: model)")
+    ap.add_argument("--rowv", type=int, default=-1,
+                    help="force the register-blocked pass along x with this segment (0: model)")
     args = ap.parse_args(argv)
 
     import torch
@@ -41,6 +45,10 @@ def main(argv=None):
     dt = np.uint8 if args.dtype == "u8" else np.uint16
     code = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
     morph.morph_set_tuning(code, args.cross_row, args.cross_col, args.tile)
+    if args.colv >= 0:
+        morph.morph_set_colv(1, args.colv)
+    if args.rowv >= 0:
+        morph.morph_set_rowv(1, args.rowv)
     img = synth.uniform_image(args.width, args.height, dt, seed=1)
     src = torch.from_numpy(img).cuda()
     dst = torch.empty_like(src)

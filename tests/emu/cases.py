@@ -136,6 +136,20 @@ def cases(full=True):
                         seed += 1
     for c in rowv:
         both.append(c + (5,))
+    # the shared-tile pass along y (wy > 32, TMA-loadable rows): tall and
+    # ragged images, every anchor extreme
+    colw = []
+    for esz in (1, 2):
+        for (w, h) in ((128, 1000), (300, 2100), (64, 700), (257, 333), (190, 41), (1000, 64)):
+            for wy in (33, 40, 63, 64, 65, 101, 127, 255, 700):
+                for ay in sorted({0, wy // 2, wy - 1}):
+                    for op in (0, 1):
+                        pad = aligned_pad(w, esz)
+                        dpad, doff = (pad, 0) if (wy + ay) % 2 else (esz, 3 * esz)
+                        colw.append((esz, op, w, h, pad, 0, dpad, doff, 1, wy, 0, ay, -1, -1, -1, seed))
+                        seed += 1
+    for c in colw:
+        both.append(c + (6,))
     return both
 
 

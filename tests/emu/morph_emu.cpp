@@ -23,7 +23,9 @@
 // SMs on odd seeds and 3 SMs on even ones, 5 = the register-blocked van
 // Herk/Gil-Werman kernel of the pass along x for wx x 1 windows, when the
 // source rows allow it, its segment planned for 152 SMs on odd seeds and 3
-// SMs on even ones).
+// SMs on even ones, 6 = the shared-tile form of the pass along y for
+// 1 x wy windows with wy > 32 and TMA-loadable rows, its warps per CTA
+// planned for 152 SMs on odd seeds and 3 SMs on even ones).
 // Output: one line per case, "OK ..." or "FAIL ...".
 #define MORPH_HOST_EMU 1
 
@@ -225,6 +227,17 @@ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
         for (int b = 0; b < m->esz; ++b) m->wbase[gy * m->pitch + gx * m->esz + b] = s[r * row + c * m->esz + b];
     }
 }
+void cp_async8(void* smem, const void* gmem) {
+  if (reinterpret_cast<uintptr_t>(gmem) % 8) emu_error("cp.async source not 8-byte aligned");
+  check_smem(smem, 8, 8, "cp.async destination outside shared memory");
+  memcpy(smem, gmem, 8);
+}
+void cp_async16(void* smem, const void* gmem) {
+  if (reinterpret_cast<uintptr_t>(gmem) % 16) emu_error("cp.async source not 16-byte aligned");
+  check_smem(smem, 16, 16, "cp.async destination outside shared memory");
+  memcpy(smem, gmem, 16);
+}
+void cp_async_commit() {}
 void bulk_commit() {}
 void bulk_wait_read_all() {}
 void bulk_wait_all() {}
@@ -501,7 +514,7 @@ int main() {
     const bool use_colv = kern == 4 && L.wx == 1 && L.wy > 1;
     if (use_colv) {
       // the warp-tiled pass along y, planned and launched as colv_launch does
-      const ColvPlan p = colv_plan(esz, W, H, L.wy, (seed & 1) ? 152 : 3, kMaxSmemBytes, 0);
+      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 8 * (1 + static_cast<int>(seed % 24)));
       if (!p.ok) {
         printf("FAIL case %d: no colv plan\n", cases);
         ++failures;
@@ -547,7 +560,7 @@ int main() {
               const int warp = tid >> 5, lane = tid & 31, task = blk * c.wpc + warp;
               if (task >= c.ntask) return;
               uint8_t* tile = sm + warp * colv_tile_bytes(c.nbox);
-              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.wpc * colv_tile_bytes(c.nbox)) + warp * kCvMaxBox;
+              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.wpc * colv_tile_bytes(c.nbox)) + warp * c.nbox;
               if (c.tma_ld && lane == 0)
                 for (int b = 0; b < c.nbox; ++b) mbar_init(&bars[b], 1);
               // lanes wait on the barriers only after lane 0 initialised them
@@ -574,7 +587,7 @@ int main() {
     const bool use_rowv = kern == 5 && L.wy == 1 && L.wx >= 9 && L.wx <= 256 &&
                           reinterpret_cast<uintptr_t>(src) % ral == 0 && sp % ral == 0;
     if (use_rowv) {
-      const RowvPlan p = rowv_plan(W, H, (seed & 1) ? 152 : 3, 16, 0);
+      const RowvPlan p = rowv_plan(W, H, (seed & 1) ? 152 : 3, 12, (seed % 3 == 0) ? 256 * static_cast<int>(1 + seed % 5) : 0);
       col_ty = p.seg;
       RowvArgs ra{};
       ra.src = src;
@@ -589,7 +602,7 @@ int main() {
       ra.nseg = p.nseg;
       ra.ntask = p.ntask;
       ra.st_vec = (reinterpret_cast<uintptr_t>(dst) % ral == 0) && (dp % ral == 0);
-      using RvFn = void (*)(const RowvArgs&, int, int, uint4*);
+      using RvFn = void (*)(const RowvArgs&, int, int, uint8_t*);
       RvFn rf = esz == 1 ? (op == 0 ? rowv_task<uint8_t, 0> : rowv_task<uint8_t, 1>)
                          : (op == 0 ? rowv_task<uint16_t, 0> : rowv_task<uint16_t, 1>);
       const int wpc = 4;
@@ -602,7 +615,7 @@ int main() {
           cta.wbar[w] = wb.back().get();
         }
         cta.bar = &bar;
-        const size_t smb = static_cast<size_t>(wpc) * kRvWarpSmem;
+        const size_t smb = static_cast<size_t>(wpc) * rv_warp_smem(esz);
         uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, smb));
         cta.smem = sm;
         cta.smem_size = smb;
@@ -612,9 +625,71 @@ int main() {
               emu_threadIdx = make_uint3(tid, 0, 0);
               const int warp = tid >> 5, lane = tid & 31, task = blk * wpc + warp;
               if (task >= p.ntask) return;
-              rf(ra, task, lane, reinterpret_cast<uint4*>(sm + warp * kRvWarpSmem));
+              rf(ra, task, lane, sm + warp * rv_warp_smem(esz));
             },
             32 * wpc);
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+    }
+    const int lw = L.wy > 64 ? 64 : L.wy > 32 ? 32 : 0;
+    const bool use_colw = kern == 6 && L.wx == 1 && lw && tma_ok(src, sp, kCvBytes / esz, kCvBox);
+    if (use_colw) {
+      const ColwPlan p = colw_plan(esz, W, H, L.wy, lw, (seed & 1) ? 152 : 3, kMaxSmemBytes, 16);
+      col_ty = p.nw;
+      ColwArgs c{};
+      c.src = src;
+      c.dst = dst;
+      c.sp = sp;
+      c.dp = dp;
+      c.W = W;
+      c.H = H;
+      c.w = L.wy;
+      c.a = L.ay;
+      c.nw = p.nw;
+      c.nbox = p.nbox;
+      c.ns = cdiv(W * esz, kCvBytes);
+      c.ntile = p.ntile;
+      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
+      c.err = &errword;
+      a.tma_ld = 1;
+      EmuMap mc{src, nullptr, esz, W, H, sp, kCvBytes / esz, kCvBox};
+      CUtensorMap tc{};
+      memcpy(&tc, &mc, sizeof(mc));
+      using WFn = bool (*)(const ColwArgs&, int, int, int, const uint8_t*, uint64_t*);
+      WFn wf = lw == 64 ? (esz == 1 ? (op == 0 ? colw_warp<uint8_t, 0, 64> : colw_warp<uint8_t, 1, 64>)
+                                    : (op == 0 ? colw_warp<uint16_t, 0, 64> : colw_warp<uint16_t, 1, 64>))
+                        : (esz == 1 ? (op == 0 ? colw_warp<uint8_t, 0, 32> : colw_warp<uint8_t, 1, 32>)
+                                    : (op == 0 ? colw_warp<uint16_t, 0, 32> : colw_warp<uint16_t, 1, 32>));
+      const int nthr = 32 * c.nw;
+      for (int t = 0; t < c.ntile; ++t) {
+        EmuCta cta;
+        std::barrier<> bar(nthr);
+        cta.bar = &bar;
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (p.smem + 127) / 128 * 128));
+        cta.smem = sm;
+        cta.smem_size = p.smem;
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.nbox * kCvBoxBytes);
+              if (tid == 0) {
+                for (int b = 0; b < c.nbox; ++b) mbar_init(&bars[b], 1);
+                const int s = t % c.ns;
+                const int ysc = (t / c.ns) * (c.nw * lw) - c.a;
+                for (int b = 0; b < c.nbox; ++b) {
+                  mbar_arrive_expect_tx(&bars[b], static_cast<uint32_t>(kCvBoxBytes));
+                  tma_load_2d(sm + b * kCvBoxBytes, &tc, &bars[b], s * (kCvBytes / esz), ysc + b * kCvBox);
+                }
+              }
+              __syncthreads();
+              wf(c, t, tid >> 5, tid & 31, sm, bars);
+              if (tid == 0)
+                for (int b = 0; b < c.nbox; ++b) mbar_wait_bounded(&bars[b], 0);
+            },
+            nthr);
         free(sm);
         errors += cta.errors.load();
         if (cta.errors.load() && first.empty()) first = cta.first_error;
@@ -668,7 +743,7 @@ int main() {
       }
       a.tma_ld = ra.tma_ld;
     }
-    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv ? 0 : ncta); ++c) {
+    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv || use_colw ? 0 : ncta); ++c) {
       const int bx = c % gx, by = c / gx;
       EmuCta cta;
       std::barrier<> bar(kThreads);
@@ -716,7 +791,7 @@ int main() {
     printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
            "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_rowv ? 5 : use_colv ? 4 : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_colw ? 6 : use_rowv ? 5 : use_colv ? 4 : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);
