@@ -255,13 +255,13 @@ int morph_set_column_kernel(int mode);
  * kernel for every wy >= 2 whose warp tile fits in shared memory; -1
  * (default): wherever the van Herk/Gil-Werman method is chosen (wy above the
  * crossover of section 5.3; measured faster than the column kernel there);
- * 0: never (the column kernel of morph_set_column_kernel instead).  rows:
- * output rows per warp tile, 1 to 1024 (rounded up to a multiple of 8), or 0
- * for the library's choice: for wy > 32 (and TMA-loadable rows) a
- * shared-tile form in which the warps of a CTA share one input tile and keep
- * the block suffix of their 32 or 64 output rows in registers, else warp
- * tiles of 64 rows.  The result never changes.
- * MORPH_ERR_ARG for another mode or rows.
+ * 0: never (the column kernel of morph_set_column_kernel instead); 2: as 1,
+ * but for wy > 32 and TMA-loadable rows a shared-tile form in which the
+ * warps of a CTA share one input tile and keep the block suffix of their 32
+ * or 64 output rows in registers (measured slower on the GB300, so not a
+ * default).  rows: output rows per warp tile, 1 to 1024, or 0 for the
+ * launch-shape model's choice (a multiple of wy, or 64).  The result never
+ * changes.  MORPH_ERR_ARG for another mode or rows.
  */
 int morph_set_colv(int mode, int rows);
 

@@ -84,7 +84,7 @@ struct Scratch {
 bool use_colv(const FusedLaunch& L) {
   const int m = tuning().colv_mode;
   if (m == 0) return false;
-  return (m == 1 || L.vhgw_col) && colv_fits(L);
+  return (m >= 1 || L.vhgw_col) && colv_fits(L);
 }
 bool use_rowv(const FusedLaunch& L) {
   const int m = tuning().rowv_mode;
@@ -95,8 +95,8 @@ bool use_rowv(const FusedLaunch& L) {
 int launch_one(FusedLaunch L, cudaStream_t stream) {
   if (!plan_single(&L)) return MORPH_ERR_WINDOW;
   if (L.wx == 1 && L.wy > 1 && use_colv(L)) {
-    // rows per warp tile not forced: the shared-tile form where it applies
-    if (tuning().colv_rows == 0 && colw_fits(L))
+    // mode 2: the shared-tile form where it applies
+    if (tuning().colv_mode == 2 && colw_fits(L))
       return colw_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
     return colv_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   }
@@ -505,7 +505,7 @@ int morph_set_row_kernel(int mode) {
 }
 
 int morph_set_colv(int mode, int rows) {
-  if (mode < -1 || mode > 1 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
+  if (mode < -1 || mode > 2 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
   tuning().colv_mode = mode;
   tuning().colv_rows = rows;
   return MORPH_OK;

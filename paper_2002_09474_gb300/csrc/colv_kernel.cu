@@ -155,7 +155,7 @@ bool colv_fits(const FusedLaunch& L) {
 
 cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int E = L.esz;
-  const ColvPlan p = colv_plan(E, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows);
+  const ColvPlan p = colv_plan(E, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, sm_count_w());
   if (!p.ok) return cudaErrorInvalidConfiguration;
   ColvArgs a;
   a.src = static_cast<const uint8_t*>(L.src);

@@ -254,46 +254,75 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
 namespace morph {
 
 // Launch shape of the pass along y: output rows per warp tile (L), warps per
-// CTA, shared memory.  L = 64 unless forced (or the image is shorter):
-// measured on the GB300 over 4096^2 u8/u16 images and windows of 51, 101
-// and 127 rows, it was within 10% of the best height everywhere; smaller
-// tiles spend more of their time on the partial first block and on loading
-// halo rows, taller ones leave SMs idle.  Warps per CTA: the choice that
-// keeps the most warps resident per SM.
+// CTA, shared memory.  A tile of L rows scans L rows backwards and, per block
+// it touches, w - 1 rows forwards: L + ceil(L / w) * (w - 1) row steps, which
+// is least per output when L is a multiple of w (no partial block).  The
+// candidates are the multiples of w and 64; each costs its waves of
+// (SMs x resident warps) times a tile's row steps plus a fixed start-up
+// (the first boxes' latency), discounted when fewer than 6 warps per SM are
+// busy.  Warps per CTA: the choice that keeps the most warps resident.
 struct ColvPlan {
   int L, nbox, wpc, ntask, smem;
   bool ok;
 };
 
-inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L) {
+inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, int* wps_out) {
   ColvPlan p{0, 0, 0, 0, 0, false};
-  if (w < 2 || W < 1 || H < 1) return p;
   const int ns = (W * esz + kCvBytes - 1) / kCvBytes;
-  int hmax = (H + 7) / 8 * 8;
-  if (hmax > 1024) hmax = 1024;
-  int L = forced_L > 0 ? (forced_L + 7) / 8 * 8 : 64;
-  if (L > hmax) L = hmax;
-  // very long windows: shorter tiles until the tile fits
-  for (; L >= 8; L -= 8) {
-    const int nbox = (L + w - 1 + kCvBox - 1) / kCvBox;
-    if (nbox > kCvMaxBox) continue;
-    int wpc = 0, wps = 0;
-    for (int c = 4; c >= 1; c /= 2) {
-      if (colv_smem_bytes(nbox, c) > max_smem) continue;
-      int ctas = 233472 / (colv_smem_bytes(nbox, c) + 1024);
-      if (ctas > 32) ctas = 32;
-      if (ctas * c > 64) ctas = 64 / c;
-      if (ctas * c > wps) {
-        wps = ctas * c;
-        wpc = c;
-      }
+  const int nbox = (L + w - 1 + kCvBox - 1) / kCvBox;
+  if (nbox > kCvMaxBox) return p;
+  int wpc = 0, wps = 0;
+  for (int c = 4; c >= 1; c /= 2) {
+    if (colv_smem_bytes(nbox, c) > max_smem) continue;
+    int ctas = 233472 / (colv_smem_bytes(nbox, c) + 1024);
+    if (ctas > 32) ctas = 32;
+    if (ctas * c > 64) ctas = 64 / c;
+    if (ctas * c > wps) {
+      wps = ctas * c;
+      wpc = c;
     }
-    if (wpc == 0) continue;
-    const long long ntask = static_cast<long long>(ns) * ((H + L - 1) / L);
-    if (ntask > (1ll << 30)) return p;
-    return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc), true};
   }
-  return p;
+  if (wpc == 0) return p;
+  const long long ntask = static_cast<long long>(ns) * ((H + L - 1) / L);
+  if (ntask > (1ll << 30)) return p;
+  *wps_out = wps;
+  return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc), true};
+}
+
+inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L, int sms = 152) {
+  ColvPlan best{0, 0, 0, 0, 0, false};
+  if (w < 2 || W < 1 || H < 1) return best;
+  const int hmax = H < 1024 ? H : 1024;
+  int wps = 0;
+  if (forced_L > 0) {
+    for (int L = forced_L < hmax ? forced_L : hmax; L >= 1; L -= 8) {
+      best = colv_shape(esz, W, H, w, max_smem, L, &wps);
+      if (best.ok) break;
+    }
+    return best;
+  }
+  double best_cost = 1e300;
+  auto consider = [&](int L) {
+    if (L < 1) return;
+    if (L > hmax) L = hmax;
+    const ColvPlan p = colv_shape(esz, W, H, w, max_smem, L, &wps);
+    if (!p.ok) return;
+    const double per_sm = static_cast<double>(p.ntask) / sms;
+    const double waves = static_cast<double>(static_cast<long long>((per_sm + wps - 1) / wps));
+    const double busy = per_sm < wps ? per_sm : wps;
+    const double steps = L + static_cast<double>((L + w - 1) / w) * (w - 1);
+    const double eff = busy >= 6 ? 1.0 : busy / 6.0;
+    const double cost = waves * (steps + 60.0) / eff;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = p;
+    }
+  };
+  consider(64);
+  for (int k = 1; k * w <= 1024 && k <= 16; ++k) consider(k * w);
+  // very long windows: shorter tiles until one fits
+  for (int L = 56; !best.ok && L >= 8; L -= 8) consider(L);
+  return best;
 }
 
 }  // namespace morph

@@ -1,6 +1,6 @@
 """GPU parity of the single-pass kernels against the CPU oracle, each forced
 on in turn: the warp-tiled van Herk/Gil-Werman pass along y (section 5.1.1,
-every tile height the launch-shape model can pick from), the register-blocked
+tile heights from 8 to 512 rows) and its shared-tile form, the register-blocked
 pass along x (sections 4 and 5.1.1's decomposition on 8-pixel blocks, every
 segment length), and the older column and row kernels.  Bit-exact over ragged
 shapes, anchor extremes, even and odd windows, pitched and unaligned buffers,
@@ -53,6 +53,28 @@ def test_pass_along_y_warp_tiled(lib, dtype, rows):
                 off = 0 if i % 4 < 2 else np.dtype(dtype).itemsize
                 got = run(lib, torch, img, 1, wy, 0, ay, op, pad=pad, offset=off, dst_pad=pad)
                 assert np.array_equal(got, want), (h, w, wy, ay, op, pad, off, rows)
+    finally:
+        lib.morph_set_colv(-1, 0)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_pass_along_y_shared_tile(lib, dtype):
+    """The shared-tile form (warps share one input tile, block suffix in
+    registers) for windows longer than 32 rows, TMA-loadable rows."""
+    torch = need_cuda()
+    g = synth.rng(350)
+    try:
+        assert lib.morph_set_colv(2, 0) == 0
+        for (h, w) in ((40, 300), (300, 129), (1000, 257), (2049, 64)):
+            img = synth.uniform_image(w, h, dtype, gen=g)
+            for i, (wy, ay) in enumerate(((33, 0), (40, 39), (63, 31), (64, 0), (65, 64), (101, 50),
+                                          (127, 0), (255, 127), (300, 299))):
+                op = ("erode", "dilate")[i % 2]
+                want = oracle.morph(img, 1, wy, 0, ay, op)
+                pad = aligned_pad(w, dtype)
+                dpad, doff = (pad, 0) if i % 2 else (np.dtype(dtype).itemsize, 3 * np.dtype(dtype).itemsize)
+                got = run(lib, torch, img, 1, wy, 0, ay, op, pad=pad, dst_pad=dpad, dst_offset=doff)
+                assert np.array_equal(got, want), (h, w, wy, ay, op)
     finally:
         lib.morph_set_colv(-1, 0)
 
