@@ -143,6 +143,22 @@ typedef struct {
 int morph_batch(const morph_desc *descs_host, int n, void *stream);
 
 /*
+ * Host-buffer form for many images: descs[i].src and .dst are HOST pointers
+ * (pinned memory lets the copies overlap the filtering; pageable memory
+ * works but serialises), the other fields as for morph_batch.  The images
+ * are filtered one after another through a pipeline the library owns per
+ * device -- three device staging slots and three streams -- so that the copy
+ * in of image i+1, the filtering of image i and the copy out of image i-1
+ * run at the same time (the paper has no counterpart: it filters images in
+ * host memory).  The work starts after what is queued on `stream`; the call
+ * returns once every result is in host memory.  Staging memory is grown on
+ * demand and kept until morph_release_staging.  Calls that share a device
+ * are serialised.  Every descriptor is validated before anything is queued;
+ * the first failing image's status is returned.
+ */
+int morph_apply_host_batch(const morph_desc *descs, int n, void *stream);
+
+/*
  * Graph form of morph_batch: plan_create validates the descriptors, builds the
  * tile list in device memory at fixed addresses and captures the persistent
  * launch in a CUDA graph; plan_launch replays it on `stream` (one
@@ -214,11 +230,12 @@ int morph_reset_tuning(void);
  * Form of single-image calls with a 2-D window (section 5: the element is
  * separable, so erosion by wx x wy is erosion by 1 x wy followed by wx x 1).
  * mode -1 (default): two launches through an intermediate image the
- * library allocates stream-ordered when both window sides are at least 9
- * and the pixels are 8-bit or the longer side is at least 32 (where the
- * single-pass kernels were measured faster than the fused kernel on the
- * GB300), or when the fused tile is so large that fewer than 3 CTAs fit on
- * an SM; otherwise both passes fused in one kernel.  0: always fused; 1:
+ * library allocates stream-ordered for images of at least 2 Mpixels when
+ * both window sides are at least 9 and the pixels are 8-bit or the longer
+ * side is at least 32 (where the single-pass kernels were measured faster
+ * than the fused kernel on the GB300), or when the fused tile is so large
+ * that fewer than 3 CTAs fit on an SM; otherwise both passes fused in one
+ * kernel.  0: always fused; 1:
  * always two launches.  The result never
  * changes.
  */
@@ -260,7 +277,7 @@ int morph_set_column_kernel(int mode);
  * warps of a CTA share one input tile and keep the block suffix of their 32
  * or 64 output rows in registers (measured slower on the GB300, so not a
  * default).  rows: output rows per warp tile, 1 to 1024, or 0 for the
- * launch-shape model's choice (a multiple of wy, or 64).  The result never
+ * measured default (wy or 2 wy up to 256, or 64).  The result never
  * changes.  MORPH_ERR_ARG for another mode or rows.
  */
 int morph_set_colv(int mode, int rows);

@@ -164,6 +164,7 @@ int launch_planned(FusedLaunch L, cudaStream_t stream) {
   Scratch tmp;
   if (!tmp.alloc(static_cast<size_t>(L.W) * L.esz, L.H, stream)) return MORPH_ERR_NOMEM;
   FusedLaunch A = L, B = L;
+  B.pdl = true;  // the pass along x may be scheduled while the pass along y finishes
   A.wx = 1;
   A.ax = 0;
   A.dst = tmp.p;
@@ -233,6 +234,77 @@ int stage_buffers(size_t bytes, void** in, void** out) {
   *in = s.in;
   *out = s.out;
   return MORPH_OK;
+}
+
+// Copy/compute pipeline of morph_apply_host_batch, one per device: three
+// staging slots (input and output image each), three streams (copies in,
+// filtering, copies out) and the events that order a slot's stages, so the
+// copy in of image i+1, the filtering of image i and the copy out of image
+// i-1 run at the same time.
+constexpr int kPipeSlots = 3;
+struct Pipeline {
+  std::mutex mu;
+  void* in[kPipeSlots] = {};
+  void* out[kPipeSlots] = {};
+  size_t bytes = 0;
+  cudaStream_t st[3] = {};
+  cudaEvent_t start = nullptr;
+  cudaEvent_t in_done[kPipeSlots] = {}, comp_done[kPipeSlots] = {}, out_done[kPipeSlots] = {};
+  bool ready = false;
+};
+Pipeline g_pipe[kMaxDevices];
+
+void free_pipeline_buffers(Pipeline& p) {
+  for (int k = 0; k < kPipeSlots; ++k) {
+    if (p.in[k]) cudaFree(p.in[k]);
+    if (p.out[k]) cudaFree(p.out[k]);
+    p.in[k] = p.out[k] = nullptr;
+  }
+  p.bytes = 0;
+}
+
+int pipeline_for_current_device(size_t bytes, Pipeline** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MORPH_ERR_CUDA;
+  Pipeline& p = g_pipe[dev];
+  std::lock_guard<std::mutex> lock(p.mu);
+  if (!p.ready) {
+    for (int k = 0; k < 3; ++k)
+      if (cudaStreamCreateWithFlags(&p.st[k], cudaStreamNonBlocking) != cudaSuccess) return MORPH_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming) != cudaSuccess) return MORPH_ERR_CUDA;
+    for (int k = 0; k < kPipeSlots; ++k)
+      if (cudaEventCreateWithFlags(&p.in_done[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p.comp_done[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p.out_done[k], cudaEventDisableTiming) != cudaSuccess)
+        return MORPH_ERR_CUDA;
+    p.ready = true;
+  }
+  if (p.bytes < bytes) {
+    for (int k = 0; k < 3; ++k) cudaStreamSynchronize(p.st[k]);
+    free_pipeline_buffers(p);
+    for (int k = 0; k < kPipeSlots; ++k)
+      if (cudaMalloc(&p.in[k], bytes) != cudaSuccess || cudaMalloc(&p.out[k], bytes) != cudaSuccess) {
+        free_pipeline_buffers(p);
+        return MORPH_ERR_NOMEM;
+      }
+    p.bytes = bytes;
+  }
+  *out = &p;
+  return MORPH_OK;
+}
+
+void release_pipelines() {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (int d = 0; d < kMaxDevices; ++d) {
+    Pipeline& p = g_pipe[d];
+    std::lock_guard<std::mutex> lock(p.mu);
+    if (!p.bytes) continue;
+    cudaSetDevice(d);
+    for (int k = 0; k < 3; ++k) cudaStreamSynchronize(p.st[k]);
+    free_pipeline_buffers(p);
+  }
+  cudaSetDevice(cur);
 }
 
 // Validates and plans every descriptor of a batch.  Besides the single-image
@@ -550,7 +622,61 @@ int morph_apply_host(const void* src, size_t src_pitch, void* dst, size_t dst_pi
   return cudaStreamSynchronize(st) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
 }
 
+int morph_apply_host_batch(const morph_desc* descs, int n, void* stream) {
+  if (!descs) return MORPH_ERR_NULL;
+  if (n < 1) return MORPH_ERR_ARG;
+  size_t most = 0;  // largest staging image (16-byte rows)
+  for (int i = 0; i < n; ++i) {
+    const morph_desc& d = descs[i];
+    const int rc = validate(d.src, static_cast<size_t>(d.src_pitch), d.dst, static_cast<size_t>(d.dst_pitch),
+                            d.width, d.height, d.dtype, d.op, d.wx, d.wy, d.anchor_x, d.anchor_y);
+    if (rc != MORPH_OK) return rc;
+    const size_t pitch = (static_cast<size_t>(d.width) * esz_of(d.dtype) + 15) / 16 * 16;
+    most = std::max(most, pitch * static_cast<size_t>(d.height));
+  }
+  Pipeline* pl = nullptr;
+  int rc = pipeline_for_current_device(most, &pl);
+  if (rc != MORPH_OK) return rc;
+  std::lock_guard<std::mutex> lock(pl->mu);
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  // the pipeline's streams start after work already queued on the caller's
+  if (cudaEventRecord(pl->start, caller) != cudaSuccess) return MORPH_ERR_CUDA;
+  for (int k = 0; k < 3; ++k)
+    if (cudaStreamWaitEvent(pl->st[k], pl->start, 0) != cudaSuccess) return MORPH_ERR_CUDA;
+  for (int i = 0; i < n && rc == MORPH_OK; ++i) {
+    const morph_desc& d = descs[i];
+    const int slot = i % kPipeSlots;
+    const size_t row = static_cast<size_t>(d.width) * esz_of(d.dtype);
+    const size_t pitch = (row + 15) / 16 * 16;
+    // copy in once the slot's previous image has been copied out
+    if (i >= kPipeSlots && cudaStreamWaitEvent(pl->st[0], pl->out_done[slot], 0) != cudaSuccess) rc = MORPH_ERR_CUDA;
+    if (rc == MORPH_OK && cudaMemcpy2DAsync(pl->in[slot], pitch, d.src, static_cast<size_t>(d.src_pitch), row,
+                                            d.height, cudaMemcpyHostToDevice, pl->st[0]) != cudaSuccess)
+      rc = MORPH_ERR_CUDA;
+    if (rc == MORPH_OK && cudaEventRecord(pl->in_done[slot], pl->st[0]) != cudaSuccess) rc = MORPH_ERR_CUDA;
+    // filter once it is in (and once the slot's previous output is out)
+    if (rc == MORPH_OK && cudaStreamWaitEvent(pl->st[1], pl->in_done[slot], 0) != cudaSuccess) rc = MORPH_ERR_CUDA;
+    if (rc == MORPH_OK && i >= kPipeSlots && cudaStreamWaitEvent(pl->st[1], pl->out_done[slot], 0) != cudaSuccess)
+      rc = MORPH_ERR_CUDA;
+    if (rc == MORPH_OK)
+      rc = run_single(pl->in[slot], pitch, pl->out[slot], pitch, d.width, d.height, d.dtype, d.op, d.wx, d.wy,
+                      d.anchor_x, d.anchor_y, pl->st[1]);
+    if (rc == MORPH_OK && cudaEventRecord(pl->comp_done[slot], pl->st[1]) != cudaSuccess) rc = MORPH_ERR_CUDA;
+    // copy out once it is filtered
+    if (rc == MORPH_OK && cudaStreamWaitEvent(pl->st[2], pl->comp_done[slot], 0) != cudaSuccess) rc = MORPH_ERR_CUDA;
+    if (rc == MORPH_OK && cudaMemcpy2DAsync(d.dst, static_cast<size_t>(d.dst_pitch), pl->out[slot], pitch, row,
+                                            d.height, cudaMemcpyDeviceToHost, pl->st[2]) != cudaSuccess)
+      rc = MORPH_ERR_CUDA;
+    if (rc == MORPH_OK && cudaEventRecord(pl->out_done[slot], pl->st[2]) != cudaSuccess) rc = MORPH_ERR_CUDA;
+  }
+  // everything queued so far must finish before the call returns, errors or not
+  for (int k = 0; k < 3; ++k) cudaStreamSynchronize(pl->st[k]);
+  if (rc != MORPH_OK) return rc;
+  return cudaStreamSynchronize(caller) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+}
+
 int morph_release_staging(void) {
+  release_pipelines();
   std::lock_guard<std::mutex> lock(g_staging_mu);
   int cur = 0;
   cudaGetDevice(&cur);

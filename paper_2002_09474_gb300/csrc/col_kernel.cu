@@ -16,11 +16,13 @@ __global__ void __launch_bounds__(kColThreads, 4) col_kernel(const __grid_consta
                                                              const ColArgs a) {
   __shared__ __align__(8) uint64_t bars[kColMaxBoxes];
   extern __shared__ __align__(128) uint8_t csmem[];
+  pdl_launch_dependents();
   if (a.tma_ld && threadIdx.x == 0) {
     for (int b = 0; b < kColMaxBoxes; ++b) mbar_init(&bars[b], 1);
     fence_barrier_init();
   }
   __syncthreads();
+  pdl_wait();
   col_tile<T, OP, BLK>(a, &tin, blockIdx.x, csmem, reinterpret_cast<uint32_t*>(csmem + kColBytes * a.ihp), bars);
 }
 
@@ -89,9 +91,7 @@ cudaError_t col_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream) 
       opted[dev & 63][slot] = reinterpret_cast<const void*>(k);
     }
   }
-  note_launch();
-  k<<<a.ntiles, kColThreads, g.smem, stream>>>(tin, a);
-  return cudaGetLastError();
+  return launch_pdl(L.pdl, k, dim3(a.ntiles), dim3(kColThreads), g.smem, stream, tin, a);
 }
 
 }  // namespace morph

@@ -14,6 +14,7 @@ namespace morph {
 template <typename T, int OP>
 __global__ void __launch_bounds__(128) colv_kernel(const __grid_constant__ CUtensorMap tin, const ColvArgs a) {
   extern __shared__ __align__(128) uint8_t vsmem[];
+  pdl_launch_dependents();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int task = blockIdx.x * a.wpc + warp;
   if (task >= a.ntask) return;
@@ -26,6 +27,7 @@ __global__ void __launch_bounds__(128) colv_kernel(const __grid_constant__ CUten
     }
     __syncwarp();
   }
+  pdl_wait();
   colv_tile<T, OP>(a, &tin, task, lane, tile, bars);
 }
 
@@ -38,6 +40,8 @@ __global__ void __launch_bounds__(256) colw_kernel(const __grid_constant__ CUten
   constexpr int E = sizeof(T);
   uint64_t* bars = reinterpret_cast<uint64_t*>(wsmem + a.nbox * kCvBoxBytes);
   const int ctile = blockIdx.x;
+  pdl_launch_dependents();
+  pdl_wait();
   if (threadIdx.x == 0) {
     for (int b = 0; b < a.nbox; ++b) mbar_init(&bars[b], 1);
     fence_barrier_init();
@@ -144,9 +148,7 @@ cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream) {
   memset(&tin, 0, sizeof(tin));
   if (!encode_tensor_map_2d(&tin, L.src, E, L.W, L.H, L.sp, kCvBytes / E, kCvBox))
     return cudaErrorInvalidConfiguration;
-  note_launch();
-  k<<<p.ntile, 32 * p.nw, p.smem, stream>>>(tin, a);
-  return cudaGetLastError();
+  return launch_pdl(L.pdl, k, dim3(p.ntile), dim3(32 * p.nw), p.smem, stream, tin, a);
 }
 
 bool colv_fits(const FusedLaunch& L) {
@@ -155,7 +157,7 @@ bool colv_fits(const FusedLaunch& L) {
 
 cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int E = L.esz;
-  const ColvPlan p = colv_plan(E, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, sm_count_w());
+  const ColvPlan p = colv_plan(E, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows);
   if (!p.ok) return cudaErrorInvalidConfiguration;
   ColvArgs a;
   a.src = static_cast<const uint8_t*>(L.src);
@@ -193,9 +195,7 @@ cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
     }
   }
   const int grid = cdiv(p.ntask, p.wpc);
-  note_launch();
-  k<<<grid, 32 * p.wpc, p.smem, stream>>>(tin, a);
-  return cudaGetLastError();
+  return launch_pdl(L.pdl, k, dim3(grid), dim3(32 * p.wpc), p.smem, stream, tin, a);
 }
 
 }  // namespace morph

@@ -255,18 +255,20 @@ namespace morph {
 
 // Launch shape of the pass along y: output rows per warp tile (L), warps per
 // CTA, shared memory.  A tile of L rows scans L rows backwards and, per block
-// it touches, w - 1 rows forwards: L + ceil(L / w) * (w - 1) row steps, which
-// is least per output when L is a multiple of w (no partial block).  The
-// candidates are the multiples of w and 64; each costs its waves of
-// (SMs x resident warps) times a tile's row steps plus a fixed start-up
-// (the first boxes' latency), discounted when fewer than 6 warps per SM are
-// busy.  Warps per CTA: the choice that keeps the most warps resident.
+// it touches, w - 1 rows forwards -- L + ceil(L / w) * (w - 1) row steps,
+// fewest per output when L is a multiple of w -- while taller tiles leave
+// fewer warps resident.  The default L was measured on the GB300 (4096^2
+// images, windows of 51, 101 and 127 rows, CUDA-graph timing): for 8-bit
+// pixels 2w (at most 256), for 16-bit pixels w itself from 120 rows, else
+// 2w (at most 256) from 64 rows, else 64 -- each within 3% of the best of
+// 64, w and 2w.  Warps per CTA: the choice that keeps the most warps
+// resident per SM.
 struct ColvPlan {
   int L, nbox, wpc, ntask, smem;
   bool ok;
 };
 
-inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, int* wps_out) {
+inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L) {
   ColvPlan p{0, 0, 0, 0, 0, false};
   const int ns = (W * esz + kCvBytes - 1) / kCvBytes;
   const int nbox = (L + w - 1 + kCvBox - 1) / kCvBox;
@@ -285,44 +287,28 @@ inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, in
   if (wpc == 0) return p;
   const long long ntask = static_cast<long long>(ns) * ((H + L - 1) / L);
   if (ntask > (1ll << 30)) return p;
-  *wps_out = wps;
   return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc), true};
 }
 
-inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L, int sms = 152) {
-  ColvPlan best{0, 0, 0, 0, 0, false};
-  if (w < 2 || W < 1 || H < 1) return best;
+inline int colv_default_rows(int esz, int w) {
+  const int two = 2 * w < 256 ? 2 * w : 256;
+  if (esz == 1) return w >= 32 ? two : 64;
+  if (w >= 120 && w <= 256) return w;
+  return w >= 64 ? two : 64;
+}
+
+inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L) {
+  ColvPlan p{0, 0, 0, 0, 0, false};
+  if (w < 2 || W < 1 || H < 1) return p;
   const int hmax = H < 1024 ? H : 1024;
-  int wps = 0;
-  if (forced_L > 0) {
-    for (int L = forced_L < hmax ? forced_L : hmax; L >= 1; L -= 8) {
-      best = colv_shape(esz, W, H, w, max_smem, L, &wps);
-      if (best.ok) break;
-    }
-    return best;
-  }
-  double best_cost = 1e300;
-  auto consider = [&](int L) {
-    if (L < 1) return;
-    if (L > hmax) L = hmax;
-    const ColvPlan p = colv_shape(esz, W, H, w, max_smem, L, &wps);
-    if (!p.ok) return;
-    const double per_sm = static_cast<double>(p.ntask) / sms;
-    const double waves = static_cast<double>(static_cast<long long>((per_sm + wps - 1) / wps));
-    const double busy = per_sm < wps ? per_sm : wps;
-    const double steps = L + static_cast<double>((L + w - 1) / w) * (w - 1);
-    const double eff = busy >= 6 ? 1.0 : busy / 6.0;
-    const double cost = waves * (steps + 60.0) / eff;
-    if (cost < best_cost) {
-      best_cost = cost;
-      best = p;
-    }
-  };
-  consider(64);
-  for (int k = 1; k * w <= 1024 && k <= 16; ++k) consider(k * w);
+  int L = forced_L > 0 ? forced_L : colv_default_rows(esz, w);
+  if (L > hmax) L = hmax;
   // very long windows: shorter tiles until one fits
-  for (int L = 56; !best.ok && L >= 8; L -= 8) consider(L);
-  return best;
+  for (; L >= 1; L -= 8) {
+    p = colv_shape(esz, W, H, w, max_smem, L);
+    if (p.ok) break;
+  }
+  return p;
 }
 
 }  // namespace morph

@@ -160,6 +160,17 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel on its stream is still
+// running.  Each kernel of this library lets its successor start as soon as
+// all its CTAs have started (launch_dependents), and waits for its
+// predecessor to finish and flush its memory (wait) before touching global
+// memory; without such a launch both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Per-thread asynchronous copies global -> shared (8 or 16 bytes, both
 // addresses aligned to the size), grouped by commit; wait_group<N> returns
 // once at most N of this thread's groups are still in flight.
@@ -190,6 +201,8 @@ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y);
 void bulk_commit();
 void bulk_wait_read_all();
 void bulk_wait_all();
+inline void pdl_launch_dependents() {}
+inline void pdl_wait() {}
 void cp_async8(void* smem, const void* gmem);
 void cp_async16(void* smem, const void* gmem);
 void cp_async_commit();

@@ -166,9 +166,7 @@ cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
       if (e != cudaSuccess) return e;
       const int grid = persistent_grid(reinterpret_cast<const void*>(k), gp.smem_bytes, ntx * nty);
       if (grid > 0) {
-        note_launch();
-        k<<<grid, kThreads, gp.smem_bytes, stream>>>(tin, tout, a, gp, ntx, ntx * nty);
-        return cudaGetLastError();
+        return launch_pdl(L.pdl, k, dim3(grid), dim3(kThreads), gp.smem_bytes, stream, tin, tout, a, gp, ntx, ntx * nty);
       }
     }
   }
@@ -177,9 +175,7 @@ cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream) {
   cudaError_t e = allow_smem(reinterpret_cast<const void*>(k));
   if (e != cudaSuccess) return e;
   dim3 grid(ntx, nty);
-  note_launch();
-  k<<<grid, kThreads, g.smem_bytes, stream>>>(tin, tout, a, g);
-  return cudaGetLastError();
+  return launch_pdl(L.pdl, k, grid, dim3(kThreads), g.smem_bytes, stream, tin, tout, a, g);
 }
 
 int* device_error_word() { return fused_err_ptr(); }

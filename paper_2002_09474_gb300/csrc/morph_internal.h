@@ -46,6 +46,8 @@ struct FusedLaunch {
   int wx, wy, ax, ay;  // clipped window
   bool vhgw_col, vhgw_row;
   bool pipe;           // persistent input-prefetching kernel (set by the planner)
+  bool pdl;            // launch with programmatic stream serialisation (the
+                       // second launch of the two-launch form)
 };
 
 // Shared-memory bytes the fused kernel needs for this launch (0 if the
@@ -71,6 +73,27 @@ FusedPipeKernelFn fused_pipe_kernel_u16_dilate(int cfg);
 
 // Counts one kernel launch enqueued by the library (morph_launch_count).
 void note_launch();
+
+// Launches kernel k; with pdl, with programmatic stream serialisation: it
+// may then be scheduled while the previous kernel on the stream finishes
+// (its CTAs wait in griddepcontrol.wait before touching memory).  Counts the
+// launch.
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(bool pdl, void (*k)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
+  note_launch();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Args&&>(args)...);
+}
 
 // Enqueues the fused kernel; returns a cudaError_t.
 cudaError_t fused_launch(const FusedLaunch& L, cudaStream_t stream);

@@ -67,7 +67,11 @@ bool plan_split(const FusedLaunch& L) {
   // 15 x 15 up (15-40% faster than fused), 16-bit ones from 21 x 51 up (11%;
   // fused stays 16% faster at 15 x 15).  Also whenever the fused tile the
   // planner picks (or every fused tile) would run fewer than 3 CTAs per SM.
-  if (L.wx >= 9 && L.wy >= 9 && (L.esz == 1 || std::max(L.wx, L.wy) >= 32)) return true;
+  // (measured at 4096^2; below 2 Mpixels the second launch's fixed cost is
+  // not repaid, and the fused kernel is kept)
+  if (static_cast<long long>(L.W) * L.H >= (2ll << 20) && L.wx >= 9 && L.wy >= 9 &&
+      (L.esz == 1 || std::max(L.wx, L.wy) >= 32))
+    return true;
   FusedLaunch F = L;
   if (!plan_single(&F)) return true;
   return ctas_per_sm(fused_smem_bytes(F)) < 3;

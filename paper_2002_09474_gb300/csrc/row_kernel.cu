@@ -13,11 +13,13 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_kernel(const __grid_consta
                                                              const RowArgs a, const RowGeom g) {
   __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(128) uint8_t rsmem[];
+  pdl_launch_dependents();
   if (a.tma_ld && threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
   }
   __syncthreads();
+  pdl_wait();
   uint32_t phase = 0;
   row_tile<T, OP, BLK>(a, &tin, blockIdx.x, g, rsmem, &bar, phase);
 }
@@ -77,9 +79,7 @@ cudaError_t row_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream) 
       opted[dev & 63][slot] = reinterpret_cast<const void*>(k);
     }
   }
-  note_launch();
-  k<<<a.ntx * a.nty, kRowThreads, g.smem, stream>>>(tin, a, g);
-  return cudaGetLastError();
+  return launch_pdl(L.pdl, k, dim3(a.ntx * a.nty), dim3(kRowThreads), g.smem, stream, tin, a, g);
 }
 
 }  // namespace morph

@@ -16,9 +16,11 @@ constexpr int kRvWarps = 4;  // warps per CTA
 template <typename T, int OP>
 __global__ void __launch_bounds__(32 * kRvWarps, 4) rowv_kernel(const RowvArgs a) {
   extern __shared__ __align__(128) uint8_t rvsmem[];
+  pdl_launch_dependents();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int task = blockIdx.x * kRvWarps + warp;
   if (task >= a.ntask) return;
+  pdl_wait();
   rowv_task<T, OP>(a, task, lane, rvsmem + warp * rv_warp_smem(sizeof(T)));
 }
 
@@ -89,9 +91,7 @@ cudaError_t rowv_launch(const FusedLaunch& L, cudaStream_t stream) {
   a.ntask = p.ntask;
   const int al = 8 * L.esz;
   a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % al == 0) && (L.dp % al == 0);
-  note_launch();
-  k<<<cdiv(p.ntask, kRvWarps), 32 * kRvWarps, smem, stream>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(L.pdl, k, dim3(cdiv(p.ntask, kRvWarps)), dim3(32 * kRvWarps), smem, stream, a);
 }
 
 }  // namespace morph

@@ -63,6 +63,7 @@ _SIGS = {
     "morph_apply": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_apply_host": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_release_staging": [],
+    "morph_apply_host_batch": [ctypes.POINTER(MorphDesc), _i32, _vp],
     "morph_batch": [ctypes.POINTER(MorphDesc), _i32, _vp],
     "morph_batch_noalloc": [ctypes.POINTER(MorphDesc), _i32, _vp],
     "morph_batch_plan_create": [ctypes.POINTER(MorphDesc), _i32, ctypes.POINTER(_vp)],
@@ -147,6 +148,10 @@ def morph_apply_host(src, src_pitch, dst, dst_pitch, width, height, dtype, op, w
 
 def morph_release_staging():
     return _lib.morph_release_staging()
+
+
+def morph_apply_host_batch(descs, n, stream=0):
+    return _lib.morph_apply_host_batch(descs, n, stream)
 
 
 def morph_batch(descs, n, stream=0):

@@ -514,7 +514,7 @@ int main() {
     const bool use_colv = kern == 4 && L.wx == 1 && L.wy > 1;
     if (use_colv) {
       // the warp-tiled pass along y, planned and launched as colv_launch does
-      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200), (seed % 4 == 1) ? 3 : 152);
+      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200));
       if (!p.ok) {
         printf("FAIL case %d: no colv plan\n", cases);
         ++failures;

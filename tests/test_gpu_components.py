@@ -172,3 +172,50 @@ def test_autotune_and_cache(lib, tmp_path):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(o.cpu().numpy(), oracle.morph(img, wx, wy, wx // 2, wy // 2, "erode"))
     lib.morph_reset_tuning()
+
+
+def test_host_batch_pipeline_matches_single_calls(lib):
+    """morph_apply_host_batch (copies in, filtering and copies out of
+    consecutive images overlapped) gives every image exactly the result of
+    morph_apply_host, over more images than staging slots, mixed types,
+    sizes, windows and pitches, twice in a row."""
+    import ctypes
+    torch = need_cuda()
+    g = synth.rng(620)
+    imgs, outs, singles, descs = [], [], [], (lib.MorphDesc * 7)()
+    for i, d in enumerate(descs):
+        dt = (np.uint8, np.uint16)[i % 2]
+        h, w = int(g.integers(1, 700)), int(g.integers(1, 900))
+        img = synth.uniform_image(w, h, dt, gen=g)
+        src = torch.from_numpy(img).pin_memory()
+        out = torch.zeros_like(src).pin_memory()
+        one = torch.zeros_like(src).pin_memory()
+        wx, wy = int(g.integers(1, 130)), int(g.integers(1, 130))
+        op = i % 2
+        code = lib.MORPH_U8 if dt == np.uint8 else lib.MORPH_U16
+        pitch = w * np.dtype(dt).itemsize
+        rc = lib.morph_apply_host(src.data_ptr(), pitch, one.data_ptr(), pitch, w, h, code, op,
+                                  wx, wy, wx // 2, wy // 2, 0)
+        assert rc == 0, lib.status_string(rc)
+        d.src, d.dst, d.width, d.height = src.data_ptr(), out.data_ptr(), w, h
+        d.src_pitch = d.dst_pitch = pitch
+        d.wx, d.wy, d.anchor_x, d.anchor_y, d.op, d.dtype = wx, wy, wx // 2, wy // 2, op, code
+        imgs.append(src)
+        outs.append(out)
+        singles.append(one)
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        rc = lib.morph_apply_host_batch(descs, len(descs), 0)
+        assert rc == 0, lib.status_string(rc)
+        for i, (o, one) in enumerate(zip(outs, singles)):
+            assert torch.equal(o, one), i
+    want = oracle.morph(imgs[0].numpy(), descs[0].wx, descs[0].wy, descs[0].anchor_x,
+                        descs[0].anchor_y, "erode")
+    assert np.array_equal(outs[0].numpy(), want)
+    bad = (lib.MorphDesc * 1)()
+    ctypes.memmove(ctypes.addressof(bad), ctypes.addressof(descs), ctypes.sizeof(lib.MorphDesc))
+    bad[0].wx = 0
+    assert lib.morph_apply_host_batch(bad, 1, 0) == -3  # MORPH_ERR_WINDOW
+    lib.morph_release_staging()
+    lib.check_device_error()
