@@ -242,6 +242,13 @@ int morph_reset_tuning(void);
 int morph_set_split(int mode);
 
 /*
+ * Order of the two launches of that form (section 5: the passes commute):
+ * 0 (default) the pass along y first, 1 the pass along x first.  The result
+ * never changes.  MORPH_ERR_ARG for another order.
+ */
+int morph_set_split_order(int order);
+
+/*
  * Launch form of the fused kernel for single-image calls (no counterpart in
  * the paper: a GPU scheduling choice).  mode 1: a persistent grid (resident
  * CTAs x SMs) whose CTAs walk the tiles in turn, with two input buffers per
@@ -286,15 +293,16 @@ int morph_set_colv(int mode, int rows);
  * Kernel of the pass along x (wx x 1 windows, and the second launch of the
  * two-launch form): van Herk/Gil-Werman with blocks of 8 pixels (section
  * 5.1.1's decomposition; the whole blocks inside a window folded from their
- * totals), one warp per 8 rows and a segment of `seg` output columns, each
- * lane's block transposed in registers (section 4) so that one packed
- * min/max handles 8 rows.  Accepts 9 <= wx <= 256 when the source rows are
- * aligned to 8 bytes (u8) or 16 bytes (u16).  mode 1: this kernel wherever
- * it accepts the call; -1 (default): for 16-bit pixels with the van
- * Herk/Gil-Werman method and wx >= 32 (where it was measured faster than
- * the row kernel of morph_set_row_kernel); 0: never.  seg: output columns
- * per warp task, rounded up to a multiple of 256, or 0 for the shortest
- * segment whose tasks fit in one wave of resident warps.  The result never changes.
+ * totals), one warp per 2 (default), 4 or 8 rows and a segment of `seg`
+ * output columns, each lane's block transposed in registers (section 4) so
+ * that one packed min/max handles 2 rows.  Accepts 9 <= wx <= 256 when the
+ * source rows are aligned to 8 bytes (u8) or 16 bytes (u16).  mode 1: this
+ * kernel wherever it accepts the call; 2, 3 and 4: the same with 8, 4 and 2
+ * rows per warp; -1 (default): wherever the van Herk/Gil-Werman method is
+ * chosen (measured faster than the row kernel of morph_set_row_kernel
+ * there); 0: never.  seg: output columns per warp task,
+ * rounded up to a multiple of 256, or 0 for the shortest segment whose
+ * tasks fit in one wave of resident warps.  The result never changes.
  * MORPH_ERR_ARG for another mode or seg.
  */
 int morph_set_rowv(int mode, int seg);

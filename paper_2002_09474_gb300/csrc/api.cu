@@ -75,12 +75,11 @@ struct Scratch {
 };
 
 // The warp-tiled pass along y and the register-blocked pass along x: used
-// when forced (mode 1) and they accept the launch; in auto mode (-1) where
-// they were measured faster than the column and row kernels on the GB300
-// (4096^2 images, CUDA-graph timing): the pass along y whenever the van
-// Herk/Gil-Werman method is chosen (10-25% faster at 51, 101 and 127
-// rows), the pass along x for 16-bit pixels and windows of 32 or more (about
-// 30% faster at 101 and 127; slower at 21, and slower for 8-bit pixels).
+// when forced (mode >= 1) and they accept the launch; in auto mode (-1)
+// wherever the van Herk/Gil-Werman method is chosen, where both were
+// measured faster than the column and row kernels on the GB300 (4096^2
+// images, CUDA-graph timing): along y 10-25% at 51, 101 and 127 rows, along
+// x 19-26% (u8) and 41-59% (u16) at 21, 101 and 127 columns.
 bool use_colv(const FusedLaunch& L) {
   const int m = tuning().colv_mode;
   if (m == 0) return false;
@@ -89,7 +88,7 @@ bool use_colv(const FusedLaunch& L) {
 bool use_rowv(const FusedLaunch& L) {
   const int m = tuning().rowv_mode;
   if (m == 0) return false;
-  return (m == 1 || (L.esz == 2 && L.wx >= 32 && L.vhgw_row)) && rowv_fits(L);
+  return (m >= 1 || L.vhgw_row) && rowv_fits(L);
 }
 
 int launch_one(FusedLaunch L, cudaStream_t stream) {
@@ -164,13 +163,20 @@ int launch_planned(FusedLaunch L, cudaStream_t stream) {
   Scratch tmp;
   if (!tmp.alloc(static_cast<size_t>(L.W) * L.esz, L.H, stream)) return MORPH_ERR_NOMEM;
   FusedLaunch A = L, B = L;
-  B.pdl = true;  // the pass along x may be scheduled while the pass along y finishes
-  A.wx = 1;
-  A.ax = 0;
+  B.pdl = true;  // the second pass may be scheduled while the first finishes
+  if (tuning().split_order == 1) {  // the pass along x first
+    A.wy = 1;
+    A.ay = 0;
+    B.wx = 1;
+    B.ax = 0;
+  } else {
+    A.wx = 1;
+    A.ax = 0;
+    B.wy = 1;
+    B.ay = 0;
+  }
   A.dst = tmp.p;
   A.dp = static_cast<long long>(tmp.pitch);
-  B.wy = 1;
-  B.ay = 0;
   B.src = tmp.p;
   B.sp = static_cast<long long>(tmp.pitch);
   int rc = launch_one(A, stream);
@@ -550,6 +556,12 @@ int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg) {
   return MORPH_OK;
 }
 
+int morph_set_split_order(int order) {
+  if (order < 0 || order > 1) return MORPH_ERR_ARG;
+  tuning().split_order = order;
+  return MORPH_OK;
+}
+
 int morph_set_split(int mode) {
   if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
   tuning().split_mode = mode;
@@ -584,7 +596,7 @@ int morph_set_colv(int mode, int rows) {
 }
 
 int morph_set_rowv(int mode, int seg) {
-  if (mode < -1 || mode > 1 || seg < 0 || seg > (1 << 20)) return MORPH_ERR_ARG;
+  if (mode < -1 || mode > 4 || seg < 0 || seg > (1 << 20)) return MORPH_ERR_ARG;
   tuning().rowv_mode = mode;
   tuning().rowv_seg = seg;
   return MORPH_OK;

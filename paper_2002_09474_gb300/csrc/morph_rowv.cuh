@@ -1,16 +1,17 @@
 // Pass along x (a w x 1 element; the paper's "vertical pass", section 5.2) by
-// van Herk/Gil-Werman with 8-pixel blocks, one warp per 8 rows and a segment
-// of columns, the block data in registers.
+// van Herk/Gil-Werman with 8-pixel blocks, one warp per RR rows (4 or 8)
+// and a segment of columns, the block data in registers.
 //
 // The warp walks its segment in chunks of 256 pixels.  In a chunk, lane l
 // owns block k = 32c + l: the 8 input columns whose pixels start the windows
 // of outputs x = xs + 8k .. xs + 8k + 7 (xs the segment's first output, so
 // the block starts at input column xs - a + 8k).  It loads the block's 8 rows
-// straight from global memory (each warp load reads 256 contiguous bytes of
-// one row) and transposes them in registers into 8 "octets", one per pixel
-// column, each four 32-bit words holding the 8 rows in 16-bit lanes -- the
-// paper's transpose of section 4, so that the pass along x becomes a pass
-// over registers, 8 rows per instruction pair.
+// (each warp copy reads 256 contiguous bytes of one row) and transposes them
+// in registers into 8 column vectors, one per pixel column, each RR/2 32-bit
+// words holding the RR rows in 16-bit lanes -- the paper's transpose of
+// section 4, so that the pass along x becomes a pass over registers, two rows
+// per instruction.  Fewer rows per warp (RR = 4) halve the registers and
+// shared memory a warp needs, so twice as many warps stay resident.
 //
 // With q = (w - 1) div 8 and r = (w - 1) mod 8, output 8k + i takes the
 // window from offset i of block k to offset r + i of block k + q:
@@ -39,10 +40,12 @@ constexpr int kRvRing = 64;    // prefix ring: two chunks of blocks
 // Input chunks in flight or in use per warp: 3 for u8 (copies run two
 // chunks ahead), 2 for u16 (one chunk ahead; each chunk is twice the bytes).
 __host__ __device__ constexpr int rv_slots(int esz) { return esz == 1 ? 3 : 2; }
-// Shared memory per warp: the prefix ring (8 prefixes x kRvRing blocks x 16
-// bytes), then the input slots of 8 rows x 33 entries of 8 pixels.
-__host__ __device__ constexpr int rv_raw_off() { return 8 * kRvRing * 16; }
-__host__ __device__ constexpr int rv_warp_smem(int esz) { return rv_raw_off() + rv_slots(esz) * 8 * 33 * 8 * esz; }
+// Shared memory per warp: the prefix ring (8 prefixes x kRvRing blocks x
+// RR/2 words), then the input slots of RR rows x 33 entries of 8 pixels.
+__host__ __device__ constexpr int rv_raw_off(int rr) { return 8 * kRvRing * 2 * rr; }
+__host__ __device__ constexpr int rv_warp_smem(int esz, int rr) {
+  return rv_raw_off(rr) + rv_slots(esz) * rr * 33 * 8 * esz;
+}
 
 struct RowvArgs {
   const uint8_t* src;
@@ -52,17 +55,34 @@ struct RowvArgs {
   int w, a;          // window along x and its anchor, clipped to the image (9 <= w <= 256)
   int seg;           // output columns per segment (multiple of 256)
   int nseg;          // segments across: ceil(W / seg)
-  int ntask;         // warp tasks: ceil(H / 8) * nseg
+  int ntask;         // warp tasks: ceil(H / RR) * nseg
   int st_vec;        // 1: output rows allow aligned 8 * esz-byte stores
 };
 
-template <int OP>
-__device__ __forceinline__ uint4 rv_op(uint4 a, uint4 b) {
-  return OP == 0 ? make_uint4(__vminu2(a.x, b.x), __vminu2(a.y, b.y), __vminu2(a.z, b.z), __vminu2(a.w, b.w))
-                 : make_uint4(__vmaxu2(a.x, b.x), __vmaxu2(a.y, b.y), __vmaxu2(a.z, b.z), __vmaxu2(a.w, b.w));
+// RR rows of one pixel column: word j holds rows 2j (low lane) and 2j+1.
+template <int RR>
+struct RVec {
+  uint32_t w[RR / 2];
+};
+
+template <int OP, int RR>
+__device__ __forceinline__ RVec<RR> rv_op(const RVec<RR>& a, const RVec<RR>& b) {
+  RVec<RR> r;
+#pragma unroll
+  for (int j = 0; j < RR / 2; ++j) r.w[j] = OP == 0 ? __vminu2(a.w[j], b.w[j]) : __vmaxu2(a.w[j], b.w[j]);
+  return r;
 }
-__device__ __forceinline__ uint32_t rv_word(const uint4& v, int j) {
-  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+template <int OP, int RR>
+__device__ __forceinline__ RVec<RR> rv_ident() {
+  RVec<RR> r;
+#pragma unroll
+  for (int j = 0; j < RR / 2; ++j) r.w[j] = ident_word<OP>();
+  return r;
+}
+// Shared-memory slots hold whole vectors (8 or 16 bytes).
+template <int RR>
+__device__ __forceinline__ RVec<RR> rv_lds(const RVec<RR>* p) {
+  return *p;
 }
 
 // 8 pixels of one row starting at pixel column B (any integer), as 8 * E
@@ -124,72 +144,70 @@ __device__ __forceinline__ void rv_load_row(const uint8_t* row, int B, int dl, i
   }
 }
 
-// Transposes 8 rows of 8 pixels (R[r]: u8 words 0..1 or u16 words 0..3) into
-// octets: V[p] = pixel column p, word j = rows 2j (low lane) and 2j+1 (high
-// lane); u8 bytes are duplicated into their 16-bit lane.
-template <typename T>
-__device__ __forceinline__ void rv_transpose_in(const uint32_t (&R)[8][4], uint4 (&V)[8]) {
+// Transposes RR rows of 8 pixels (R[r]: u8 words 0..1 or u16 words 0..3) into
+// column vectors: V[p] = pixel column p; u8 bytes are duplicated into their
+// 16-bit lane.
+template <typename T, int RR>
+__device__ __forceinline__ void rv_transpose_in(const uint32_t (&R)[RR][4], RVec<RR> (&V)[8]) {
   constexpr int E = sizeof(T);
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
-    uint32_t wv[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RR / 2; ++j) {
       if (E == 1) {
         // bytes p%4 of rows 2j and 2j+1, each duplicated into its 16-bit lane
         const uint32_t sel = (p & 3) * 0x11u + (4 + (p & 3)) * 0x1100u;
-        wv[j] = __byte_perm(R[2 * j][p >> 2], R[2 * j + 1][p >> 2], sel);
+        V[p].w[j] = __byte_perm(R[2 * j][p >> 2], R[2 * j + 1][p >> 2], sel);
       } else {
-        wv[j] = __byte_perm(R[2 * j][p >> 1], R[2 * j + 1][p >> 1], (p & 1) ? 0x7632u : 0x5410u);
+        V[p].w[j] = __byte_perm(R[2 * j][p >> 1], R[2 * j + 1][p >> 1], (p & 1) ? 0x7632u : 0x5410u);
       }
     }
-    V[p] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
 }
 
-// Loads block k (8 rows from y0, 8 pixels from column B) and transposes it:
-// V[p] = pixel column p, word j = rows 2j (low lane) and 2j+1 (high lane).
-template <typename T, int OP>
-__device__ __forceinline__ void rv_load_block(const RowvArgs& a, int y0, int B, int dl, uint4 (&V)[8]) {
-  uint32_t R[8][4];
+// Loads block k (RR rows from y0, 8 pixels from column B) directly from
+// global memory and transposes it.
+template <typename T, int OP, int RR>
+__device__ __forceinline__ void rv_load_block(const RowvArgs& a, int y0, int B, int dl, RVec<RR> (&V)[8]) {
+  uint32_t R[RR][4];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
+  for (int r = 0; r < RR; ++r) {
     if (y0 + r < a.H) {
       rv_load_row<T, OP>(a.src + static_cast<long long>(y0 + r) * a.sp, B, dl, a.W, R[r]);
     } else {
       R[r][0] = R[r][1] = R[r][2] = R[r][3] = ident_word<OP>();
     }
   }
-  rv_transpose_in<T>(R, V);
+  rv_transpose_in<T, RR>(R, V);
 }
 
-// Writes the 8 x 8 output block (octets O) at rows y0.., columns x..
-// (columns < xe), transposed back to rows.
-template <typename T>
-__device__ __forceinline__ void rv_store_block(const RowvArgs& a, int y0, int x, int xe, const uint4 (&O)[8]) {
+// Writes the RR x 8 output block (column vectors O) at rows y0.., columns
+// x.. (columns < xe), transposed back to rows.
+template <typename T, int RR>
+__device__ __forceinline__ void rv_store_block(const RowvArgs& a, int y0, int x, int xe, const RVec<RR> (&O)[8]) {
   constexpr int E = sizeof(T);
-  uint32_t Rw[8][4];
+  uint32_t Rw[RR][4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < RR / 2; ++j) {
     if (E == 1) {
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
-        const uint32_t A = __byte_perm(rv_word(O[4 * g], j), rv_word(O[4 * g + 1], j), 0x6240);
-        const uint32_t Bq = __byte_perm(rv_word(O[4 * g + 2], j), rv_word(O[4 * g + 3], j), 0x6240);
+        const uint32_t A = __byte_perm(O[4 * g].w[j], O[4 * g + 1].w[j], 0x6240);
+        const uint32_t Bq = __byte_perm(O[4 * g + 2].w[j], O[4 * g + 3].w[j], 0x6240);
         Rw[2 * j][g] = __byte_perm(A, Bq, 0x5410);
         Rw[2 * j + 1][g] = __byte_perm(A, Bq, 0x7632);
       }
     } else {
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        Rw[2 * j][h] = __byte_perm(rv_word(O[2 * h], j), rv_word(O[2 * h + 1], j), 0x5410);
-        Rw[2 * j + 1][h] = __byte_perm(rv_word(O[2 * h], j), rv_word(O[2 * h + 1], j), 0x7632);
+        Rw[2 * j][h] = __byte_perm(O[2 * h].w[j], O[2 * h + 1].w[j], 0x5410);
+        Rw[2 * j + 1][h] = __byte_perm(O[2 * h].w[j], O[2 * h + 1].w[j], 0x7632);
       }
     }
   }
   const bool full = a.st_vec && x + 8 <= xe;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
+  for (int r = 0; r < RR; ++r) {
     if (y0 + r >= a.H) break;
     uint8_t* row = a.dst + static_cast<long long>(y0 + r) * a.dp;
     if (full) {
@@ -206,35 +224,34 @@ __device__ __forceinline__ void rv_store_block(const RowvArgs& a, int y0, int x,
   }
 }
 
-// One warp task: rows 8 * (task / nseg) .. +7, output columns of segment
+// One warp task: rows RR * (task / nseg) .. +RR-1, output columns of segment
 // task % nseg.  ws: this warp's shared memory (rv_warp_smem bytes): the
-// prefix ring (slot n of block b at uint4 index n * kRvRing + b), then the
+// prefix ring (slot n of block b at vector index n * kRvRing + b), then the
 // input slots.
 //
 // Input chunks travel by per-lane asynchronous copies one (u16) or two (u8)
-// chunks ahead of use: lane l copies the 8 pixels at the aligned column of its block start
-// (entry l of each row), lane 31 also the 8 after the chunk (entry 32); a
-// block's pixels are entries l and l+1 shifted by the uniform B mod 8.
-// Chunks that reach outside the image (or rows past its bottom) are loaded
-// directly instead, pixel by pixel where needed.
-template <typename T, int OP>
+// chunks ahead of use: lane l copies the 8 pixels at the aligned column of
+// its block start (entry l of each row), lane 31 also the 8 after the chunk
+// (entry 32); a block's pixels are entries l and l+1 shifted by the uniform
+// B mod 8.  Chunks that reach outside the image (or rows past its bottom)
+// are loaded directly instead, pixel by pixel where needed.
+template <typename T, int OP, int RR>
 __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane, uint8_t* ws) {
   constexpr int E = sizeof(T), EB = 8 * E;  // bytes per entry
   constexpr int NS = rv_slots(E), D = NS - 1;  // input slots, chunks copied ahead
-  uint4* pb = reinterpret_cast<uint4*>(ws);
-  uint8_t* raw = ws + rv_raw_off();
-  const int y0 = 8 * (task / a.nseg);
+  using V = RVec<RR>;
+  V* pb = reinterpret_cast<V*>(ws);
+  uint8_t* raw = ws + rv_raw_off(RR);
+  const int y0 = RR * (task / a.nseg);
   const int xs = (task % a.nseg) * a.seg;
   const int xe = xs + a.seg < a.W ? xs + a.seg : a.W;
   const int nck = (xe - xs + kRvChunk - 1) / kRvChunk;  // output chunks
   const int X0 = xs - a.a;                                // input column of block 0
   const int dl = ((X0 % 8) + 8) % 8;
   const int q = (a.w - 1) >> 3, r = (a.w - 1) & 7;
-  const uint32_t IDW = ident_word<OP>();
-  const uint4 ID4 = make_uint4(IDW, IDW, IDW, IDW);
-  const bool rows_in = y0 + 8 <= a.H;
+  const bool rows_in = y0 + RR <= a.H;
 
-  auto entry = [&](int slot, int row, int e) { return raw + ((slot * 8 + row) * 33 + e) * EB; };
+  auto entry = [&](int slot, int row, int e) { return raw + ((slot * RR + row) * 33 + e) * EB; };
   auto fast_chunk = [&](int j) {
     const int cs = X0 + kRvChunk * j - dl;
     return rows_in && cs >= 0 && cs + kRvChunk + 8 <= a.W;
@@ -243,7 +260,7 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
     if (j <= nck && fast_chunk(j)) {
       const int slot = j % NS, cs = X0 + kRvChunk * j - dl;
 #pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
+      for (int rr = 0; rr < RR; ++rr) {
         const uint8_t* row = a.src + static_cast<long long>(y0 + rr) * a.sp;
         const uint8_t* g = row + static_cast<long long>(cs + 8 * lane) * E;
         if (E == 1) cp_async8(entry(slot, rr, lane), g); else cp_async16(entry(slot, rr, lane), g);
@@ -256,15 +273,15 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
     cp_async_commit();
   };
   // Block data of chunk j from its input slot: V[p] = pixel column p.
-  auto build = [&](int j, uint4 (&V)[8]) {
+  auto build = [&](int j, V (&Vb)[8]) {
     if (!fast_chunk(j)) {
-      rv_load_block<T, OP>(a, y0, X0 + kRvChunk * j + 8 * lane, dl, V);
+      rv_load_block<T, OP, RR>(a, y0, X0 + kRvChunk * j + 8 * lane, dl, Vb);
       return;
     }
     const int slot = j % NS;
-    uint32_t R[8][4];
+    uint32_t R[RR][4];
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
+    for (int rr = 0; rr < RR; ++rr) {
       const uint8_t* p0 = entry(slot, rr, lane);
       const uint8_t* p1 = entry(slot, rr, lane + 1);
       if (E == 1) {
@@ -298,15 +315,15 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
         }
       }
     }
-    rv_transpose_in<T>(R, V);
+    rv_transpose_in<T, RR>(R, Vb);
   };
-  auto prefixes = [&](const uint4 (&V)[8], int k) {
+  auto prefixes = [&](const V (&Vb)[8], int k) {
     const int b = k & (kRvRing - 1);
-    uint4 P = V[0];
+    V P = Vb[0];
     pb[b] = P;
 #pragma unroll
     for (int n = 1; n < 8; ++n) {
-      P = rv_op<OP>(P, V[n]);
+      P = rv_op<OP, RR>(P, Vb[n]);
       pb[n * kRvRing + b] = P;
     }
   };
@@ -314,7 +331,7 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
   // One step: chunk j's block data into Vnew (and its prefixes into the
   // ring), then the outputs of chunk j-1 from Vold.  Steps alternate the two
   // arrays, so no block data is copied between them.
-  auto step = [&](int j, const uint4 (&Vold)[8], uint4 (&Vnew)[8]) {
+  auto step = [&](int j, const V (&Vold)[8], V (&Vnew)[8]) {
     issue(j + D);
     cp_async_wait<D>();
     __syncwarp();
@@ -324,26 +341,26 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
     if (j >= 1) {
       // outputs of chunk j-1: block k
       const int k = 32 * (j - 1) + lane;
-      uint4 m = ID4;  // fold of the whole blocks k+1 .. k+q-1
-      for (int t = 1; t < q; ++t) m = rv_op<OP>(m, pb[7 * kRvRing + ((k + t) & (kRvRing - 1))]);
-      uint4 S[8];  // suffixes of block k, seeded with m
-      S[7] = rv_op<OP>(Vold[7], m);
+      V m = rv_ident<OP, RR>();  // fold of the whole blocks k+1 .. k+q-1
+      for (int t = 1; t < q; ++t) m = rv_op<OP, RR>(m, rv_lds(&pb[7 * kRvRing + ((k + t) & (kRvRing - 1))]));
+      V S[8];  // suffixes of block k, seeded with m
+      S[7] = rv_op<OP, RR>(Vold[7], m);
 #pragma unroll
-      for (int i = 6; i >= 0; --i) S[i] = rv_op<OP>(Vold[i], S[i + 1]);
+      for (int i = 6; i >= 0; --i) S[i] = rv_op<OP, RR>(Vold[i], S[i + 1]);
       const int bq = (k + q) & (kRvRing - 1), bq1 = (k + q + 1) & (kRvRing - 1);
-      const uint4 Tq = pb[7 * kRvRing + bq];
+      const V Tq = rv_lds(&pb[7 * kRvRing + bq]);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int n = r + i;
-        const uint4 Pv = n < 8 ? pb[n * kRvRing + bq] : rv_op<OP>(Tq, pb[(n - 8) * kRvRing + bq1]);
-        S[i] = rv_op<OP>(S[i], Pv);
+        const V Pv = n < 8 ? rv_lds(&pb[n * kRvRing + bq]) : rv_op<OP, RR>(Tq, rv_lds(&pb[(n - 8) * kRvRing + bq1]));
+        S[i] = rv_op<OP, RR>(S[i], Pv);
       }
       const int x = xs + 8 * k;
-      if (x < xe) rv_store_block<T>(a, y0, x, xe, S);
+      if (x < xe) rv_store_block<T, RR>(a, y0, x, xe, S);
     }
     __syncwarp();
   };
-  uint4 VA[8], VB[8];
+  V VA[8], VB[8];
   for (int j = 0; j < D; ++j) issue(j);
   for (int j = 0; j <= nck; j += 2) {
     step(j, VB, VA);
@@ -361,25 +378,25 @@ struct RowvPlan {
   int seg, nseg, ntask;
   bool ok;
 };
-inline RowvPlan rowv_plan(int W, int H, int sms, int wps, int forced_seg) {
+inline RowvPlan rowv_plan(int W, int H, int rr, int sms, int wps, int forced_seg) {
   RowvPlan best{0, 0, 0, false};
   if (W < 1 || H < 1 || sms < 1) return best;
   const int wmax = (W + kRvChunk - 1) / kRvChunk * kRvChunk;
   const long long slots = static_cast<long long>(sms) * wps;
-  const long long octets = (H + 7) / 8;
+  const long long bands = (H + rr - 1) / rr;
   int seg = wmax;
   if (forced_seg > 0) {
     seg = (forced_seg + kRvChunk - 1) / kRvChunk * kRvChunk;
     if (seg > wmax) seg = wmax;
   } else {
     for (int s = kRvChunk; s <= wmax; s += kRvChunk)
-      if (octets * ((W + s - 1) / s) <= slots) {
+      if (bands * ((W + s - 1) / s) <= slots) {
         seg = s;
         break;
       }
   }
   const int nseg = (W + seg - 1) / seg;
-  const long long ntask = octets * nseg;
+  const long long ntask = bands * nseg;
   if (ntask > (1ll << 30)) return best;
   return RowvPlan{seg, nseg, static_cast<int>(ntask), true};
 }

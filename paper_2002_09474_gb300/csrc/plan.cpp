@@ -85,6 +85,7 @@ void reset_tuning_defaults() {
     g_tuning.xpass_transpose[e] = 0;
   }
   g_tuning.split_mode = -1;
+  g_tuning.split_order = 0;
   g_tuning.pipe_mode = -1;
   g_tuning.col_mode = -1;
   g_tuning.row_mode = -1;

@@ -76,6 +76,7 @@ _SIGS = {
     "morph_set_tuning": [_i32, _i32, _i32, _i32],
     "morph_reset_tuning": [],
     "morph_set_split": [_i32],
+    "morph_set_split_order": [_i32],
     "morph_set_pipeline": [_i32],
     "morph_set_column_kernel": [_i32],
     "morph_set_row_kernel": [_i32],
@@ -192,6 +193,10 @@ def morph_set_tuning(dtype, cross_row, cross_col, tile_cfg):
 
 def morph_set_split(mode):
     return _lib.morph_set_split(mode)
+
+
+def morph_set_split_order(order):
+    return _lib.morph_set_split_order(order)
 
 
 def morph_set_pipeline(mode):

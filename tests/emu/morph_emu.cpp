@@ -587,7 +587,8 @@ int main() {
     const bool use_rowv = kern == 5 && L.wy == 1 && L.wx >= 9 && L.wx <= 256 &&
                           reinterpret_cast<uintptr_t>(src) % ral == 0 && sp % ral == 0;
     if (use_rowv) {
-      const RowvPlan p = rowv_plan(W, H, (seed & 1) ? 152 : 3, 12, (seed % 3 == 0) ? 256 * static_cast<int>(1 + seed % 5) : 0);
+      const int rr = (seed / 2) % 3 == 0 ? 8 : (seed / 2) % 3 == 1 ? 4 : 2;  // rows per warp
+      const RowvPlan p = rowv_plan(W, H, rr, (seed & 1) ? 152 : 3, 12, (seed % 3 == 0) ? 256 * static_cast<int>(1 + seed % 5) : 0);
       col_ty = p.seg;
       RowvArgs ra{};
       ra.src = src;
@@ -603,8 +604,12 @@ int main() {
       ra.ntask = p.ntask;
       ra.st_vec = (reinterpret_cast<uintptr_t>(dst) % ral == 0) && (dp % ral == 0);
       using RvFn = void (*)(const RowvArgs&, int, int, uint8_t*);
-      RvFn rf = esz == 1 ? (op == 0 ? rowv_task<uint8_t, 0> : rowv_task<uint8_t, 1>)
-                         : (op == 0 ? rowv_task<uint16_t, 0> : rowv_task<uint16_t, 1>);
+      RvFn rf = rr == 8 ? (esz == 1 ? (op == 0 ? rowv_task<uint8_t, 0, 8> : rowv_task<uint8_t, 1, 8>)
+                                    : (op == 0 ? rowv_task<uint16_t, 0, 8> : rowv_task<uint16_t, 1, 8>))
+              : rr == 4 ? (esz == 1 ? (op == 0 ? rowv_task<uint8_t, 0, 4> : rowv_task<uint8_t, 1, 4>)
+                                    : (op == 0 ? rowv_task<uint16_t, 0, 4> : rowv_task<uint16_t, 1, 4>))
+                        : (esz == 1 ? (op == 0 ? rowv_task<uint8_t, 0, 2> : rowv_task<uint8_t, 1, 2>)
+                                    : (op == 0 ? rowv_task<uint16_t, 0, 2> : rowv_task<uint16_t, 1, 2>));
       const int wpc = 4;
       for (int blk = 0; blk < cdiv(p.ntask, wpc); ++blk) {
         EmuCta cta;
@@ -615,8 +620,8 @@ int main() {
           cta.wbar[w] = wb.back().get();
         }
         cta.bar = &bar;
-        const size_t smb = static_cast<size_t>(wpc) * rv_warp_smem(esz);
-        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, smb));
+        const size_t smb = static_cast<size_t>(wpc) * rv_warp_smem(esz, rr);
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (smb + 127) / 128 * 128));
         cta.smem = sm;
         cta.smem_size = smb;
         pool_run(
@@ -625,7 +630,7 @@ int main() {
               emu_threadIdx = make_uint3(tid, 0, 0);
               const int warp = tid >> 5, lane = tid & 31, task = blk * wpc + warp;
               if (task >= p.ntask) return;
-              rf(ra, task, lane, sm + warp * rv_warp_smem(esz));
+              rf(ra, task, lane, sm + warp * rv_warp_smem(esz, rr));
             },
             32 * wpc);
         free(sm);

@@ -80,12 +80,14 @@ def test_pass_along_y_shared_tile(lib, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("rows", [2, 3, 4])
 @pytest.mark.parametrize("seg", [0, 256, 512, 2048])
-def test_pass_along_x_register_blocked(lib, dtype, seg):
+def test_pass_along_x_register_blocked(lib, dtype, rows, seg):
+    """rows: mode 2, 3 or 4 (8, 4 or 2 rows per warp)."""
     torch = need_cuda()
-    g = synth.rng(400 + seg)
+    g = synth.rng(400 + seg + rows)
     try:
-        assert lib.morph_set_rowv(1, seg) == 0
+        assert lib.morph_set_rowv(rows, seg) == 0
         for (h, w) in ((1, 64), (37, 300), (300, 37), (64, 1000), (13, 2049), (70, 257)):
             img = synth.uniform_image(w, h, dtype, gen=g)
             for i, (wx, ax) in enumerate(windows_1d(w)):
@@ -138,9 +140,12 @@ def test_two_launch_form_with_new_passes(lib, dtype):
                 for op in ("erode", "dilate"):
                     want = oracle.morph(img, wx, wy, ax, ay, op)
                     pad = aligned_pad(w, dtype)
-                    got = run(lib, torch, img, wx, wy, ax, ay, op, pad=pad, dst_pad=pad)
-                    assert np.array_equal(got, want), (h, w, wx, wy, op)
+                    for order in (0, 1):
+                        assert lib.morph_set_split_order(order) == 0
+                        got = run(lib, torch, img, wx, wy, ax, ay, op, pad=pad, dst_pad=pad)
+                        assert np.array_equal(got, want), (h, w, wx, wy, op, order)
     finally:
         lib.morph_set_split(-1)
+        lib.morph_set_split_order(0)
         lib.morph_set_colv(-1, 0)
         lib.morph_set_rowv(-1, 0)
