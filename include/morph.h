@@ -231,11 +231,11 @@ int morph_reset_tuning(void);
  * separable, so erosion by wx x wy is erosion by 1 x wy followed by wx x 1).
  * mode -1 (default): two launches through an intermediate image the
  * library allocates stream-ordered for images of at least 2 Mpixels when
- * both window sides are at least 9 and the pixels are 8-bit or the longer
- * side is at least 32 (where the single-pass kernels were measured faster
- * than the fused kernel on the GB300), or when the fused tile is so large
- * that fewer than 3 CTAs fit on an SM; otherwise both passes fused in one
- * kernel.  0: always fused; 1:
+ * both passes take the van Herk/Gil-Werman method (both window sides above
+ * the crossovers of morph_set_tuning; there the single-pass kernels were
+ * measured faster than the fused kernel on the GB300), or when the fused
+ * tile is so large that fewer than 3 CTAs fit on an SM; otherwise both
+ * passes fused in one kernel.  0: always fused; 1:
  * always two launches.  The result never
  * changes.
  */
@@ -243,10 +243,24 @@ int morph_set_split(int mode);
 
 /*
  * Order of the two launches of that form (section 5: the passes commute):
- * 0 (default) the pass along y first, 1 the pass along x first.  The result
- * never changes.  MORPH_ERR_ARG for another order.
+ * 1 (default) the pass along x first, 0 the pass along y first.  On the
+ * GB300 the pass along x first was measured 6-13% faster (at 4096^2, 15 x 15
+ * to 127 x 127): the pass along y then reads the intermediate image while it
+ * is still in L2.  The result never changes.  MORPH_ERR_ARG for another
+ * order.
  */
 int morph_set_split_order(int order);
+
+/*
+ * Whether the second launch of that form uses programmatic dependent launch
+ * (1): it may then be scheduled while the first finishes, its CTAs waiting
+ * in griddepcontrol.wait before touching memory.  0 (default) launches it
+ * after the first has finished.  On the GB300, 1 saved about 1% on one
+ * stream but cost 12% when independent calls ran on two streams (the
+ * waiting CTAs hold SMs the other stream could use).  A GPU scheduling
+ * choice; the result never changes.  MORPH_ERR_ARG for another value.
+ */
+int morph_set_split_pdl(int on);
 
 /*
  * Launch form of the fused kernel for single-image calls (no counterpart in

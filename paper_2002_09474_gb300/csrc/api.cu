@@ -157,13 +157,14 @@ int launch_transposed_x(const FusedLaunch& L, cudaStream_t stream) {
 int launch_planned(FusedLaunch L, cudaStream_t stream) {
   if (L.wx > 1 && tuning().xpass_transpose[L.esz - 1]) return launch_transposed_x(L, stream);
   if (!plan_split(L)) return launch_one(L, stream);
-  // Split form (section 5's separability): the 1 x wy pass into an
-  // intermediate image, then the wx x 1 pass from it.  The intermediate is a
+  // Split form (section 5's separability): one 1-D pass into an
+  // intermediate image, then the other from it (the pass along x first by
+  // default).  The intermediate is a
   // stream-ordered allocation (16-byte rows, so both launches can use TMA).
   Scratch tmp;
   if (!tmp.alloc(static_cast<size_t>(L.W) * L.esz, L.H, stream)) return MORPH_ERR_NOMEM;
   FusedLaunch A = L, B = L;
-  B.pdl = true;  // the second pass may be scheduled while the first finishes
+  B.pdl = tuning().split_pdl != 0;  // the second pass may be scheduled while the first finishes
   if (tuning().split_order == 1) {  // the pass along x first
     A.wy = 1;
     A.ay = 0;
@@ -559,6 +560,12 @@ int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg) {
 int morph_set_split_order(int order) {
   if (order < 0 || order > 1) return MORPH_ERR_ARG;
   tuning().split_order = order;
+  return MORPH_OK;
+}
+
+int morph_set_split_pdl(int on) {
+  if (on < 0 || on > 1) return MORPH_ERR_ARG;
+  tuning().split_pdl = on;
   return MORPH_OK;
 }
 

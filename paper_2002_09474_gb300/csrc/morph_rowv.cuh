@@ -341,7 +341,10 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
     if (j >= 1) {
       // outputs of chunk j-1: block k
       const int k = 32 * (j - 1) + lane;
-      V m = rv_ident<OP, RR>();  // fold of the whole blocks k+1 .. k+q-1
+      // fold of the whole blocks k+1 .. k+q-1 (a sparse table of pairwise
+      // folds was measured slower at q of 12-15: its warp synchronisations
+      // cost more than the loads they save)
+      V m = rv_ident<OP, RR>();
       for (int t = 1; t < q; ++t) m = rv_op<OP, RR>(m, rv_lds(&pb[7 * kRvRing + ((k + t) & (kRvRing - 1))]));
       V S[8];  // suffixes of block k, seeded with m
       S[7] = rv_op<OP, RR>(Vold[7], m);

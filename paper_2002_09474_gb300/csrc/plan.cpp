@@ -61,17 +61,18 @@ bool plan_split(const FusedLaunch& L) {
   if (L.wx <= 1 || L.wy <= 1) return false;
   if (t.split_mode == 0) return false;
   if (t.split_mode == 1) return true;
-  // auto: two launches when both passes are long enough for the single-pass
-  // kernels to pay for the second trip through memory (the intermediate
-  // mostly stays in L2): measured on the GB300 at 4096^2, 8-bit images from
-  // 15 x 15 up (15-40% faster than fused), 16-bit ones from 21 x 51 up (11%;
-  // fused stays 16% faster at 15 x 15).  Also whenever the fused tile the
-  // planner picks (or every fused tile) would run fewer than 3 CTAs per SM.
-  // (measured at 4096^2; below 2 Mpixels the second launch's fixed cost is
-  // not repaid, and the fused kernel is kept)
-  if (static_cast<long long>(L.W) * L.H >= (2ll << 20) && L.wx >= 9 && L.wy >= 9 &&
-      (L.esz == 1 || std::max(L.wx, L.wy) >= 32))
-    return true;
+  // auto: two launches when both passes take the van Herk/Gil-Werman method
+  // (above the crossovers), i.e. run on the single-pass kernels, which then
+  // pay for the second trip through memory (the intermediate mostly stays
+  // in L2).  Measured on the GB300 at 4096^2: 15 x 15 to 127 x 127 run
+  // 6-50% faster as two launches; with a direct-method pass (3 x 3 to 9 x 9)
+  // the fused kernel is 7-39% faster.  Below 2 Mpixels the second launch's
+  // fixed cost is not repaid, and the fused kernel is kept.  Also whenever
+  // the fused tile the planner picks (or every fused tile) would run fewer
+  // than 3 CTAs per SM.
+  const int e = L.esz - 1;
+  const bool vhgw_y = L.wy > t.cross_col[e] && L.wy >= 8, vhgw_x = L.wx > t.cross_row[e] && L.wx >= 8;
+  if (static_cast<long long>(L.W) * L.H >= (2ll << 20) && vhgw_x && vhgw_y) return true;
   FusedLaunch F = L;
   if (!plan_single(&F)) return true;
   return ctas_per_sm(fused_smem_bytes(F)) < 3;
@@ -85,7 +86,8 @@ void reset_tuning_defaults() {
     g_tuning.xpass_transpose[e] = 0;
   }
   g_tuning.split_mode = -1;
-  g_tuning.split_order = 0;
+  g_tuning.split_order = 1;
+  g_tuning.split_pdl = 0;
   g_tuning.pipe_mode = -1;
   g_tuning.col_mode = -1;
   g_tuning.row_mode = -1;

@@ -13,7 +13,8 @@ struct Tuning {
   int cross_row[2];  // [esz-1]: pass along x uses the direct method iff wx <= cross_row
   int forced_cfg[2];              // [esz-1]: tile configuration to use when it fits (-1: cost model)
   int split_mode;                 // 2-D windows as two 1-D launches: -1 auto, 0 never, 1 always
-  int split_order;                // their order: 0 pass along y first, 1 pass along x first
+  int split_order;                // their order: 0 pass along y first, 1 (default) pass along x first
+  int split_pdl;                  // their second launch with programmatic stream serialisation (0, default: no)
   int pipe_mode;                  // persistent input-prefetching kernel: -1 auto, 0 never, 1 always
   int xpass_transpose[2];         // [esz-1]: pass along x through the transpose kernels (1) or fused (0)
   int col_mode;                   // 1 x wy windows by the column kernel: -1 auto (yes), 0 never, 1 always

@@ -77,6 +77,7 @@ _SIGS = {
     "morph_reset_tuning": [],
     "morph_set_split": [_i32],
     "morph_set_split_order": [_i32],
+    "morph_set_split_pdl": [_i32],
     "morph_set_pipeline": [_i32],
     "morph_set_column_kernel": [_i32],
     "morph_set_row_kernel": [_i32],
@@ -197,6 +198,10 @@ def morph_set_split(mode):
 
 def morph_set_split_order(order):
     return _lib.morph_set_split_order(order)
+
+
+def morph_set_split_pdl(on):
+    return _lib.morph_set_split_pdl(on)
 
 
 def morph_set_pipeline(mode):

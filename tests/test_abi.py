@@ -123,5 +123,6 @@ def test_tuning_arguments():
     assert m.morph_set_colv(-1, 2000) == -10 and m.morph_set_colv(-1, 0) == 0
     assert m.morph_set_rowv(5, 0) == -10 and m.morph_set_rowv(-1, -2) == -10
     assert m.morph_set_rowv(-1, 0) == 0
-    assert m.morph_set_split_order(2) == -10 and m.morph_set_split_order(0) == 0
+    assert m.morph_set_split_order(2) == -10 and m.morph_set_split_order(1) == 0
+    assert m.morph_set_split_pdl(2) == -10 and m.morph_set_split_pdl(1) == 0
     assert m.morph_reset_tuning() == 0

@@ -146,6 +146,6 @@ def test_two_launch_form_with_new_passes(lib, dtype):
                         assert np.array_equal(got, want), (h, w, wx, wy, op, order)
     finally:
         lib.morph_set_split(-1)
-        lib.morph_set_split_order(0)
+        lib.morph_set_split_order(1)
         lib.morph_set_colv(-1, 0)
         lib.morph_set_rowv(-1, 0)
