@@ -297,7 +297,8 @@ int morph_set_column_kernel(int mode);
  * but for wy > 32 and TMA-loadable rows a shared-tile form in which the
  * warps of a CTA share one input tile and keep the block suffix of their 32
  * or 64 output rows in registers (measured slower on the GB300, so not a
- * default).  rows: output rows per warp tile, 1 to 1024, or 0 for the
+ * default); 4: as 1, with strips 256 bytes wide, each lane owning two
+ * words (two independent scan chains per lane).  rows: output rows per warp tile, 1 to 1024, or 0 for the
  * measured default (wy or 2 wy up to 256, or 64).  The result never
  * changes.  MORPH_ERR_ARG for another mode or rows.
  */

@@ -596,7 +596,7 @@ int morph_set_row_kernel(int mode) {
 }
 
 int morph_set_colv(int mode, int rows) {
-  if (mode < -1 || mode > 2 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
+  if (mode < -1 || mode > 4 || mode == 3 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
   tuning().colv_mode = mode;
   tuning().colv_rows = rows;
   return MORPH_OK;

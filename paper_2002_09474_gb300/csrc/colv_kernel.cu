@@ -11,15 +11,15 @@
 
 namespace morph {
 
-template <typename T, int OP>
+template <typename T, int OP, int NWL>
 __global__ void __launch_bounds__(128) colv_kernel(const __grid_constant__ CUtensorMap tin, const ColvArgs a) {
   extern __shared__ __align__(128) uint8_t vsmem[];
   pdl_launch_dependents();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int task = blockIdx.x * a.wpc + warp;
   if (task >= a.ntask) return;
-  uint8_t* tile = vsmem + warp * colv_tile_bytes(a.nbox);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(vsmem + a.wpc * colv_tile_bytes(a.nbox)) + warp * a.nbox;
+  uint8_t* tile = vsmem + warp * colv_tile_bytes(a.nbox, NWL);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(vsmem + a.wpc * colv_tile_bytes(a.nbox, NWL)) + warp * a.nbox;
   if (a.tma_ld) {
     if (lane == 0) {
       for (int b = 0; b < a.nbox; ++b) mbar_init(&bars[b], 1);
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(128) colv_kernel(const __grid_constant__ CUten
     __syncwarp();
   }
   pdl_wait();
-  colv_tile<T, OP>(a, &tin, task, lane, tile, bars);
+  colv_tile<T, OP, NWL>(a, &tin, task, lane, tile, bars);
 }
 
 // The shared-tile form (w > LW): thread 0 issues the CTA tile's boxes, every
@@ -79,10 +79,17 @@ int sm_count_w() {
   return n;
 }
 
-ColvFn colv_kernel_for(int esz, int op) {
-  if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0> : colv_kernel<uint8_t, 1>;
-  return op == 0 ? colv_kernel<uint16_t, 0> : colv_kernel<uint16_t, 1>;
+ColvFn colv_kernel_for(int esz, int op, int nwl) {
+  if (nwl == 2) {
+    if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0, 2> : colv_kernel<uint8_t, 1, 2>;
+    return op == 0 ? colv_kernel<uint16_t, 0, 2> : colv_kernel<uint16_t, 1, 2>;
+  }
+  if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0, 1> : colv_kernel<uint8_t, 1, 1>;
+  return op == 0 ? colv_kernel<uint16_t, 0, 1> : colv_kernel<uint16_t, 1, 1>;
 }
+
+// Words per lane: 2 when forced (colv mode 4), else 1.
+int colv_words() { return tuning().colv_mode == 4 ? 2 : 1; }
 
 
 }  // namespace
@@ -152,12 +159,12 @@ cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream) {
 }
 
 bool colv_fits(const FusedLaunch& L) {
-  return L.wy >= 2 && colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows).ok;
+  return L.wy >= 2 && colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, colv_words()).ok;
 }
 
 cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int E = L.esz;
-  const ColvPlan p = colv_plan(E, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows);
+  const ColvPlan p = colv_plan(E, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, colv_words());
   if (!p.ok) return cudaErrorInvalidConfiguration;
   ColvArgs a;
   a.src = static_cast<const uint8_t*>(L.src);
@@ -170,24 +177,24 @@ cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
   a.a = L.ay;
   a.L = p.L;
   a.nbox = p.nbox;
-  a.ns = cdiv(L.W * E, kCvBytes);
+  a.ns = cdiv(L.W * E, kCvBytes * p.nwl);
   a.ntask = p.ntask;
   a.wpc = p.wpc;
   a.ld_vec = (reinterpret_cast<uintptr_t>(L.src) % 4 == 0) && (L.sp % 4 == 0);
-  a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % 4 == 0) && (L.dp % 4 == 0);
+  a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % (4 * p.nwl) == 0) && (L.dp % (4 * p.nwl) == 0);
   a.err = device_error_word();
   if (!a.err) return cudaErrorInvalidDevice;
   CUtensorMap tin;
   memset(&tin, 0, sizeof(tin));
-  a.tma_ld = encode_tensor_map_2d(&tin, L.src, E, L.W, L.H, L.sp, kCvBytes / E, kCvBox) ? 1 : 0;
-  ColvFn k = colv_kernel_for(E, L.op);
+  a.tma_ld = encode_tensor_map_2d(&tin, L.src, E, L.W, L.H, L.sp, kCvBytes * p.nwl / E, kCvBox) ? 1 : 0;
+  ColvFn k = colv_kernel_for(E, L.op, p.nwl);
   static std::mutex mu;
-  static const void* opted[64][4] = {};
+  static const void* opted[64][8] = {};
   {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
-    const int slot = (E - 1) * 2 + L.op;
+    const int slot = (E - 1) * 4 + L.op * 2 + (p.nwl == 2 ? 1 : 0);
     if (opted[dev & 63][slot] != reinterpret_cast<const void*>(k)) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
       if (e != cudaSuccess) return e;

@@ -49,14 +49,15 @@ struct ColvArgs {
   int wpc;           // warps per CTA
   int tma_ld;        // 1: input boxes arrive by TMA
   int ld_vec;        // 1: rows allow aligned 32-bit loads
-  int st_vec;        // 1: rows allow aligned 32-bit stores
+  int st_vec;        // 1: rows allow aligned stores of a lane's words (4 * words per lane bytes)
   int* err;          // device error word
 };
 
-// Shared memory of one CTA: wpc warp tiles, then wpc * nbox mbarriers.
-__host__ __device__ inline int colv_tile_bytes(int nbox) { return nbox * kCvBoxBytes; }
-__host__ __device__ inline int colv_smem_bytes(int nbox, int wpc) {
-  return wpc * colv_tile_bytes(nbox) + wpc * nbox * 8;
+// Shared memory of one CTA: wpc warp tiles (boxes of 32 rows of 128 * nwl
+// bytes), then wpc * nbox mbarriers.
+__host__ __device__ inline int colv_tile_bytes(int nbox, int nwl = 1) { return nbox * kCvBoxBytes * nwl; }
+__host__ __device__ inline int colv_smem_bytes(int nbox, int wpc, int nwl = 1) {
+  return wpc * colv_tile_bytes(nbox, nwl) + wpc * nbox * 8;
 }
 
 // Two 16-bit-lane carriers of one 32-bit word (u8: odd pixels in v[0], even
@@ -101,14 +102,44 @@ __device__ __forceinline__ void colv_store(const ColvArgs& a, int y, int px0, ui
   }
 }
 
-// One warp tile.  tile: this warp's shared memory (nbox boxes); bars: its
-// nbox mbarriers, initialised with count 1.  lane: 0..31.  Returns false
-// when a bounded wait gave up (error word set by lane 0).
-template <typename T, int OP>
+// NWL 32-bit words of one row of a lane's column (NWL = 1 or 2).
+template <int NWL>
+struct Wd {
+  uint32_t v[NWL];
+};
+template <int NWL>
+__device__ __forceinline__ Wd<NWL> wd_ld(const uint8_t* p) {
+  Wd<NWL> w;
+  if (NWL == 2) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    w.v[0] = u.x;
+    w.v[NWL - 1] = u.y;
+  } else {
+    w.v[0] = *reinterpret_cast<const uint32_t*>(p);
+  }
+  return w;
+}
+template <int NWL>
+__device__ __forceinline__ void wd_st(uint8_t* p, const Wd<NWL>& w) {
+  if (NWL == 2)
+    *reinterpret_cast<uint2*>(p) = make_uint2(w.v[0], w.v[NWL - 1]);
+  else
+    *reinterpret_cast<uint32_t*>(p) = w.v[0];
+}
+
+// One warp tile.  tile: this warp's shared memory (nbox boxes of 32 rows of
+// 128 * NWL bytes); bars: its nbox mbarriers, initialised with count 1.
+// lane: 0..31, owning bytes 4 NWL lane .. 4 NWL lane + 4 NWL - 1 of each row
+// of the strip.  Two words per lane give each lane two independent scan
+// chains.  Returns false when a bounded wait gave up (error word set by lane
+// 0).
+template <typename T, int OP, int NWL = 1>
 __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* tin, int task, int lane,
                                           uint8_t* tile, uint64_t* bars) {
   constexpr int E = sizeof(T), PPW = 4 / E;
+  constexpr int SB = kCvBytes * NWL, BOXB = SB * kCvBox;  // strip bytes, box bytes
   using C = Cw<E>;
+  using Wv = Wd<NWL>;
   const uint32_t IDW = ident_word<OP>();
   const int s = task % a.ns;                  // strip
   const int y0 = (task / a.ns) * a.L;         // first output row
@@ -117,38 +148,45 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
   const int ys = y0 - a.a;                    // image row of tile row 0
   const int nin = Lr + w - 1;                 // input rows
   const int nb = (nin + kCvBox - 1) / kCvBox;  // boxes to fill
-  const int px0 = s * (kCvBytes / E) + lane * PPW;
+  const int px0 = s * (SB / E) + lane * PPW * NWL;  // the lane's first pixel
   const bool col_in = px0 < a.W;
-  const bool fast = a.st_vec && px0 + PPW <= a.W;
-  uint8_t* col = tile + 4 * lane;
+  const bool fast = a.st_vec && px0 + PPW * NWL <= a.W;
+  uint8_t* col = tile + 4 * NWL * lane;
 
-  auto LD = [&](int r) { return *reinterpret_cast<const uint32_t*>(col + r * kCvBytes); };
-  auto ST = [&](int r, uint32_t v) { *reinterpret_cast<uint32_t*>(col + r * kCvBytes) = v; };
+  auto LD = [&](int r) { return wd_ld<NWL>(col + r * SB); };
+  auto ST = [&](int r, const Wv& v) { wd_st<NWL>(col + r * SB, v); };
+  Wv IDV;
+#pragma unroll
+  for (int i = 0; i < NWL; ++i) IDV.v[i] = IDW;
 
   int have = 0;  // boxes landed (and fixed up)
   if (a.tma_ld) {
     if (lane == 0) {
       fence_proxy_async_smem();
       for (int b = 0; b < nb; ++b) {
-        mbar_arrive_expect_tx(&bars[b], static_cast<uint32_t>(kCvBoxBytes));
-        tma_load_2d(tile + b * kCvBoxBytes, tin, &bars[b], s * (kCvBytes / E), ys + b * kCvBox);
+        mbar_arrive_expect_tx(&bars[b], static_cast<uint32_t>(BOXB));
+        tma_load_2d(tile + b * BOXB, tin, &bars[b], s * (SB / E), ys + b * kCvBox);
       }
     }
   } else {
     for (int r = 0; r < nin; ++r) {
       const int y = ys + r;
-      uint32_t v = IDW;
-      if (y >= 0 && y < a.H && col_in) {
+      Wv v = IDV;
+      if (y >= 0 && y < a.H) {
         const uint8_t* row = a.src + static_cast<long long>(y) * a.sp;
-        if (a.ld_vec && px0 + PPW <= a.W) {
-          v = *reinterpret_cast<const uint32_t*>(row + static_cast<long long>(px0) * E);
-        } else {
 #pragma unroll
-          for (int t = 0; t < PPW; ++t)
-            if (px0 + t < a.W) {
-              const uint32_t sh = 8 * E * t, m = (E == 1 ? 0xFFu : 0xFFFFu) << sh;
-              v = (v & ~m) | (static_cast<uint32_t>(reinterpret_cast<const T*>(row)[px0 + t]) << sh);
-            }
+        for (int i = 0; i < NWL; ++i) {
+          const int p0 = px0 + i * PPW;
+          if (a.ld_vec && p0 + PPW <= a.W) {
+            v.v[i] = *reinterpret_cast<const uint32_t*>(row + static_cast<long long>(p0) * E);
+          } else {
+#pragma unroll
+            for (int t = 0; t < PPW; ++t)
+              if (p0 + t < a.W) {
+                const uint32_t sh = 8 * E * t, m = (E == 1 ? 0xFFu : 0xFFFFu) << sh;
+                v.v[i] = (v.v[i] & ~m) | (static_cast<uint32_t>(reinterpret_cast<const T*>(row)[p0 + t]) << sh);
+              }
+          }
         }
       }
       ST(r, v);
@@ -172,10 +210,20 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
         const int r0 = have * kCvBox;
         if (ys + r0 < 0 || ys + r0 + kCvBox > a.H)
           for (int r = r0; r < r0 + kCvBox; ++r)
-            if (ys + r < 0 || ys + r >= a.H) ST(r, IDW);
+            if (ys + r < 0 || ys + r >= a.H) ST(r, IDV);
       }
     }
     return true;
+  };
+  // stores output row y from the lane's words
+  auto store = [&](int y, const Wv& v, bool vec) {
+    if (vec) {
+      wd_st<NWL>(a.dst + static_cast<long long>(y) * a.dp + static_cast<long long>(px0) * E, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < NWL; ++i)
+        if (px0 + i * PPW < a.W) colv_store<T>(a, y, px0 + i * PPW, v.v[i], false);
+    }
   };
 
   // Rows move between shared memory and registers 8 at a time: the 8 loads
@@ -191,59 +239,80 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
     const int lo = E0 - w > 0 ? E0 - w : 0;
     if (!ensure(E0 + w - 1)) return false;
     // h-scan, rows E0-1 down to lo, in place
-    C h = IDC;
+    C h[NWL];
+#pragma unroll
+    for (int i = 0; i < NWL; ++i) h[i] = IDC;
     int r = E0 - 1;
     for (; r - (kB - 1) >= lo; r -= kB) {
-      uint32_t x[kB];
+      Wv x[kB];
 #pragma unroll
       for (int t = 0; t < kB; ++t) x[t] = LD(r - t);
 #pragma unroll
-      for (int t = 0; t < kB; ++t) {
-        h = cw_op<OP, E>(h, cw_of<E>(x[t]));
-        x[t] = cw_word<E>(h);
-      }
+      for (int t = 0; t < kB; ++t)
+#pragma unroll
+        for (int i = 0; i < NWL; ++i) {
+          h[i] = cw_op<OP, E>(h[i], cw_of<E>(x[t].v[i]));
+          x[t].v[i] = cw_word<E>(h[i]);
+        }
 #pragma unroll
       for (int t = 0; t < kB; ++t) ST(r - t, x[t]);
     }
     for (; r >= lo; --r) {
-      h = cw_op<OP, E>(h, cw_of<E>(LD(r)));
-      ST(r, cw_word<E>(h));
+      Wv x = LD(r);
+#pragma unroll
+      for (int i = 0; i < NWL; ++i) {
+        h[i] = cw_op<OP, E>(h[i], cw_of<E>(x.v[i]));
+        x.v[i] = cw_word<E>(h[i]);
+      }
+      ST(r, x);
     }
-    if (E0 - w >= 0 && col_in) colv_store<T>(a, y0 + E0 - w, px0, cw_word<E>(h), fast);
+    if (E0 - w >= 0 && col_in) {
+      Wv o;
+#pragma unroll
+      for (int i = 0; i < NWL; ++i) o.v[i] = cw_word<E>(h[i]);
+      store(y0 + E0 - w, o, fast);
+    }
     // g-scan over rows E0 .. E0+w-2; row e closes the window of output
     // e-w+1, so rows before w-1 (a partial first block only) emit nothing
-    C g = IDC;
+    C g[NWL];
+#pragma unroll
+    for (int i = 0; i < NWL; ++i) g[i] = IDC;
     const int e_emit = E0 > w - 1 ? E0 : w - 1;
     const int last = E0 + w - 2;
     int e = E0;
-    for (; e < e_emit; ++e) g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
+    for (; e < e_emit; ++e) {
+      const Wv x = LD(e);
+#pragma unroll
+      for (int i = 0; i < NWL; ++i) g[i] = cw_op<OP, E>(g[i], cw_of<E>(x.v[i]));
+    }
     if (!col_in) continue;
-    if (fast) {
-      uint8_t* out = a.dst + static_cast<long long>(y0 + e - w + 1) * a.dp + static_cast<long long>(px0) * E;
-      for (; e + (kB - 1) <= last; e += kB) {
-        uint32_t xe[kB], xh[kB];
+    for (; e + (kB - 1) <= last; e += kB) {
+      Wv xe[kB], xh[kB];
 #pragma unroll
-        for (int t = 0; t < kB; ++t) {
-          xe[t] = LD(e + t);
-          xh[t] = LD(e + t - w + 1);
-        }
+      for (int t = 0; t < kB; ++t) {
+        xe[t] = LD(e + t);
+        xh[t] = LD(e + t - w + 1);
+      }
 #pragma unroll
-        for (int t = 0; t < kB; ++t) {
-          g = cw_op<OP, E>(g, cw_of<E>(xe[t]));
-          *reinterpret_cast<uint32_t*>(out) = cw_word<E>(cw_op<OP, E>(cw_of<E>(xh[t]), g));
-          out += a.dp;
+      for (int t = 0; t < kB; ++t) {
+        Wv o;
+#pragma unroll
+        for (int i = 0; i < NWL; ++i) {
+          g[i] = cw_op<OP, E>(g[i], cw_of<E>(xe[t].v[i]));
+          o.v[i] = cw_word<E>(cw_op<OP, E>(cw_of<E>(xh[t].v[i]), g[i]));
         }
+        store(y0 + e + t - w + 1, o, fast);
       }
-      for (; e <= last; ++e) {
-        g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
-        *reinterpret_cast<uint32_t*>(out) = cw_word<E>(cw_op<OP, E>(cw_of<E>(LD(e - w + 1)), g));
-        out += a.dp;
+    }
+    for (; e <= last; ++e) {
+      const Wv xe = LD(e), xh = LD(e - w + 1);
+      Wv o;
+#pragma unroll
+      for (int i = 0; i < NWL; ++i) {
+        g[i] = cw_op<OP, E>(g[i], cw_of<E>(xe.v[i]));
+        o.v[i] = cw_word<E>(cw_op<OP, E>(cw_of<E>(xh.v[i]), g[i]));
       }
-    } else {
-      for (; e <= last; ++e) {
-        g = cw_op<OP, E>(g, cw_of<E>(LD(e)));
-        colv_store<T>(a, y0 + e - w + 1, px0, cw_word<E>(cw_op<OP, E>(cw_of<E>(LD(e - w + 1)), g)), false);
-      }
+      store(y0 + e - w + 1, o, fast);
     }
   }
   return true;
@@ -264,19 +333,19 @@ namespace morph {
 // 64, w and 2w.  Warps per CTA: the choice that keeps the most warps
 // resident per SM.
 struct ColvPlan {
-  int L, nbox, wpc, ntask, smem;
+  int L, nbox, wpc, ntask, smem, nwl;
   bool ok;
 };
 
-inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L) {
-  ColvPlan p{0, 0, 0, 0, 0, false};
-  const int ns = (W * esz + kCvBytes - 1) / kCvBytes;
+inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, int nwl) {
+  ColvPlan p{0, 0, 0, 0, 0, nwl, false};
+  const int ns = (W * esz + kCvBytes * nwl - 1) / (kCvBytes * nwl);
   const int nbox = (L + w - 1 + kCvBox - 1) / kCvBox;
   if (nbox > kCvMaxBox) return p;
   int wpc = 0, wps = 0;
   for (int c = 4; c >= 1; c /= 2) {
-    if (colv_smem_bytes(nbox, c) > max_smem) continue;
-    int ctas = 233472 / (colv_smem_bytes(nbox, c) + 1024);
+    if (colv_smem_bytes(nbox, c, nwl) > max_smem) continue;
+    int ctas = 233472 / (colv_smem_bytes(nbox, c, nwl) + 1024);
     if (ctas > 32) ctas = 32;
     if (ctas * c > 64) ctas = 64 / c;
     if (ctas * c > wps) {
@@ -287,7 +356,7 @@ inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L) {
   if (wpc == 0) return p;
   const long long ntask = static_cast<long long>(ns) * ((H + L - 1) / L);
   if (ntask > (1ll << 30)) return p;
-  return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc), true};
+  return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc, nwl), nwl, true};
 }
 
 inline int colv_default_rows(int esz, int w) {
@@ -297,15 +366,16 @@ inline int colv_default_rows(int esz, int w) {
   return w >= 64 ? two : 64;
 }
 
-inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L) {
-  ColvPlan p{0, 0, 0, 0, 0, false};
+// nwl: 32-bit words per lane (1, or 2 for strips 256 bytes wide).
+inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L, int nwl = 1) {
+  ColvPlan p{0, 0, 0, 0, 0, nwl, false};
   if (w < 2 || W < 1 || H < 1) return p;
   const int hmax = H < 1024 ? H : 1024;
   int L = forced_L > 0 ? forced_L : colv_default_rows(esz, w);
   if (L > hmax) L = hmax;
   // very long windows: shorter tiles until one fits
   for (; L >= 1; L -= 8) {
-    p = colv_shape(esz, W, H, w, max_smem, L);
+    p = colv_shape(esz, W, H, w, max_smem, L, nwl);
     if (p.ok) break;
   }
   return p;

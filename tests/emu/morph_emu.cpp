@@ -514,7 +514,8 @@ int main() {
     const bool use_colv = kern == 4 && L.wx == 1 && L.wy > 1;
     if (use_colv) {
       // the warp-tiled pass along y, planned and launched as colv_launch does
-      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200));
+      const int nwl = (seed / 2) % 2 ? 2 : 1;  // words per lane
+      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200), nwl);
       if (!p.ok) {
         printf("FAIL case %d: no colv plan\n", cases);
         ++failures;
@@ -532,19 +533,21 @@ int main() {
       c.a = L.ay;
       c.L = p.L;
       c.nbox = p.nbox;
-      c.ns = cdiv(W * esz, kCvBytes);
+      c.ns = cdiv(W * esz, kCvBytes * nwl);
       c.ntask = p.ntask;
       c.wpc = p.wpc;
       c.ld_vec = a.ld_vec;
-      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
+      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % (4 * nwl) == 0) && (dp % (4 * nwl) == 0);
       c.err = &errword;
-      c.tma_ld = tma_ok(src, sp, kCvBytes / esz, kCvBox);
-      EmuMap mc{src, nullptr, esz, W, H, sp, kCvBytes / esz, kCvBox};
+      c.tma_ld = tma_ok(src, sp, kCvBytes * nwl / esz, kCvBox);
+      EmuMap mc{src, nullptr, esz, W, H, sp, kCvBytes * nwl / esz, kCvBox};
       CUtensorMap tc{};
       memcpy(&tc, &mc, sizeof(mc));
       using VFn = bool (*)(const ColvArgs&, const CUtensorMap*, int, int, uint8_t*, uint64_t*);
-      VFn vf = esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0> : colv_tile<uint8_t, 1>)
-                        : (op == 0 ? colv_tile<uint16_t, 0> : colv_tile<uint16_t, 1>);
+      VFn vf = nwl == 2 ? (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 2> : colv_tile<uint8_t, 1, 2>)
+                                    : (op == 0 ? colv_tile<uint16_t, 0, 2> : colv_tile<uint16_t, 1, 2>))
+                        : (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 1> : colv_tile<uint8_t, 1, 1>)
+                                    : (op == 0 ? colv_tile<uint16_t, 0, 1> : colv_tile<uint16_t, 1, 1>));
       const int nthr = 32 * c.wpc;
       for (int blk = 0; blk < cdiv(c.ntask, c.wpc); ++blk) {
         EmuCta cta;
@@ -559,8 +562,8 @@ int main() {
               emu_threadIdx = make_uint3(tid, 0, 0);
               const int warp = tid >> 5, lane = tid & 31, task = blk * c.wpc + warp;
               if (task >= c.ntask) return;
-              uint8_t* tile = sm + warp * colv_tile_bytes(c.nbox);
-              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.wpc * colv_tile_bytes(c.nbox)) + warp * c.nbox;
+              uint8_t* tile = sm + warp * colv_tile_bytes(c.nbox, nwl);
+              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.wpc * colv_tile_bytes(c.nbox, nwl)) + warp * c.nbox;
               if (c.tma_ld && lane == 0)
                 for (int b = 0; b < c.nbox; ++b) mbar_init(&bars[b], 1);
               // lanes wait on the barriers only after lane 0 initialised them

@@ -36,12 +36,14 @@ def windows_1d(n):
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("mode", [1, 4])
 @pytest.mark.parametrize("rows", [0, 8, 40, 128, 512])
-def test_pass_along_y_warp_tiled(lib, dtype, rows):
+def test_pass_along_y_warp_tiled(lib, dtype, mode, rows):
+    """mode 1: one word per lane (128-byte strips); 4: two (256-byte)."""
     torch = need_cuda()
-    g = synth.rng(300 + rows)
+    g = synth.rng(300 + rows + mode)
     try:
-        assert lib.morph_set_colv(1, rows) == 0
+        assert lib.morph_set_colv(mode, rows) == 0
         for (h, w) in ((1, 64), (37, 300), (300, 37), (1000, 129), (129, 1000), (2049, 64)):
             img = synth.uniform_image(w, h, dtype, gen=g)
             for i, (wy, ay) in enumerate(windows_1d(h)):
