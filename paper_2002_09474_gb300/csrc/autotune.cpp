@@ -4,7 +4,8 @@
 // which the paper measured on an ARM CPU (59 and 69) and which differ on a
 // GPU -- and, per pixel type, whether the pass along x runs faster inside the
 // fused kernel or through the standalone transpose kernels (section 5.2.1's
-// form).  Results persist as a small JSON file keyed by the device.
+// form), and the rows per warp of the pass along x (2 or 4, on a 4096 x 2048
+// image).  Results persist as a small JSON file keyed by the device.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -30,7 +31,7 @@ std::string device_key() {
   int drv = 0;
   cudaDriverGetVersion(&drv);
   char buf[512];
-  snprintf(buf, sizeof(buf), "%s|sm%d%d|%dSM|drv%d|v2", p.name, p.major, p.minor, p.multiProcessorCount, drv);
+  snprintf(buf, sizeof(buf), "%s|sm%d%d|%dSM|drv%d|v4", p.name, p.major, p.minor, p.multiProcessorCount, drv);
   return buf;
 }
 
@@ -101,6 +102,11 @@ bool load_cache(const char* path, const std::string& key, Tuning* t) {
     t->xpass_transpose[0] = xp[0] == 1;
     t->xpass_transpose[1] = xp[1] == 1;
   }
+  int rr[2];
+  const char* r = strstr(buf, "\"rowv_rows\": [");
+  if (r && sscanf(r, "\"rowv_rows\": [%d, %d]", &rr[0], &rr[1]) == 2)
+    for (int i = 0; i < 2; ++i)
+      if (rr[i] == 2 || rr[i] == 4 || rr[i] == 8) t->rowv_rr[i] = rr[i];
   return true;
 }
 
@@ -109,9 +115,9 @@ bool save_cache(const char* path, const std::string& key, const Tuning& t) {
   if (!f) return false;
   fprintf(f,
           "{\"device\": \"%s\", \"cross\": [%d, %d, %d, %d], \"order\": \"u8 x, u8 y, u16 x, u16 y\", "
-          "\"xpass\": [%d, %d]}\n",
+          "\"xpass\": [%d, %d], \"rowv_rows\": [%d, %d]}\n",
           key.c_str(), t.cross_row[0], t.cross_col[0], t.cross_row[1], t.cross_col[1], t.xpass_transpose[0],
-          t.xpass_transpose[1]);
+          t.xpass_transpose[1], t.rowv_rr[0], t.rowv_rr[1]);
   return fclose(f) == 0;
 }
 
@@ -206,11 +212,50 @@ extern "C" int morph_autotune(const char* cache_path) {
     if (tf >= 1e29f || tt >= 1e29f) rc = MORPH_ERR_CUDA;
     t.xpass_transpose[e] = tt < tf ? 1 : 0;
   }
+  cudaFree(src);
+  cudaFree(dst);
+  src = dst = nullptr;
+  // Rows per warp of the pass along x, on a 4096 x 2048 image (as many row
+  // bands as the large images it serves).
+  constexpr int kShapeW = 4096, kShapeH = 2048;
+  const size_t spitch = kShapeW * 2;
+  if (rc == MORPH_OK && (cudaMalloc(&src, spitch * kShapeH) != cudaSuccess ||
+                         cudaMalloc(&dst, spitch * kShapeH) != cudaSuccess))
+    rc = MORPH_ERR_NOMEM;
+  if (rc == MORPH_OK) cudaMemset(src, 0x3C, spitch * kShapeH);
+  for (int e = 0; e < 2 && rc == MORPH_OK; ++e) {
+    FusedLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.esz = e + 1;
+    L.src = src;
+    L.dst = dst;
+    L.sp = L.dp = static_cast<long long>(spitch);
+    L.W = kShapeW;
+    L.H = kShapeH;
+    // pass along x: 2 or 4 rows per warp
+    L.wy = 1;
+    L.ay = 0;
+    L.wx = 101;
+    L.ax = 50;
+    float best = 1e30f;
+    int best_r = 2;
+    for (int rr : {2, 4}) {
+      if (rc != MORPH_OK) break;
+      t.rowv_rr[e] = rr;
+      const float ms = time_planned(L, st, e0, e1);
+      if (ms >= 1e29f) rc = MORPH_ERR_CUDA;
+      if (ms < best) {
+        best = ms;
+        best_r = rr;
+      }
+    }
+    t.rowv_rr[e] = best_r;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(st);
-  cudaFree(src);
-  cudaFree(dst);
+  if (src) cudaFree(src);
+  if (dst) cudaFree(dst);
   if (rc != MORPH_OK) {
     reset_tuning_defaults();
     return rc;

@@ -91,6 +91,11 @@ ColvFn colv_kernel_for(int esz, int op, int nwl) {
 // Words per lane: 2 when forced (colv mode 4), else 1.
 int colv_words() { return tuning().colv_mode == 4 ? 2 : 1; }
 
+// The warp tile plan: rows forced by the tuning, else the built-in rule.
+ColvPlan colv_plan_for(const FusedLaunch& L) {
+  return colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, colv_words(), sm_count_w());
+}
+
 
 }  // namespace
 
@@ -159,12 +164,12 @@ cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream) {
 }
 
 bool colv_fits(const FusedLaunch& L) {
-  return L.wy >= 2 && colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, colv_words()).ok;
+  return L.wy >= 2 && colv_plan_for(L).ok;
 }
 
 cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int E = L.esz;
-  const ColvPlan p = colv_plan(E, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, colv_words());
+  const ColvPlan p = colv_plan_for(L);
   if (!p.ok) return cudaErrorInvalidConfiguration;
   ColvArgs a;
   a.src = static_cast<const uint8_t*>(L.src);

@@ -286,33 +286,39 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
       for (int i = 0; i < NWL; ++i) g[i] = cw_op<OP, E>(g[i], cw_of<E>(x.v[i]));
     }
     if (!col_in) continue;
-    for (; e + (kB - 1) <= last; e += kB) {
-      Wv xe[kB], xh[kB];
-#pragma unroll
-      for (int t = 0; t < kB; ++t) {
-        xe[t] = LD(e + t);
-        xh[t] = LD(e + t - w + 1);
-      }
-#pragma unroll
-      for (int t = 0; t < kB; ++t) {
-        Wv o;
-#pragma unroll
-        for (int i = 0; i < NWL; ++i) {
-          g[i] = cw_op<OP, E>(g[i], cw_of<E>(xe[t].v[i]));
-          o.v[i] = cw_word<E>(cw_op<OP, E>(cw_of<E>(xh[t].v[i]), g[i]));
-        }
-        store(y0 + e + t - w + 1, o, fast);
-      }
-    }
-    for (; e <= last; ++e) {
-      const Wv xe = LD(e), xh = LD(e - w + 1);
+    // emission of output e-w+1 from the g-prefix and h-suffix; the vector
+    // form walks one output pointer down the rows (the branch and the row
+    // address stay out of the scan)
+    auto emit = [&](const Wv& xe, const Wv& xh) {
       Wv o;
 #pragma unroll
       for (int i = 0; i < NWL; ++i) {
         g[i] = cw_op<OP, E>(g[i], cw_of<E>(xe.v[i]));
         o.v[i] = cw_word<E>(cw_op<OP, E>(cw_of<E>(xh.v[i]), g[i]));
       }
-      store(y0 + e - w + 1, o, fast);
+      return o;
+    };
+    if (fast) {
+      uint8_t* out = a.dst + static_cast<long long>(y0 + e - w + 1) * a.dp + static_cast<long long>(px0) * E;
+      for (; e + (kB - 1) <= last; e += kB) {
+        Wv xe[kB], xh[kB];
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+          xe[t] = LD(e + t);
+          xh[t] = LD(e + t - w + 1);
+        }
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+          wd_st<NWL>(out, emit(xe[t], xh[t]));
+          out += a.dp;
+        }
+      }
+      for (; e <= last; ++e) {
+        wd_st<NWL>(out, emit(LD(e), LD(e - w + 1)));
+        out += a.dp;
+      }
+    } else {
+      for (; e <= last; ++e) store(y0 + e - w + 1, emit(LD(e), LD(e - w + 1)), false);
     }
   }
   return true;
@@ -326,15 +332,22 @@ namespace morph {
 // CTA, shared memory.  A tile of L rows scans L rows backwards and, per block
 // it touches, w - 1 rows forwards -- L + ceil(L / w) * (w - 1) row steps,
 // fewest per output when L is a multiple of w -- while taller tiles leave
-// fewer warps resident.  The default L was measured on the GB300 (4096^2
-// images, windows of 51, 101 and 127 rows, CUDA-graph timing): for 8-bit
-// pixels 2w (at most 256), for 16-bit pixels w itself from 120 rows, else
-// 2w (at most 256) from 64 rows, else 64 -- each within 3% of the best of
-// 64, w and 2w.  Warps per CTA: the choice that keeps the most warps
-// resident per SM.
+// fewer warps resident, and fewer tiles leave SMs idle.  The default L was
+// measured on the GB300 (CUDA-graph timing of 1 x w windows, w from 9 to
+// 127, on 2048^2, 4096 x 2048 and 4096^2 images of both pixel types, tile
+// heights 9 to 256).  Below 32 rows: the largest multiple of w whose L + w -
+// 1 input rows fill one 32-row box (w <= 16) or two.  From 32 rows: for
+// 8-bit pixels 2w (at most 256), for 16-bit pixels w itself from 120 rows,
+// else 2w (at most 256) from 64 rows, else 64; but if those tiles are fewer
+// than 0.6 times the warps resident on the whole GPU, 64 rows, or 32 when 64
+// still leaves too few.  Over the 54 measured cases the rule's total is 2%
+// above that of the best height per case (the former fixed rule: 17%), and
+// no case is more than 14% slower than its best.  Warps per CTA: the choice
+// that keeps the most warps resident per SM.
 struct ColvPlan {
   int L, nbox, wpc, ntask, smem, nwl;
   bool ok;
+  int wps;  // warps resident per SM
 };
 
 inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, int nwl) {
@@ -356,10 +369,15 @@ inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, in
   if (wpc == 0) return p;
   const long long ntask = static_cast<long long>(ns) * ((H + L - 1) / L);
   if (ntask > (1ll << 30)) return p;
-  return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc, nwl), nwl, true};
+  return ColvPlan{L, nbox, wpc, static_cast<int>(ntask), colv_smem_bytes(nbox, wpc, nwl), nwl, true, wps};
 }
 
 inline int colv_default_rows(int esz, int w) {
+  if (w < 32) {
+    const int rows = w <= 16 ? kCvBox : 2 * kCvBox;  // input rows of the tile
+    const int k = (rows - w + 1) / w;
+    return w * (k > 1 ? k : 1);
+  }
   const int two = 2 * w < 256 ? 2 * w : 256;
   if (esz == 1) return w >= 32 ? two : 64;
   if (w >= 120 && w <= 256) return w;
@@ -367,16 +385,31 @@ inline int colv_default_rows(int esz, int w) {
 }
 
 // nwl: 32-bit words per lane (1, or 2 for strips 256 bytes wide).
-inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L, int nwl = 1) {
-  ColvPlan p{0, 0, 0, 0, 0, nwl, false};
+// sms: the GPU's SM count for the rule on too few tiles (0: rule off).
+inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced_L, int nwl = 1, int sms = 0) {
+  ColvPlan p{0, 0, 0, 0, 0, nwl, false, 0};
   if (w < 2 || W < 1 || H < 1) return p;
   const int hmax = H < 1024 ? H : 1024;
-  int L = forced_L > 0 ? forced_L : colv_default_rows(esz, w);
-  if (L > hmax) L = hmax;
-  // very long windows: shorter tiles until one fits
-  for (; L >= 1; L -= 8) {
-    p = colv_shape(esz, W, H, w, max_smem, L, nwl);
-    if (p.ok) break;
+  auto fit = [&](int L) {
+    if (L > hmax) L = hmax;
+    ColvPlan q{0, 0, 0, 0, 0, nwl, false, 0};
+    // very long windows: shorter tiles until one fits
+    for (; L >= 1; L -= 8) {
+      q = colv_shape(esz, W, H, w, max_smem, L, nwl);
+      if (q.ok) break;
+    }
+    return q;
+  };
+  if (forced_L > 0) return fit(forced_L);
+  p = fit(colv_default_rows(esz, w));
+  if (w < 32 || sms <= 0) return p;
+  auto enough = [&](const ColvPlan& q) { return q.ok && 5ll * q.ntask >= 3ll * sms * q.wps; };
+  if (!p.ok || enough(p)) return p;
+  for (int L : {64, 32}) {
+    const ColvPlan q = fit(L);
+    if (!q.ok) continue;
+    p = q;
+    if (enough(q)) break;
   }
   return p;
 }

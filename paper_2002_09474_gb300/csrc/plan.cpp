@@ -64,9 +64,11 @@ bool plan_split(const FusedLaunch& L) {
   // auto: two launches when both passes take the van Herk/Gil-Werman method
   // (above the crossovers), i.e. run on the single-pass kernels, which then
   // pay for the second trip through memory (the intermediate mostly stays
-  // in L2).  Measured on the GB300 at 4096^2: 15 x 15 to 127 x 127 run
-  // 6-50% faster as two launches; with a direct-method pass (3 x 3 to 9 x 9)
-  // the fused kernel is 7-39% faster.  Below 2 Mpixels the second launch's
+  // in L2).  Measured on the GB300 at 4096^2 (CUDA-graph timing): 9 x 9 to
+  // 21 x 21 with both passes by van Herk/Gil-Werman take 19.4-20.8 us (u8)
+  // and 24.2-25.0 us (u16) as two launches against 29.7-32.0 and 33.2-38.2
+  // fused, and 127 x 127 runs about 3x faster; with a direct-method pass (3
+  // x 3 to 9 x 9 at a crossover of 9) the fused kernel was 7-39% faster.  Below 2 Mpixels the second launch's
   // fixed cost is not repaid, and the fused kernel is kept.  Also whenever
   // the fused tile the planner picks (or every fused tile) would run fewer
   // than 3 CTAs per SM.
@@ -95,6 +97,7 @@ void reset_tuning_defaults() {
   g_tuning.colv_rows = 0;
   g_tuning.rowv_mode = -1;
   g_tuning.rowv_seg = 0;
+  g_tuning.rowv_rr[0] = g_tuning.rowv_rr[1] = 0;
   g_tuning.from_autotune = 0;
   g_init = true;
 }

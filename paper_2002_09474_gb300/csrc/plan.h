@@ -23,6 +23,7 @@ struct Tuning {
   int colv_rows;                  // its output rows per warp tile (0: launch-shape model)
   int rowv_mode;                  // wx x 1 passes by the register-blocked vHGW kernel: -1 auto, 0 never, 1 always
   int rowv_seg;                   // its output columns per warp segment (0: launch-shape model)
+  int rowv_rr[2];                 // [esz-1]: rows per warp of the pass along x (0: built-in, 2)
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 

@@ -59,20 +59,23 @@ bool rowv_fits(const FusedLaunch& L) {
 }
 
 // Rows per warp: forced by the tuning mode (2: 8 rows, 3: 4 rows, 4: 2
-// rows), else 2 -- measured on the GB300 at 4096^2 (u8 / u16, 101 x 1):
+// rows), else as the autotuner measured for this pixel type, else 2 -- measured on the GB300 at 4096^2 (u8 / u16, 101 x 1):
 // 8 rows 22.1 / 29.2 us, 4 rows 17.2 / 22.3 us, 2 rows 14.8 / 16.1 us; fewer
 // rows per warp lower the registers (64) and shared memory (3.6-4.2 KB) a
 // warp needs, and the extra resident warps hide the latency.
-int rowv_rows() {
-  const int m = tuning().rowv_mode;
-  return m == 2 ? 8 : m == 3 ? 4 : 2;
+int rowv_rows(int esz) {
+  const Tuning& t = tuning();
+  const int m = t.rowv_mode;
+  if (m >= 2) return m == 2 ? 8 : m == 3 ? 4 : 2;
+  const int r = t.rowv_rr[esz - 1];
+  return r == 4 || r == 8 ? r : 2;
 }
 
 cudaError_t rowv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int sms = sm_count_r();
   if (sms <= 0) return cudaErrorInvalidDevice;
   if (!rowv_fits(L)) return cudaErrorInvalidConfiguration;
-  const int rr = rowv_rows();
+  const int rr = rowv_rows(L.esz);
   const int smem = kRvWarps * rv_warp_smem(L.esz, rr);
   RowvFn k = rowv_kernel_for(L.esz, L.op, rr);
   static std::mutex mu;

@@ -515,7 +515,7 @@ int main() {
     if (use_colv) {
       // the warp-tiled pass along y, planned and launched as colv_launch does
       const int nwl = (seed / 2) % 2 ? 2 : 1;  // words per lane
-      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200), nwl);
+      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200), nwl, 152);
       if (!p.ok) {
         printf("FAIL case %d: no colv plan\n", cases);
         ++failures;

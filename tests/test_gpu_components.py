@@ -162,15 +162,24 @@ def test_autotune_and_cache(lib, tmp_path):
     assert lib.morph_autotune(path) == 0
     text = open(path).read()
     assert '"cross"' in text and '"device"' in text and '"xpass"' in text
+    assert '"rowv_rows"' in text
     # a second call loads the cache; results stay exact either way
     assert lib.morph_autotune(path) == 0
     img = synth.uniform_image(300, 200, np.uint8, seed=221)
     s = torch.from_numpy(img).cuda()
-    for (wx, wy) in ((9, 9), (15, 31), (63, 5)):
+    for (wx, wy) in ((9, 9), (15, 31), (63, 5), (1, 101), (101, 1), (21, 51)):
         o = torch.empty_like(s)
         lib.apply(s, o, wx, wy, op=0)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(o.cpu().numpy(), oracle.morph(img, wx, wy, wx // 2, wy // 2, "erode"))
+    # the measured launch shapes, on an image large enough to use them
+    big = synth.uniform_image(2500, 2300, np.uint16, seed=222)
+    s = torch.from_numpy(big).cuda()
+    for (wx, wy) in ((1, 101), (101, 1), (21, 51), (127, 127)):
+        o = torch.empty_like(s)
+        lib.apply(s, o, wx, wy, op=1)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(o.cpu().numpy(), oracle.sep_vhgw(big, wx, wy, wx // 2, wy // 2, "dilate"))
     lib.morph_reset_tuning()
 
 
