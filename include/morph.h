@@ -298,7 +298,11 @@ int morph_set_column_kernel(int mode);
  * warps of a CTA share one input tile and keep the block suffix of their 32
  * or 64 output rows in registers (measured slower on the GB300, so not a
  * default); 4: as 1, with strips 256 bytes wide, each lane owning two
- * words (two independent scan chains per lane).  rows: output rows per
+ * words (two independent scan chains per lane); 5: as 1, but for 9 <= wy
+ * <= 256 and TMA-loadable rows the strip-streaming form: 8-row blocks, the
+ * whole blocks inside a window folded from their totals, the rows wy - 1
+ * behind read a second time, so shared memory does not grow with wy (rows
+ * is then the band height per warp, rounded up to a multiple of 8).  rows: output rows per
  * warp tile, 1 to 1024, or 0 for the measured default (a multiple of wy
  * filling one or two 32-row input boxes below 32 rows; else wy or 2 wy up
  * to 256, or 64, with 64 or 32 where those tiles would leave the GPU's

@@ -97,6 +97,9 @@ int launch_one(FusedLaunch L, cudaStream_t stream) {
     // mode 2: the shared-tile form where it applies
     if (tuning().colv_mode == 2 && colw_fits(L))
       return colw_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+    // mode 5: the strip-streaming form where it applies
+    if (tuning().colv_mode == 5 && cols_fits(L))
+      return cols_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
     return colv_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   }
   if (L.wx == 1 && L.wy > 1 && tuning().col_mode != 0)
@@ -596,7 +599,7 @@ int morph_set_row_kernel(int mode) {
 }
 
 int morph_set_colv(int mode, int rows) {
-  if (mode < -1 || mode > 4 || mode == 3 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
+  if (mode < -1 || mode > 5 || mode == 3 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
   tuning().colv_mode = mode;
   tuning().colv_rows = rows;
   return MORPH_OK;

@@ -114,6 +114,10 @@ cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream);
 // and keep the block suffix in registers; colw_fits).
 bool colw_fits(const FusedLaunch& L);
 cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream);
+// Its strip-streaming form (8-row blocks, the rows w - 1 behind read a
+// second time; 9 <= wy <= 256 and TMA-loadable rows; cols_fits).
+bool cols_fits(const FusedLaunch& L);
+cudaError_t cols_launch(const FusedLaunch& L, cudaStream_t stream);
 
 // The register-blocked van Herk/Gil-Werman kernel of the pass along x
 // (9 <= wx <= 256, rows aligned to 8 * esz bytes; rowv_fits).

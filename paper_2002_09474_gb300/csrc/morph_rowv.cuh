@@ -317,7 +317,7 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
     }
     rv_transpose_in<T, RR>(R, Vb);
   };
-  auto prefixes = [&](const V (&Vb)[8], int k) {
+  auto prefixes = [&](const V (&Vb)[8], int k) {  // returns the block total
     const int b = k & (kRvRing - 1);
     V P = Vb[0];
     pb[b] = P;
@@ -326,7 +326,22 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
       P = rv_op<OP, RR>(P, Vb[n]);
       pb[n * kRvRing + b] = P;
     }
+    return P;
   };
+  auto shfl = [&](const V& v, int src) {
+    V o;
+#pragma unroll
+    for (int t = 0; t < RR / 2; ++t) o.w[t] = __shfl_sync(0xffffffffu, v.w[t], src);
+    return o;
+  };
+  auto pick = [&](bool c, const V& x, const V& y) {
+    V o;
+#pragma unroll
+    for (int t = 0; t < RR / 2; ++t) o.w[t] = c ? x.w[t] : y.w[t];
+    return o;
+  };
+  const V ID = rv_ident<OP, RR>();
+  V Tprev = ID;  // block totals of the previous chunk (lane l: block 32(j-1) + l)
 
   // One step: chunk j's block data into Vnew (and its prefixes into the
   // ring), then the outputs of chunk j-1 from Vold.  Steps alternate the two
@@ -336,16 +351,40 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
     cp_async_wait<D>();
     __syncwarp();
     build(j, Vnew);
-    prefixes(Vnew, kRvChunk / 8 * j + lane);
+    const V Tnew = prefixes(Vnew, kRvChunk / 8 * j + lane);
     __syncwarp();
     if (j >= 1) {
       // outputs of chunk j-1: block k
       const int k = 32 * (j - 1) + lane;
-      // fold of the whole blocks k+1 .. k+q-1 (a sparse table of pairwise
-      // folds was measured slower at q of 12-15: its warp synchronisations
-      // cost more than the loads they save)
-      V m = rv_ident<OP, RR>();
-      for (int t = 1; t < q; ++t) m = rv_op<OP, RR>(m, rv_lds(&pb[7 * kRvRing + ((k + t) & (kRvRing - 1))]));
+      // fold of the whole blocks k+1 .. k+q-1.  For q >= 5 by doubling over
+      // the 64 totals of chunks j-1 (lo) and j (hi) held in the lanes:
+      // after the levels, element i holds the fold of totals i .. i+p-1 (p
+      // the largest power of two <= q-1), and the fold of k+1 .. k+q-1 is
+      // that of elements k+1 and k+q-p (q-1 <= 2p, so the two overlap or
+      // meet; the last total used is element 62 at most).  Shorter folds
+      // read the ring (a sparse table of pairwise folds in shared memory
+      // was measured slower: its warp synchronisations cost more than the
+      // loads they save).
+      V m = ID;
+      if (q >= 5) {
+        V lo = Tprev, hi = Tnew;
+        int p = 1;
+        for (; 2 * p <= q - 1; p *= 2) {
+          const int src = (lane + p) & 31;
+          const bool in = lane + p < 32;
+          const V al = shfl(lo, src), ah = shfl(hi, src);
+          lo = rv_op<OP, RR>(lo, pick(in, al, ah));
+          hi = rv_op<OP, RR>(hi, pick(in, ah, ID));
+        }
+        auto gather = [&](int off) {
+          const int src = (lane + off) & 31;
+          const V al = shfl(lo, src), ah = shfl(hi, src);
+          return pick(lane + off < 32, al, ah);
+        };
+        m = rv_op<OP, RR>(gather(1), gather(q - p));
+      } else {
+        for (int t = 1; t < q; ++t) m = rv_op<OP, RR>(m, rv_lds(&pb[7 * kRvRing + ((k + t) & (kRvRing - 1))]));
+      }
       V S[8];  // suffixes of block k, seeded with m
       S[7] = rv_op<OP, RR>(Vold[7], m);
 #pragma unroll
@@ -361,6 +400,7 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
       const int x = xs + 8 * k;
       if (x < xe) rv_store_block<T, RR>(a, y0, x, xe, S);
     }
+    Tprev = Tnew;
     __syncwarp();
   };
   V VA[8], VB[8];

@@ -6,7 +6,9 @@ pitch and offset) also appears in the persistent two-slot form (kern 1), and
 every 1 x wy case (wy > 1) also through the column kernel (kern 2), every
 wx x 1 case (wx > 1) also through the row kernel (kern 3), and every 1 x wy
 case also through the warp-tiled van Herk/Gil-Werman kernel of the pass
-along y (kern 4).  --only K keeps the cases of kernel K."""
+along y (kern 4); kern 5 is the register-blocked pass along x, kern 6 the
+shared-tile pass along y, kern 7 the strip-streaming pass along y.  --only
+K keeps the cases of kernel K."""
 import itertools
 import sys
 
@@ -150,6 +152,21 @@ def cases(full=True):
                         seed += 1
     for c in colw:
         both.append(c + (6,))
+    # the strip-streaming pass along y (9 <= wy <= 256, TMA-loadable rows):
+    # the warp-tiled kernel's cases, plus tall, short and ragged images,
+    # windows around the block and box sizes, every anchor extreme
+    cols = [c for c in colv if 9 <= c[9] <= 256]
+    for esz in (1, 2):
+        for (w, h) in ((128, 1000), (300, 2100), (64, 700), (257, 333), (190, 41), (1000, 64), (130, 16), (640, 17)):
+            for wy in (9, 10, 15, 16, 17, 24, 33, 64, 65, 101, 127, 256):
+                for ay in sorted({0, wy // 2, wy - 1}):
+                    for op in (0, 1):
+                        pad = aligned_pad(w, esz)
+                        dpad, doff = (pad, 0) if (wy + ay + op) % 2 else (esz, 3 * esz)
+                        cols.append((esz, op, w, h, pad, 0, dpad, doff, 1, wy, 0, ay, -1, -1, -1, seed))
+                        seed += 1
+    for c in cols:
+        both.append(c + (7,))
     return both
 
 

@@ -56,6 +56,8 @@ struct EmuCta {
   std::barrier<>* bar = nullptr;
   std::barrier<>* wbar[8] = {};  // one per warp (__syncwarp)
   std::atomic<int> orflag{0};
+  std::atomic<int> anyfalse[8] = {};  // per warp (__all_sync)
+  uint32_t shfl[8][32] = {};           // per warp (__shfl_sync)
   // mbarriers by address: a phase completes when its arrivals are in and
   // its transaction count is back to zero; the phase bit then flips.
   struct Mbar {
@@ -79,6 +81,26 @@ static void emu_error(const char* what) {
 
 static inline void __syncthreads() { g_cta->bar->arrive_and_wait(); }
 static inline void __syncwarp() { g_cta->wbar[threadIdx.x >> 5]->arrive_and_wait(); }
+// every lane of the warp takes part (full mask): lane src's v
+static inline unsigned int __shfl_sync(unsigned, unsigned int v, int src) {
+  uint32_t* x = g_cta->shfl[threadIdx.x >> 5];
+  x[threadIdx.x & 31] = v;
+  __syncwarp();
+  const unsigned int r = x[src & 31];
+  __syncwarp();
+  return r;
+}
+// every lane of the warp takes part (full mask): true when no lane's p is false
+static inline bool __all_sync(unsigned, bool p) {
+  std::atomic<int>& f = g_cta->anyfalse[threadIdx.x >> 5];
+  if (!p) f.store(1);
+  __syncwarp();
+  const bool r = f.load() == 0;
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) f.store(0);
+  __syncwarp();
+  return r;
+}
 static inline int __syncthreads_or(int p) {
   if (p) g_cta->orflag.store(1);
   g_cta->bar->arrive_and_wait();
@@ -122,6 +144,7 @@ static inline unsigned int __funnelshift_r(unsigned int lo, unsigned int hi, uns
 #include "morph_row.cuh"
 #include "morph_colv.cuh"
 #include "morph_rowv.cuh"
+#include "morph_cols.cuh"
 
 // ---- TMA / mbarrier model ------------------------------------------------------
 struct EmuMap {
@@ -703,6 +726,75 @@ int main() {
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
     }
+    const bool use_cols = kern == 7 && L.wx == 1 && L.wy >= 9 && L.wy <= kCsMaxW &&
+                          tma_ok(src, sp, 128 / esz, kCsBox);
+    if (use_cols) {
+      // the strip-streaming pass along y, planned as cols_launch does (forced
+      // band heights on even seeds; few SMs on odd seeds of 3)
+      const int sms = seed % 3 == 0 ? 3 : 152;
+      const ColsPlan p = cols_plan(esz, W, H, L.wy, kMaxSmemBytes, sms, (seed / 2) % 2 ? 28 : 64,
+                                   (seed & 1) ? 0 : 1 + static_cast<int>(seed % 300));
+      if (!p.ok) {
+        printf("FAIL case %d: no cols plan\n", cases);
+        ++failures;
+        continue;
+      }
+      col_ty = p.Lo;
+      ColsArgs c{};
+      c.dst = dst;
+      c.dp = dp;
+      c.W = W;
+      c.H = H;
+      c.w = L.wy;
+      c.a = L.ay;
+      c.Lo = p.Lo;
+      c.ns = cdiv(W * esz, 128);
+      c.ntask = p.ntask;
+      c.wpc = p.wpc;
+      c.rs = p.rs;
+      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
+      c.err = &errword;
+      a.tma_ld = 1;
+      EmuMap mc{src, nullptr, esz, W, H, sp, 128 / esz, kCsBox};
+      CUtensorMap tc{};
+      memcpy(&tc, &mc, sizeof(mc));
+      using SFn = bool (*)(const ColsArgs&, const CUtensorMap*, int, int, uint8_t*);
+      SFn sf = esz == 1 ? (op == 0 ? cols_task<uint8_t, 0> : cols_task<uint8_t, 1>)
+                        : (op == 0 ? cols_task<uint16_t, 0> : cols_task<uint16_t, 1>);
+      const int nthr = 32 * c.wpc;
+      const int wsz = cols_warp_smem(c.rs);
+      for (int blk = 0; blk < cdiv(c.ntask, c.wpc); ++blk) {
+        EmuCta cta;
+        std::barrier<> bar(nthr);
+        cta.bar = &bar;
+        std::barrier<>* wb[8] = {};
+        for (int wi = 0; wi < c.wpc; ++wi) wb[wi] = new std::barrier<>(32);
+        for (int wi = 0; wi < c.wpc; ++wi) cta.wbar[wi] = wb[wi];
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (p.smem + 127) / 128 * 128));
+        cta.smem = sm;
+        cta.smem_size = p.smem;
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              const int warp = tid >> 5, lane = tid & 31, task = blk * c.wpc + warp;
+              // a warp whose task is past the end returns at once in the
+              // kernel; here its lanes still meet the warp barrier count
+              if (task >= c.ntask) return;
+              uint8_t* ws = sm + warp * wsz;
+              uint64_t* bars = cols_bars(ws, c.rs);
+              if (lane == 0)
+                for (int b = 0; b < 2 * kCsSlots; ++b) mbar_init(&bars[b], 1);
+              __syncwarp();
+              sf(c, &tc, task, lane, ws);
+            },
+            nthr);
+        for (int wi = 0; wi < c.wpc; ++wi) delete wb[wi];
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+    }
     if (use_row) {
       // the row kernel, launched as row_launch does
       const bool blk = L.vhgw_row && L.wx >= 9;
@@ -751,7 +843,7 @@ int main() {
       }
       a.tma_ld = ra.tma_ld;
     }
-    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv || use_colw ? 0 : ncta); ++c) {
+    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv || use_colw || use_cols ? 0 : ncta); ++c) {
       const int bx = c % gx, by = c / gx;
       EmuCta cta;
       std::barrier<> bar(kThreads);
@@ -799,7 +891,7 @@ int main() {
     printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
            "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_colw ? 6 : use_rowv ? 5 : use_colv ? 4 : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_cols ? 7 : use_colw ? 6 : use_rowv ? 5 : use_colv ? 4 : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);

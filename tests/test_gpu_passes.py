@@ -60,6 +60,32 @@ def test_pass_along_y_warp_tiled(lib, dtype, mode, rows):
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("rows", [0, 8, 64, 300])
+def test_pass_along_y_strip_streaming(lib, dtype, rows):
+    """The strip-streaming form (8-row blocks, the rows w - 1 behind read a
+    second time) for 9 <= wy <= 256 and TMA-loadable rows; band heights
+    forced or planned; windows outside that range fall back to the warp
+    tiles."""
+    torch = need_cuda()
+    g = synth.rng(340 + rows)
+    esz = np.dtype(dtype).itemsize
+    try:
+        assert lib.morph_set_colv(5, rows) == 0
+        for (h, w) in ((16, 128), (17, 640), (40, 300), (300, 129), (1000, 257), (2049, 64)):
+            img = synth.uniform_image(w, h, dtype, gen=g)
+            for i, (wy, ay) in enumerate(((9, 4), (10, 0), (16, 15), (17, 8), (33, 0), (64, 63), (65, 32),
+                                          (101, 50), (127, 0), (256, 255), (5, 2), (300, 150))):
+                op = ("erode", "dilate")[(i + h) % 2]
+                want = oracle.morph(img, 1, wy, 0, ay, op)
+                pad = aligned_pad(w, dtype)
+                dpad, doff = (pad, 0) if i % 2 else (esz, 3 * esz)
+                got = run(lib, torch, img, 1, wy, 0, ay, op, pad=pad, dst_pad=dpad, dst_offset=doff)
+                assert np.array_equal(got, want), (h, w, wy, ay, op, rows)
+    finally:
+        lib.morph_set_colv(-1, 0)
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 def test_pass_along_y_shared_tile(lib, dtype):
     """The shared-tile form (warps share one input tile, block suffix in
     registers) for windows longer than 32 rows, TMA-loadable rows."""
