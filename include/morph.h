@@ -302,7 +302,11 @@ int morph_set_column_kernel(int mode);
  * <= 256 and TMA-loadable rows the strip-streaming form: 8-row blocks, the
  * whole blocks inside a window folded from their totals, the rows wy - 1
  * behind read a second time, so shared memory does not grow with wy (rows
- * is then the band height per warp, rounded up to a multiple of 8).  rows: output rows per
+ * is then the band height per warp, rounded up to a multiple of 8); 6: as
+ * 1, but where rows are TMA-loadable the ring form: the tile's rows cycle
+ * through ceil((wy + 39) / 32) + 1 boxes, each refilled once the scan has
+ * passed it (rows: the tile height; 0: a multiple of wy).  Modes 2, 4, 5
+ * and 6 were measured slower than 1 on the GB300 at the bench's windows.  rows: output rows per
  * warp tile, 1 to 1024, or 0 for the measured default (a multiple of wy
  * filling one or two 32-row input boxes below 32 rows; else wy or 2 wy up
  * to 256, or 64, with 64 or 32 where those tiles would leave the GPU's

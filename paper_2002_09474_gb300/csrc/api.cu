@@ -599,7 +599,7 @@ int morph_set_row_kernel(int mode) {
 }
 
 int morph_set_colv(int mode, int rows) {
-  if (mode < -1 || mode > 5 || mode == 3 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
+  if (mode < -1 || mode > 6 || mode == 3 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
   tuning().colv_mode = mode;
   tuning().colv_rows = rows;
   return MORPH_OK;

@@ -11,7 +11,7 @@
 
 namespace morph {
 
-template <typename T, int OP, int NWL>
+template <typename T, int OP, int NWL, bool RG>
 __global__ void __launch_bounds__(128) colv_kernel(const __grid_constant__ CUtensorMap tin, const ColvArgs a) {
   extern __shared__ __align__(128) uint8_t vsmem[];
   pdl_launch_dependents();
@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(128) colv_kernel(const __grid_constant__ CUten
     __syncwarp();
   }
   pdl_wait();
-  colv_tile<T, OP, NWL>(a, &tin, task, lane, tile, bars);
+  colv_tile<T, OP, NWL, RG>(a, &tin, task, lane, tile, bars);
 }
 
 // The shared-tile form (w > LW): thread 0 issues the CTA tile's boxes, every
@@ -79,20 +79,32 @@ int sm_count_w() {
   return n;
 }
 
-ColvFn colv_kernel_for(int esz, int op, int nwl) {
-  if (nwl == 2) {
-    if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0, 2> : colv_kernel<uint8_t, 1, 2>;
-    return op == 0 ? colv_kernel<uint16_t, 0, 2> : colv_kernel<uint16_t, 1, 2>;
+ColvFn colv_kernel_for(int esz, int op, int nwl, bool ring) {
+  if (ring) {
+    if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0, 1, true> : colv_kernel<uint8_t, 1, 1, true>;
+    return op == 0 ? colv_kernel<uint16_t, 0, 1, true> : colv_kernel<uint16_t, 1, 1, true>;
   }
-  if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0, 1> : colv_kernel<uint8_t, 1, 1>;
-  return op == 0 ? colv_kernel<uint16_t, 0, 1> : colv_kernel<uint16_t, 1, 1>;
+  if (nwl == 2) {
+    if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0, 2, false> : colv_kernel<uint8_t, 1, 2, false>;
+    return op == 0 ? colv_kernel<uint16_t, 0, 2, false> : colv_kernel<uint16_t, 1, 2, false>;
+  }
+  if (esz == 1) return op == 0 ? colv_kernel<uint8_t, 0, 1, false> : colv_kernel<uint8_t, 1, 1, false>;
+  return op == 0 ? colv_kernel<uint16_t, 0, 1, false> : colv_kernel<uint16_t, 1, 1, false>;
 }
 
 // Words per lane: 2 when forced (colv mode 4), else 1.
 int colv_words() { return tuning().colv_mode == 4 ? 2 : 1; }
 
+// The ring form (colv mode 6): rows a TMA box can load.
+bool colv_ring_on(const FusedLaunch& L) {
+  if (tuning().colv_mode != 6) return false;
+  CUtensorMap probe;
+  return encode_tensor_map_2d(&probe, L.src, L.esz, L.W, L.H, L.sp, kCvBytes / L.esz, kCvBox);
+}
+
 // The warp tile plan: rows forced by the tuning, else the built-in rule.
-ColvPlan colv_plan_for(const FusedLaunch& L) {
+ColvPlan colv_plan_for(const FusedLaunch& L, bool ring) {
+  if (ring) return colv_ring_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, sm_count_w());
   return colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, colv_words(), sm_count_w());
 }
 
@@ -164,12 +176,13 @@ cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream) {
 }
 
 bool colv_fits(const FusedLaunch& L) {
-  return L.wy >= 2 && colv_plan_for(L).ok;
+  return L.wy >= 2 && colv_plan_for(L, colv_ring_on(L)).ok;
 }
 
 cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
   const int E = L.esz;
-  const ColvPlan p = colv_plan_for(L);
+  const bool ring = colv_ring_on(L);
+  const ColvPlan p = colv_plan_for(L, ring);
   if (!p.ok) return cudaErrorInvalidConfiguration;
   ColvArgs a;
   a.src = static_cast<const uint8_t*>(L.src);
@@ -189,17 +202,22 @@ cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream) {
   a.st_vec = (reinterpret_cast<uintptr_t>(L.dst) % (4 * p.nwl) == 0) && (L.dp % (4 * p.nwl) == 0);
   a.err = device_error_word();
   if (!a.err) return cudaErrorInvalidDevice;
+  // ring form: the tile's rows cycle through the plan's boxes (when the
+  // whole tile fits in fewer, nothing wraps)
+  a.nring = ring ? p.nbox : 0;
+  a.ring_mul = ring ? ((1 << 20) + p.nbox - 1) / p.nbox : 0;
   CUtensorMap tin;
   memset(&tin, 0, sizeof(tin));
   a.tma_ld = encode_tensor_map_2d(&tin, L.src, E, L.W, L.H, L.sp, kCvBytes * p.nwl / E, kCvBox) ? 1 : 0;
-  ColvFn k = colv_kernel_for(E, L.op, p.nwl);
+  if (ring && !a.tma_ld) return cudaErrorInvalidConfiguration;
+  ColvFn k = colv_kernel_for(E, L.op, p.nwl, ring);
   static std::mutex mu;
-  static const void* opted[64][8] = {};
+  static const void* opted[64][16] = {};
   {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
-    const int slot = (E - 1) * 4 + L.op * 2 + (p.nwl == 2 ? 1 : 0);
+    const int slot = (E - 1) * 8 + L.op * 4 + (p.nwl == 2 ? 2 : 0) + (ring ? 1 : 0);
     if (opted[dev & 63][slot] != reinterpret_cast<const void*>(k)) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes);
       if (e != cudaSuccess) return e;

@@ -51,6 +51,8 @@ struct ColvArgs {
   int ld_vec;        // 1: rows allow aligned 32-bit loads
   int st_vec;        // 1: rows allow aligned stores of a lane's words (4 * words per lane bytes)
   int* err;          // device error word
+  int nring;         // ring form: boxes of the ring (the tile's rows cycle through them)
+  int ring_mul;      // ceil(2^20 / nring): floor(b / nring) = (b * ring_mul) >> 20 for b < 2^10
 };
 
 // Shared memory of one CTA: wpc warp tiles (boxes of 32 rows of 128 * nwl
@@ -133,9 +135,21 @@ __device__ __forceinline__ void wd_st(uint8_t* p, const Wd<NWL>& w) {
 // of the strip.  Two words per lane give each lane two independent scan
 // chains.  Returns false when a bounded wait gave up (error word set by lane
 // 0).
-template <typename T, int OP, int NWL = 1>
+//
+// Ring form (RG, TMA-loaded rows, one word per lane): the tile's rows cycle
+// through a.nring boxes.  Row r is last read at g-scan step r + w - 1 (as
+// the suffix h), so once the g-scan has passed 32 (b - nring) + 30 + w, box
+// b can be loaded into the slot of box b - nring.  Every wait then finds its
+// box issued when nring >= ceil((w + 39) / 32) (the h-scan of a block waits
+// for rows below E0 with the g-scan done to E0 - 2; a g-scan batch at e
+// waits for rows to e + 7 with the g-scan done to e - 2 at worst); one box
+// more lets a load run ahead.  The shared memory then no longer grows with
+// the tile height L.
+template <typename T, int OP, int NWL = 1, bool RG = false>
 __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* tin, int task, int lane,
                                           uint8_t* tile, uint64_t* bars) {
+  static_assert(!RG || NWL == 1, "the ring form has one word per lane");
+  static_assert(kCvBox == 32, "rows per box");
   constexpr int E = sizeof(T), PPW = 4 / E;
   constexpr int SB = kCvBytes * NWL, BOXB = SB * kCvBox;  // strip bytes, box bytes
   using C = Cw<E>;
@@ -153,20 +167,26 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
   const bool fast = a.st_vec && px0 + PPW * NWL <= a.W;
   uint8_t* col = tile + 4 * NWL * lane;
 
-  auto LD = [&](int r) { return wd_ld<NWL>(col + r * SB); };
-  auto ST = [&](int r, const Wv& v) { wd_st<NWL>(col + r * SB, v); };
+  const int NR = RG ? a.nring : 0;
+  auto slot_of = [&](int b) { return RG ? b - ((b * a.ring_mul) >> 20) * NR : b; };
+  auto rowp = [&](int r) { return RG ? col + slot_of(r >> 5) * BOXB + (r & 31) * SB : col + r * SB; };
+  auto LD = [&](int r) { return wd_ld<NWL>(rowp(r)); };
+  auto ST = [&](int r, const Wv& v) { wd_st<NWL>(rowp(r), v); };
   Wv IDV;
 #pragma unroll
   for (int i = 0; i < NWL; ++i) IDV.v[i] = IDW;
 
   int have = 0;  // boxes landed (and fixed up)
+  int nxt = RG && NR < nb ? NR : nb;  // boxes issued
+  auto issue = [&](int b) {  // lane 0
+    const int sl = slot_of(b);
+    mbar_arrive_expect_tx(&bars[sl], static_cast<uint32_t>(BOXB));
+    tma_load_2d(tile + sl * BOXB, tin, &bars[sl], s * (SB / E), ys + b * kCvBox);
+  };
   if (a.tma_ld) {
     if (lane == 0) {
       fence_proxy_async_smem();
-      for (int b = 0; b < nb; ++b) {
-        mbar_arrive_expect_tx(&bars[b], static_cast<uint32_t>(BOXB));
-        tma_load_2d(tile + b * BOXB, tin, &bars[b], s * (SB / E), ys + b * kCvBox);
-      }
+      for (int b = 0; b < nxt; ++b) issue(b);
     }
   } else {
     for (int r = 0; r < nin; ++r) {
@@ -199,10 +219,14 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
   auto ensure = [&](int rows) -> bool {
     const int need = (rows + kCvBox - 1) / kCvBox;
     for (; have < need; ++have) {
-      if (!mbar_wait_bounded(&bars[have], 0)) {
+      const uint32_t par = RG ? static_cast<uint32_t>(((have * a.ring_mul) >> 20) & 1) : 0u;
+      bool got = mbar_wait_bounded(&bars[slot_of(have)], par);
+      if (RG) got = __all_sync(0xffffffffu, got);
+      if (!got) {
         if (lane == 0) {
           atomicExch(a.err, kDevErrTmaTimeout);
-          for (int b = have + 1; b < nb; ++b) mbar_wait_bounded(&bars[b], 0);  // let copies in flight land
+          for (int b = have + 1; b < nxt; ++b)  // let copies in flight land
+            mbar_wait_bounded(&bars[slot_of(b)], RG ? static_cast<uint32_t>(((b * a.ring_mul) >> 20) & 1) : 0u);
         }
         return false;
       }
@@ -214,6 +238,17 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
       }
     }
     return true;
+  };
+  // Ring form: loads the boxes whose slots the g-scan, done to row e_done,
+  // has freed.  The h-scan's in-place stores went to those slots, so every
+  // lane orders them before the copy (proxy fence), then lane 0 issues.
+  auto release = [&](int e_done) {
+    while (nxt < nb && 32 * (nxt - NR) + 30 + w <= e_done) {
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) issue(nxt);
+      ++nxt;
+    }
   };
   // stores output row y from the lane's words
   auto store = [&](int y, const Wv& v, bool vec) {
@@ -237,7 +272,7 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
   const int beta = Lr % w;
   for (int E0 = beta ? beta : w; E0 <= Lr; E0 += w) {
     const int lo = E0 - w > 0 ? E0 - w : 0;
-    if (!ensure(E0 + w - 1)) return false;
+    if (!ensure(RG ? E0 : E0 + w - 1)) return false;
     // h-scan, rows E0-1 down to lo, in place
     C h[NWL];
 #pragma unroll
@@ -280,12 +315,13 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
     const int e_emit = E0 > w - 1 ? E0 : w - 1;
     const int last = E0 + w - 2;
     int e = E0;
+    if (RG && !ensure(e_emit)) return false;
     for (; e < e_emit; ++e) {
       const Wv x = LD(e);
 #pragma unroll
       for (int i = 0; i < NWL; ++i) g[i] = cw_op<OP, E>(g[i], cw_of<E>(x.v[i]));
     }
-    if (!col_in) continue;
+    if (!RG && !col_in) continue;
     // emission of output e-w+1 from the g-prefix and h-suffix; the vector
     // form walks one output pointer down the rows (the branch and the row
     // address stay out of the scan)
@@ -298,7 +334,40 @@ __device__ __forceinline__ bool colv_tile(const ColvArgs& a, const CUtensorMap* 
       }
       return o;
     };
-    if (fast) {
+    if (RG) {
+      // every lane runs the same loops (the releases synchronise the
+      // warp); only the store differs
+      uint8_t* out = a.dst + static_cast<long long>(y0 + e - w + 1) * a.dp + static_cast<long long>(px0) * E;
+      for (; e + (kB - 1) <= last; e += kB) {
+        if (!ensure(e + kB)) return false;
+        Wv xe[kB], xh[kB];
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+          xe[t] = LD(e + t);
+          xh[t] = LD(e + t - w + 1);
+        }
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+          const Wv o = emit(xe[t], xh[t]);
+          if (fast)
+            wd_st<NWL>(out, o);
+          else if (col_in)
+            store(y0 + e + t - w + 1, o, false);
+          out += a.dp;
+        }
+        release(e + kB - 1);
+      }
+      for (; e <= last; ++e) {
+        if (!ensure(e + 1)) return false;
+        const Wv o = emit(LD(e), LD(e - w + 1));
+        if (fast)
+          wd_st<NWL>(out, o);
+        else if (col_in)
+          store(y0 + e - w + 1, o, false);
+        out += a.dp;
+        release(e);
+      }
+    } else if (fast) {
       uint8_t* out = a.dst + static_cast<long long>(y0 + e - w + 1) * a.dp + static_cast<long long>(px0) * E;
       for (; e + (kB - 1) <= last; e += kB) {
         Wv xe[kB], xh[kB];
@@ -350,10 +419,12 @@ struct ColvPlan {
   int wps;  // warps resident per SM
 };
 
-inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, int nwl) {
+// cap_box > 0: at most that many boxes per warp (the ring form).
+inline ColvPlan colv_shape(int esz, int W, int H, int w, int max_smem, int L, int nwl, int cap_box = 0) {
   ColvPlan p{0, 0, 0, 0, 0, nwl, false};
   const int ns = (W * esz + kCvBytes * nwl - 1) / (kCvBytes * nwl);
-  const int nbox = (L + w - 1 + kCvBox - 1) / kCvBox;
+  int nbox = (L + w - 1 + kCvBox - 1) / kCvBox;
+  if (cap_box > 0 && nbox > cap_box) nbox = cap_box;
   if (nbox > kCvMaxBox) return p;
   int wpc = 0, wps = 0;
   for (int c = 4; c >= 1; c /= 2) {
@@ -410,6 +481,29 @@ inline ColvPlan colv_plan(int esz, int W, int H, int w, int max_smem, int forced
     if (!q.ok) continue;
     p = q;
     if (enough(q)) break;
+  }
+  return p;
+}
+
+
+// The ring form's plan: nring = ceil((w + 39) / 32) + 1 boxes per warp
+// (see colv_tile), tiles of L = k w rows (whole blocks), k the largest of 1
+// .. 8 (L <= 1024) whose tiles still give at least 0.6 x the warps resident
+// on the whole GPU; forced_L > 0 overrides.  Needs TMA-loaded rows.
+inline int colv_ring_boxes(int w) { return (w + 39 + kCvBox - 1) / kCvBox + 1; }
+inline ColvPlan colv_ring_plan(int esz, int W, int H, int w, int max_smem, int forced_L, int sms) {
+  ColvPlan p{0, 0, 0, 0, 0, 1, false, 0};
+  if (w < 2 || W < 1 || H < 1) return p;
+  const int nr = colv_ring_boxes(w);
+  const int hmax = H < 1024 ? H : 1024;
+  if (forced_L > 0) return colv_shape(esz, W, H, w, max_smem, forced_L < hmax ? forced_L : hmax, 1, nr);
+  p = colv_shape(esz, W, H, w, max_smem, w < hmax ? w : hmax, 1, nr);
+  if (!p.ok || sms <= 0) return p;
+  for (int k = 8; k >= 2; --k) {
+    const int L = k * w;
+    if (L > hmax) continue;
+    const ColvPlan q = colv_shape(esz, W, H, w, max_smem, L, 1, nr);
+    if (q.ok && 5ll * q.ntask >= 3ll * sms * q.wps) return q;
   }
   return p;
 }

@@ -534,11 +534,17 @@ int main() {
       }
       a.tma_ld = c.tma_ld;
     }
-    const bool use_colv = kern == 4 && L.wx == 1 && L.wy > 1;
+    const bool use_colv = (kern == 4 || kern == 8) && L.wx == 1 && L.wy > 1 &&
+                          (kern == 4 || tma_ok(src, sp, kCvBytes / esz, kCvBox));
     if (use_colv) {
       // the warp-tiled pass along y, planned and launched as colv_launch does
-      const int nwl = (seed / 2) % 2 ? 2 : 1;  // words per lane
-      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200), nwl, 152);
+      const int nwl = kern == 8 ? 1 : (seed / 2) % 2 ? 2 : 1;  // words per lane
+      // the ring form: kernel 8, and half the one-word cases of kernel 4
+      // whose rows TMA can load
+      const bool ring = kern == 8 || (nwl == 1 && (seed / 4) % 2 == 1 && tma_ok(src, sp, kCvBytes / esz, kCvBox));
+      const int forced = (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200);
+      const ColvPlan p = ring ? colv_ring_plan(esz, W, H, L.wy, kMaxSmemBytes, forced, (seed % 3) ? 152 : 3)
+                              : colv_plan(esz, W, H, L.wy, kMaxSmemBytes, forced, nwl, 152);
       if (!p.ok) {
         printf("FAIL case %d: no colv plan\n", cases);
         ++failures;
@@ -563,11 +569,15 @@ int main() {
       c.st_vec = (reinterpret_cast<uintptr_t>(dst) % (4 * nwl) == 0) && (dp % (4 * nwl) == 0);
       c.err = &errword;
       c.tma_ld = tma_ok(src, sp, kCvBytes * nwl / esz, kCvBox);
+      c.nring = ring ? p.nbox : 0;
+      c.ring_mul = ring ? ((1 << 20) + p.nbox - 1) / p.nbox : 0;
       EmuMap mc{src, nullptr, esz, W, H, sp, kCvBytes * nwl / esz, kCvBox};
       CUtensorMap tc{};
       memcpy(&tc, &mc, sizeof(mc));
       using VFn = bool (*)(const ColvArgs&, const CUtensorMap*, int, int, uint8_t*, uint64_t*);
-      VFn vf = nwl == 2 ? (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 2> : colv_tile<uint8_t, 1, 2>)
+      VFn vf = ring ? (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 1, true> : colv_tile<uint8_t, 1, 1, true>)
+                                : (op == 0 ? colv_tile<uint16_t, 0, 1, true> : colv_tile<uint16_t, 1, 1, true>))
+               : nwl == 2 ? (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 2> : colv_tile<uint8_t, 1, 2>)
                                     : (op == 0 ? colv_tile<uint16_t, 0, 2> : colv_tile<uint16_t, 1, 2>))
                         : (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 1> : colv_tile<uint8_t, 1, 1>)
                                     : (op == 0 ? colv_tile<uint16_t, 0, 1> : colv_tile<uint16_t, 1, 1>));
@@ -576,6 +586,8 @@ int main() {
         EmuCta cta;
         std::barrier<> bar(nthr);
         cta.bar = &bar;
+        std::barrier<>* wbv[8] = {};  // per warp (__syncwarp, __all_sync of the ring form)
+        for (int wi = 0; wi < c.wpc; ++wi) cta.wbar[wi] = wbv[wi] = new std::barrier<>(32);
         uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (p.smem + 127) / 128 * 128));
         cta.smem = sm;
         cta.smem_size = p.smem;
@@ -603,6 +615,7 @@ int main() {
               vf(c, &tc, task, lane, tile, bars);
             },
             nthr);
+        for (int wi = 0; wi < c.wpc; ++wi) delete wbv[wi];
         free(sm);
         errors += cta.errors.load();
         if (cta.errors.load() && first.empty()) first = cta.first_error;
@@ -891,7 +904,7 @@ int main() {
     printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
            "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_cols ? 7 : use_colw ? 6 : use_rowv ? 5 : use_colv ? 4 : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_cols ? 7 : use_colw ? 6 : use_rowv ? 5 : use_colv ? kern : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);

@@ -36,10 +36,12 @@ def windows_1d(n):
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
-@pytest.mark.parametrize("mode", [1, 4])
+@pytest.mark.parametrize("mode", [1, 4, 6])
 @pytest.mark.parametrize("rows", [0, 8, 40, 128, 512])
 def test_pass_along_y_warp_tiled(lib, dtype, mode, rows):
-    """mode 1: one word per lane (128-byte strips); 4: two (256-byte)."""
+    """mode 1: one word per lane (128-byte strips); 4: two (256-byte); 6:
+    the ring form where rows are TMA-loadable (the tile's rows cycle
+    through a few boxes), the whole-tile form elsewhere."""
     torch = need_cuda()
     g = synth.rng(300 + rows + mode)
     try:
