@@ -210,7 +210,11 @@ class GpuExecutor:
     def finish(self, r: ServeRequest) -> None:
         out, buf = r.out
         if self.keep is not None:
+            # the copy runs on the current stream, which is not ordered with
+            # the executor's streams: it must complete before the buffer
+            # returns to the pool, or a later micro-batch may overwrite it
             self.keep[r.rid] = out.clone()
+            self.torch.cuda.current_stream().synchronize()
         c = buf.numel()
         if self.pooled + c <= self.pool_cap:
             self.free[c].append(buf)
