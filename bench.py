@@ -231,6 +231,81 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def measure_composite(torch, morph, reps: int = 7) -> dict:
+    """Opening, closing and gradient of a 4096 x 4096 image (u8 and u16,
+    21 x 51 and 127 x 127) as one morph_composite call, against the same
+    steps as separate morph_apply calls into a caller buffer (opening and
+    closing: two calls; gradient: two calls, without the subtraction).  Both
+    are timed as CUDA-graph replays of 8 calls; the results are checked
+    identical first.  Algorithmic bytes: read and write the image once."""
+    out = {}
+    for dt, tdt, code, name in ((np.uint8, torch.uint8, morph.MORPH_U8, "u8"),
+                                (np.uint16, torch.uint16, morph.MORPH_U16, "u16")):
+        img = synth.uniform_image(SIDE, SIDE, dt, seed=960)
+        esz = np.dtype(dt).itemsize
+        srcs = [torch.from_numpy(img).cuda() for _ in range(4)]
+        dsts = [torch.empty_like(srcs[0]) for _ in range(4)]
+        tmp = torch.empty_like(srcs[0])
+        pitch = SIDE * esz
+        for (wx, wy) in ((21, 51), (127, 127)):
+            ax, ay = wx // 2, wy // 2
+            rx, ry = wx - 1 - ax, wy - 1 - ay
+            for kind, kname in ((morph.MORPH_OPEN, "open"), (morph.MORPH_CLOSE, "close"),
+                                (morph.MORPH_GRADIENT, "gradient")):
+                first = morph.MORPH_DILATE if kind == morph.MORPH_CLOSE else morph.MORPH_ERODE
+                second = morph.MORPH_ERODE if kind == morph.MORPH_CLOSE else morph.MORPH_DILATE
+                sa, sb = (ax, ay) if kind == morph.MORPH_GRADIENT else (rx, ry)
+
+                def one(i, sh):
+                    rc = morph.morph_composite(srcs[i % 4].data_ptr(), pitch, dsts[i % 4].data_ptr(), pitch, SIDE,
+                                               SIDE, code, kind, wx, wy, ax, ay, sh)
+                    if rc != 0:
+                        raise morph.MorphError("morph_composite", rc)
+
+                def sep(i, sh):
+                    s, d = srcs[i % 4], dsts[i % 4]
+                    a_src = s.data_ptr()
+                    b_src = a_src if kind == morph.MORPH_GRADIENT else tmp.data_ptr()
+                    for (sp_, dp_, op, x_, y_) in ((a_src, tmp.data_ptr(), first, ax, ay),
+                                                   (b_src, d.data_ptr(), second, sa, sb)):
+                        rc = morph.morph_apply(sp_, pitch, dp_, pitch, SIDE, SIDE, code, op, wx, wy, x_, y_, sh)
+                        if rc != 0:
+                            raise morph.MorphError("morph_apply", rc)
+
+                st = torch.cuda.current_stream()
+                one(0, st.cuda_stream)
+                torch.cuda.synchronize()
+                ref = dsts[0].clone()
+                if kind != morph.MORPH_GRADIENT:
+                    sep(0, st.cuda_stream)
+                    torch.cuda.synchronize()
+                    if not torch.equal(ref, dsts[0]):
+                        raise RuntimeError("composite differs from separate calls")
+                times = {}
+                for label, fn in (("composite", one), ("separate", sep)):
+                    g = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(g):
+                        for i in range(8):
+                            fn(i, torch.cuda.current_stream().cuda_stream)
+                    for _ in range(2):
+                        g.replay()
+                    torch.cuda.synchronize()
+                    ts = []
+                    for _ in range(reps):
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        g.replay()
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1) * 1e3 / 8)
+                    times[label] = round(sorted(ts)[len(ts) // 2], 2)
+                out["%s_%s_%dx%d" % (name, kname, wx, wy)] = {
+                    "us_per_call": times["composite"], "separate_calls_us": times["separate"],
+                    "gpix_s": round(SIDE * SIDE / times["composite"] / 1e3, 1)}
+        del srcs, dsts, tmp
+    return out
+
+
 def measure_batched(torch, morph, reps: int = 5) -> dict:
     """2000 uneven u8 images: one CUDA-graph persistent launch against 2000
     per-image morph_apply calls on one stream (inputs 2.2 GB, larger than L2).
@@ -529,6 +604,7 @@ def run_gpu(args):
     extras = {}
     if not args.no_extras:
         extras["batched"] = measure_batched(torch, morph)
+        extras["composite"] = measure_composite(torch, morph)
         extras["serving"] = measure_serving(torch, rates=args.serving_rates,
                                             duration_s=args.serving_seconds)
 

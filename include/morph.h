@@ -107,6 +107,29 @@ int morph_apply(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
                 int wx, int wy, int anchor_x, int anchor_y, void *stream);
 
 /*
+ * Composite operations (section 2: opening, closing and the morphological
+ * gradient are expressed through erosion, dilation and arithmetic), one call
+ * on the caller's stream:
+ *   MORPH_OPEN      dilation by the reflected element of the erosion:
+ *                   dilate(erode(S, wx x wy, (ax, ay)), wx x wy,
+ *                          (wx-1-ax, wy-1-ay)); idempotent for every window
+ *   MORPH_CLOSE     erosion by the reflected element of the dilation
+ *   MORPH_GRADIENT  dilate(S) - erode(S), both by the same element and
+ *                   anchor (never negative)
+ * Arguments as in morph_apply (kind replaces op; the anchor is the first
+ * step's).  The library allocates one scratch image of width x height pixels
+ * (pitch rounded to 16 bytes) with cudaMallocAsync on the stream and frees it
+ * there, so the intermediate stays in L2 where it fits; the call is safe to
+ * capture in a CUDA graph.  The gradient's subtraction is a separate
+ * elementwise kernel.  Errors as morph_apply; MORPH_ERR_ARG for another kind,
+ * MORPH_ERR_NOMEM when the scratch cannot be allocated.
+ */
+enum { MORPH_OPEN = 0, MORPH_CLOSE = 1, MORPH_GRADIENT = 2 };
+int morph_composite(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
+                    int width, int height, int dtype, int kind,
+                    int wx, int wy, int anchor_x, int anchor_y, void *stream);
+
+/*
  * Host-buffer form: src and dst are HOST pointers (pinned memory gives full
  * copy speed; pageable memory works).  The library copies the image to a
  * device staging buffer that it owns and reuses (grown on demand, one pair per

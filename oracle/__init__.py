@@ -19,6 +19,10 @@ Functions (all integer, so exact; see the C file's header for the citations):
   checker (section 5, section 5.1.1).
 * ``line_wedge(line, w, a, op)`` -- monotone-deque 1-D sliding min/max.
 * ``transpose(src)`` -- section 4, D[j][i] = S[i][j].
+* ``opening``, ``closing``, ``gradient`` -- section 2's compositions of
+  erosion, dilation and arithmetic (the second step of an opening or closing
+  by the reflected element; the gradient is dilation minus erosion by the
+  same element).
 """
 from __future__ import annotations
 
@@ -198,3 +202,15 @@ def closing(src: np.ndarray, wx: int, wy: int, ax: int | None = None,
     ay = wy // 2 if ay is None else ay
     d = morph(src, wx, wy, ax, ay, "dilate")
     return morph(d, wx, wy, reflect_anchor(wx, ax), reflect_anchor(wy, ay), "erode")
+
+
+def gradient(src: np.ndarray, wx: int, wy: int, ax: int | None = None,
+             ay: int | None = None) -> np.ndarray:
+    """Morphological gradient: dilation minus erosion by the same element and
+    anchor (section 2: expressed through erosion, dilation and arithmetic).
+    Never negative, so it fits the source's pixel type."""
+    ax = wx // 2 if ax is None else ax
+    ay = wy // 2 if ay is None else ay
+    d = morph(src, wx, wy, ax, ay, "dilate")
+    e = morph(src, wx, wy, ax, ay, "erode")
+    return (d - e).astype(src.dtype)

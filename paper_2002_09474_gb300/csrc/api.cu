@@ -400,6 +400,36 @@ int morph_apply(const void* src, size_t src_pitch, void* dst, size_t dst_pitch, 
                     static_cast<cudaStream_t>(stream));
 }
 
+int morph_composite(const void* src, size_t src_pitch, void* dst, size_t dst_pitch, int width, int height,
+                    int dtype, int kind, int wx, int wy, int anchor_x, int anchor_y, void* stream) {
+  if (kind != MORPH_OPEN && kind != MORPH_CLOSE && kind != MORPH_GRADIENT) return MORPH_ERR_ARG;
+  int rc = validate(src, src_pitch, dst, dst_pitch, width, height, dtype, MORPH_ERODE, wx, wy, anchor_x, anchor_y);
+  if (rc != MORPH_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int esz = esz_of(dtype);
+  // the intermediate (opening, closing) or the erosion (gradient), ordered
+  // on the caller's stream and freed there
+  Scratch t;
+  if (!t.alloc(static_cast<size_t>(width) * esz, height, st)) return MORPH_ERR_NOMEM;
+  const int rx = wx - 1 - anchor_x, ry = wy - 1 - anchor_y;  // the reflected element's anchor
+  if (kind == MORPH_GRADIENT) {
+    rc = run_single(src, src_pitch, t.p, t.pitch, width, height, dtype, MORPH_ERODE, wx, wy, anchor_x, anchor_y, st);
+    if (rc == MORPH_OK)
+      rc = run_single(src, src_pitch, dst, dst_pitch, width, height, dtype, MORPH_DILATE, wx, wy, anchor_x, anchor_y,
+                      st);
+    if (rc == MORPH_OK &&
+        sub_launch(dst, static_cast<long long>(dst_pitch), t.p, static_cast<long long>(t.pitch), width * esz, height,
+                   esz, st) != cudaSuccess)
+      rc = MORPH_ERR_CUDA;
+    return rc;
+  }
+  const int first = kind == MORPH_OPEN ? MORPH_ERODE : MORPH_DILATE;
+  const int second = kind == MORPH_OPEN ? MORPH_DILATE : MORPH_ERODE;
+  rc = run_single(src, src_pitch, t.p, t.pitch, width, height, dtype, first, wx, wy, anchor_x, anchor_y, st);
+  if (rc == MORPH_OK) rc = run_single(t.p, t.pitch, dst, dst_pitch, width, height, dtype, second, wx, wy, rx, ry, st);
+  return rc;
+}
+
 int morph_erode(const uint8_t* src, int width, int height, size_t pitch, int wx, int wy, int anchor_x,
                 int anchor_y, uint8_t* dst, void* stream) {
   return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U8, MORPH_ERODE, wx, wy, anchor_x, anchor_y,

@@ -119,6 +119,11 @@ cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream);
 bool cols_fits(const FusedLaunch& L);
 cudaError_t cols_launch(const FusedLaunch& L, cudaStream_t stream);
 
+// dst -= sub for row_bytes bytes of each of H rows (pixels of esz bytes; the
+// gradient's dilation minus erosion, which never wraps).
+cudaError_t sub_launch(void* dst, long long dp, const void* sub, long long sp, int row_bytes, int H, int esz,
+                       cudaStream_t stream);
+
 // The register-blocked van Herk/Gil-Werman kernel of the pass along x
 // (9 <= wx <= 256, rows aligned to 8 * esz bytes; rowv_fits).
 bool rowv_fits(const FusedLaunch& L);

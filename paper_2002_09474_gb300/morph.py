@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "morph.h")
 MORPH_OK = 0
 MORPH_U8, MORPH_U16 = 0, 1
 MORPH_ERODE, MORPH_DILATE = 0, 1
+MORPH_OPEN, MORPH_CLOSE, MORPH_GRADIENT = 0, 1, 2
 MORPH_NOALLOC_MAX_IMAGES = 256
 
 
@@ -61,6 +62,7 @@ _SIGS = {
     "morph_erode_u16": [_vp, _i32, _i32, _sz, _i32, _i32, _i32, _i32, _vp, _vp],
     "morph_dilate_u16": [_vp, _i32, _i32, _sz, _i32, _i32, _i32, _i32, _vp, _vp],
     "morph_apply": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
+    "morph_composite": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_apply_host": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_release_staging": [],
     "morph_apply_host_batch": [ctypes.POINTER(MorphDesc), _i32, _vp],
@@ -140,6 +142,12 @@ def morph_apply(src, src_pitch, dst, dst_pitch, width, height, dtype, op, wx, wy
                 anchor_x, anchor_y, stream=0):
     return _lib.morph_apply(src, src_pitch, dst, dst_pitch, width, height, dtype, op, wx, wy,
                             anchor_x, anchor_y, stream)
+
+
+def morph_composite(src, src_pitch, dst, dst_pitch, width, height, dtype, kind, wx, wy,
+                    anchor_x, anchor_y, stream=0):
+    return _lib.morph_composite(src, src_pitch, dst, dst_pitch, width, height, dtype, kind, wx, wy,
+                                anchor_x, anchor_y, stream)
 
 
 def morph_apply_host(src, src_pitch, dst, dst_pitch, width, height, dtype, op, wx, wy,
@@ -282,6 +290,23 @@ def apply(src, dst, wx: int, wy: int, anchor_x: int | None = None, anchor_y: int
     _check("morph_apply", morph_apply(src.data_ptr(), _pitch(src), dst.data_ptr(), _pitch(dst),
                                       w, h, _dtype_code(src), op, wx, wy, ax, ay,
                                       _stream_handle(stream)))
+
+
+def composite(src, dst, kind: int, wx: int, wy: int, anchor_x: int | None = None,
+              anchor_y: int | None = None, stream=None) -> None:
+    """morph_composite (MORPH_OPEN, MORPH_CLOSE or MORPH_GRADIENT) on two
+    CUDA tensors of shape (height, width).  Raises MorphError on a negative
+    status."""
+    if src.shape != dst.shape or src.dtype != dst.dtype:
+        raise ValueError("src and dst must have the same shape and dtype")
+    if not (src.is_cuda and dst.is_cuda):
+        raise ValueError("src and dst must be CUDA tensors")
+    h, w = src.shape
+    ax = wx // 2 if anchor_x is None else anchor_x
+    ay = wy // 2 if anchor_y is None else anchor_y
+    _check("morph_composite", morph_composite(src.data_ptr(), _pitch(src), dst.data_ptr(), _pitch(dst),
+                                              w, h, _dtype_code(src), kind, wx, wy, ax, ay,
+                                              _stream_handle(stream)))
 
 
 def apply_host(src, dst, wx: int, wy: int, anchor_x: int | None = None, anchor_y: int | None = None,

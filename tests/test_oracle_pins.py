@@ -308,3 +308,28 @@ def test_bad_arguments_rejected():
     for args in ((0, 1, 0, 0), (1, 0, 0, 0), (3, 3, 3, 0), (3, 3, 0, 3), (3, 3, -1, 0)):
         with pytest.raises(ValueError):
             oracle.morph(img, *args, op="erode")
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_gradient_against_window_range_brute_force(dtype):
+    """The gradient is the range (max - min) of each pixel's clipped window,
+    written out here in plain Python loops; constant images and 1 x 1 windows
+    give 0; it never exceeds the type's range."""
+    g = synth.rng(901)
+    hi = np.iinfo(dtype).max
+    for _ in range(12):
+        h, w = int(g.integers(1, 9)), int(g.integers(1, 9))
+        wx, wy = int(g.integers(1, 2 * w + 2)), int(g.integers(1, 2 * h + 2))
+        ax, ay = int(g.integers(0, wx)), int(g.integers(0, wy))
+        x = g.integers(0, hi + 1, size=(h, w)).astype(dtype)
+        want = np.zeros_like(x)
+        for y in range(h):
+            for xx in range(w):
+                cells = [int(x[v, u]) for v in range(y - ay, y - ay + wy) for u in range(xx - ax, xx - ax + wx)
+                         if 0 <= v < h and 0 <= u < w]
+                want[y, xx] = max(cells) - min(cells)
+        np.testing.assert_array_equal(oracle.gradient(x, wx, wy, ax, ay), want)
+    c = np.full((7, 5), 3 if dtype == np.uint8 else 40000, dtype)
+    np.testing.assert_array_equal(oracle.gradient(c, 3, 5), np.zeros_like(c))
+    x = g.integers(0, hi + 1, size=(6, 6)).astype(dtype)
+    np.testing.assert_array_equal(oracle.gradient(x, 1, 1), np.zeros_like(x))
