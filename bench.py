@@ -390,13 +390,19 @@ def measure_batched(torch, morph, reps: int = 5) -> dict:
             "ms": {"graph": round(t_graph, 3), "per_image": round(t_img, 3), "morph_batch": round(t_batch, 3)}}
 
 
-def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0) -> list:
+def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0, host_copies: bool = False) -> list:
     """Poisson request streams through the continuous-batching server, 4 GB
-    admission budget, inputs pre-staged in device memory (host-to-device
-    copies excluded).  A short run at the same rate warms the pools first."""
+    admission budget.  Inputs pre-staged in device memory (host-to-device
+    copies excluded), or, with host_copies, pinned host images copied in and
+    results copied back to pinned host buffers inside each request's latency
+    (HostCopyExecutor).  A short run at the same rate warms the pools first."""
     from paper_2002_09474_gb300 import serve
-    pool_img, pool_dev = serve.source_pool(torch, seed=6)
-    ex = serve.GpuExecutor(n_streams=4)
+    if host_copies:
+        pool_img, pool_dev = serve.host_source_pool(torch, seed=6)
+        ex = serve.HostCopyExecutor(n_streams=4)
+    else:
+        pool_img, pool_dev = serve.source_pool(torch, seed=6)
+        ex = serve.GpuExecutor(n_streams=4)
     out = []
     for rate in rates:
         warm = serve.make_requests(rate, min(0.5, duration_s), pool_img, pool_dev, seed=60)
@@ -607,6 +613,8 @@ def run_gpu(args):
         extras["composite"] = measure_composite(torch, morph)
         extras["serving"] = measure_serving(torch, rates=args.serving_rates,
                                             duration_s=args.serving_seconds)
+        extras["serving_host_copies"] = measure_serving(torch, rates=args.serving_rates,
+                                                        duration_s=args.serving_seconds, host_copies=True)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,

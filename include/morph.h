@@ -125,6 +125,18 @@ int morph_apply(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
  * MORPH_ERR_NOMEM when the scratch cannot be allocated.
  */
 enum { MORPH_OPEN = 0, MORPH_CLOSE = 1, MORPH_GRADIENT = 2 };
+
+/*
+ * Asynchronous 2-D copy of `height` rows of `width_bytes` bytes between any
+ * two of host (pinned for full speed and true asynchrony) and device memory,
+ * in the order of `stream` (cudaMemcpy2DAsync with the direction taken from
+ * the pointers).  No counterpart in the paper: the serving loop's host-copy
+ * form stages request images through it.  MORPH_ERR_NULL for a null
+ * pointer, MORPH_ERR_SIZE for height < 1, MORPH_ERR_PITCH when a pitch is
+ * below width_bytes, MORPH_ERR_CUDA when the copy cannot be queued.
+ */
+int morph_copy_2d(void *dst, size_t dst_pitch, const void *src, size_t src_pitch,
+                  size_t width_bytes, int height, void *stream);
 int morph_composite(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
                     int width, int height, int dtype, int kind,
                     int wx, int wy, int anchor_x, int anchor_y, void *stream);

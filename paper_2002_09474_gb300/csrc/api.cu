@@ -430,6 +430,18 @@ int morph_composite(const void* src, size_t src_pitch, void* dst, size_t dst_pit
   return rc;
 }
 
+int morph_copy_2d(void* dst, size_t dst_pitch, const void* src, size_t src_pitch, size_t width_bytes, int height,
+                  void* stream) {
+  if (!dst || !src) return MORPH_ERR_NULL;
+  if (height < 1) return MORPH_ERR_SIZE;
+  if (dst_pitch < width_bytes || src_pitch < width_bytes) return MORPH_ERR_PITCH;
+  if (width_bytes == 0) return MORPH_OK;
+  return cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, width_bytes, static_cast<size_t>(height), cudaMemcpyDefault,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? MORPH_OK
+             : MORPH_ERR_CUDA;
+}
+
 int morph_erode(const uint8_t* src, int width, int height, size_t pitch, int wx, int wy, int anchor_x,
                 int anchor_y, uint8_t* dst, void* stream) {
   return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U8, MORPH_ERODE, wx, wy, anchor_x, anchor_y,

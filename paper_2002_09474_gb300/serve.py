@@ -10,9 +10,14 @@ found by polling CUDA events; a completed request frees its budget and its
 output buffer goes back to a pool for reuse.  Latency is arrival to
 completion.
 
-Inputs are pre-staged in device memory (requests point into a resident
-source pool), so host-to-device copies are not part of the latency; the
-budget still charges each request its input bytes as if staged.
+With ``GpuExecutor`` inputs are pre-staged in device memory (requests point
+into a resident source pool), so host-to-device copies are not part of the
+latency; the budget still charges each request its input bytes as if
+staged.  With ``HostCopyExecutor`` requests hold pinned HOST images: each
+micro-batch's stream copies its inputs to device buffers, runs the batch and
+copies the results back to pinned host buffers, so the latency (arrival to
+the results in host memory) includes both copies, and the copies of one
+micro-batch overlap the filtering of others on the other streams.
 
 The scheduling logic is independent of CUDA: it talks to an executor
 (``GpuExecutor`` here; tests use a host-only fake).
@@ -246,6 +251,103 @@ class GpuExecutor:
 
     def idle_wait(self) -> None:
         time.sleep(0.00005)
+
+
+class HostCopyExecutor(GpuExecutor):
+    """GpuExecutor for requests whose ``src`` is a pinned HOST image (a 2-D
+    CPU tensor, rows may be strided).  Each request takes a device input and
+    a device output buffer (both pooled in power-of-two size classes, both
+    charged to the budget) and a pinned host output buffer (pooled the same
+    way); ``launch`` queues, on the micro-batch's stream, the copies in
+    (morph_copy_2d), the persistent launch (morph_batch) and the copies out,
+    then records the completion event."""
+
+    def __init__(self, device="cuda", n_streams: int = 4, pool_cap: int = 4 << 30,
+                 host_pool_cap: int = 4 << 30):
+        super().__init__(device=device, n_streams=n_streams, pool_cap=pool_cap)
+        self.host_free = collections.defaultdict(list)
+        self.host_pooled = 0
+        self.host_pool_cap = host_pool_cap
+
+    def charge(self, r: ServeRequest) -> int:
+        """Device input and output buffers' size classes."""
+        return 2 * self.size_class(r.width * r.height * r.dtype_size)
+
+    def _dev(self, c):
+        if self.free[c]:
+            self.pooled -= c
+            return self.free[c].pop()
+        return self.torch.empty(c, dtype=self.torch.uint8, device=self.device)
+
+    def _host(self, c):
+        if self.host_free[c]:
+            self.host_pooled -= c
+            return self.host_free[c].pop()
+        return self.torch.empty(c, dtype=self.torch.uint8).pin_memory()
+
+    def _view(self, buf, r):
+        v = buf[:r.width * r.height * r.dtype_size]
+        if r.dtype_size == 2:
+            v = v.view(self.torch.uint16)
+        return v.view(r.height, r.width)
+
+    def alloc_out(self, r: ServeRequest):
+        c = self.size_class(r.width * r.height * r.dtype_size)
+        din, dout, hout = self._dev(c), self._dev(c), self._host(c)
+        return (self._view(hout, r), (din, dout, hout))
+
+    def finish(self, r: ServeRequest) -> None:
+        out, (din, dout, hout) = r.out
+        if self.keep is not None:
+            self.keep[r.rid] = out.clone()  # host memory, complete at the event
+        c = din.numel()
+        for b in (din, dout):
+            if self.pooled + c <= self.pool_cap:
+                self.free[c].append(b)
+                self.pooled += c
+        if self.host_pooled + c <= self.host_pool_cap:
+            self.host_free[c].append(hout)
+            self.host_pooled += c
+        r.out = None
+
+    def launch(self, reqs, stream_index: int):
+        m = self.morph
+        s = self.streams[stream_index]
+        sh = s.cuda_stream
+        descs = (m.MorphDesc * len(reqs))()
+        for d, r in zip(descs, reqs):
+            _, (din, dout, _) = r.out
+            row = r.width * r.dtype_size
+            src = r.src
+            rc = m.morph_copy_2d(din.data_ptr(), row, src.data_ptr(), src.stride(0) * src.element_size(), row,
+                                 r.height, sh)
+            if rc != 0:
+                raise m.MorphError("morph_copy_2d", rc)
+            d.src, d.dst = din.data_ptr(), dout.data_ptr()
+            d.width, d.height = r.width, r.height
+            d.src_pitch = d.dst_pitch = row
+            d.wx, d.wy, d.anchor_x, d.anchor_y = r.wx, r.wy, r.ax, r.ay
+            d.op = r.op
+            d.dtype = m.MORPH_U8 if r.dtype_size == 1 else m.MORPH_U16
+        rc = m.morph_batch(descs, len(reqs), sh)
+        if rc != 0:
+            raise m.MorphError("morph_batch", rc)
+        for r in reqs:
+            out, (_, dout, _) = r.out
+            row = r.width * r.dtype_size
+            rc = m.morph_copy_2d(out.data_ptr(), row, dout.data_ptr(), row, row, r.height, sh)
+            if rc != 0:
+                raise m.MorphError("morph_copy_2d", rc)
+        ev = self.torch.cuda.Event()
+        ev.record(s)
+        return ev
+
+
+def host_source_pool(torch, width: int = 4096, height: int = 4096, seed: int = 6):
+    """The u8 source pool as a pinned host tensor (and its numpy copy)."""
+    from paper_2002_09474_gb300 import synth
+    img = synth.uniform_image(width, height, np.uint8, seed=seed)
+    return img, torch.from_numpy(img.copy()).pin_memory()
 
 
 def source_pool(torch, width: int = 4096, height: int = 4096, seed: int = 6, device="cuda"):

@@ -116,3 +116,35 @@ def test_serving_budget_binds(env):
         alone = torch.empty((r.height, r.width), dtype=torch.uint8, device="cuda")
         morph.apply(r.src, alone, r.wx, r.wy, r.ax, r.ay, op=r.op)
         assert torch.equal(alone, ex.keep[r.rid]), r
+
+
+def test_serving_with_host_copies(env):
+    """Requests hold pinned host images; each micro-batch copies its inputs
+    in, filters and copies the results back on its stream: every result (in
+    host memory) equals the request run alone on the device, a sample equals
+    the oracle, and the budget (device input and output buffers) holds."""
+    torch, morph = env
+    from paper_2002_09474_gb300 import serve
+    pool_img, pool_host = serve.host_source_pool(torch, seed=8)
+    rs = serve.make_requests(3000.0, 0.1, pool_img, pool_host, seed=8)
+    assert len(rs) > 150
+    ex = serve.HostCopyExecutor(n_streams=4)
+    ex.keep = {}
+    budget = 2 << 30
+    st = serve.Server(ex, budget_bytes=budget).run(rs, timeout_s=120)
+    torch.cuda.synchronize()
+    assert morph.morph_device_error() == 0
+    assert st.completed == len(rs) and st.rejected == 0 and st.batches > 1
+    assert st.max_budget_used <= budget
+    for r in rs:
+        res = ex.keep[r.rid]
+        assert not res.is_cuda
+        src = r.src.cuda()
+        alone = torch.empty_like(src)
+        morph.apply(src, alone, r.wx, r.wy, r.ax, r.ay, op=r.op)
+        assert torch.equal(alone.cpu(), res), r
+    for i in synth.rng(88).choice(len(rs), 16, replace=False):
+        r = rs[int(i)]
+        x0, y0 = r.origin
+        img = pool_img[y0:y0 + r.height, x0:x0 + r.width]
+        check_sample(img, ex.keep[r.rid].numpy(), r.wx, r.wy, r.ax, r.ay, r.op, 800 + int(i))
