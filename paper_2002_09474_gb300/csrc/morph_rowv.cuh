@@ -1,6 +1,6 @@
 // Pass along x (a w x 1 element; the paper's "vertical pass", section 5.2) by
-// van Herk/Gil-Werman with 8-pixel blocks, one warp per RR rows (4 or 8)
-// and a segment of columns, the block data in registers.
+// van Herk/Gil-Werman with 8-pixel blocks, one warp per RR rows (2, 4 or
+// 8) and a segment of columns, the block data in registers.
 //
 // The warp walks its segment in chunks of 256 pixels.  In a chunk, lane l
 // owns block k = 32c + l: the 8 input columns whose pixels start the windows
@@ -10,8 +10,8 @@
 // in registers into 8 column vectors, one per pixel column, each RR/2 32-bit
 // words holding the RR rows in 16-bit lanes -- the paper's transpose of
 // section 4, so that the pass along x becomes a pass over registers, two rows
-// per instruction.  Fewer rows per warp (RR = 4) halve the registers and
-// shared memory a warp needs, so twice as many warps stay resident.
+// per instruction.  Fewer rows per warp (RR = 2 by default) cut the
+// registers and shared memory a warp needs, so more warps stay resident.
 //
 // With q = (w - 1) div 8 and r = (w - 1) mod 8, output 8k + i takes the
 // window from offset i of block k to offset r + i of block k + q:
@@ -22,8 +22,9 @@
 // blocks of 8 and the whole blocks between folded from their totals.  Every
 // lane writes its block's prefixes (the last one is its total) to a ring in
 // shared memory; the outputs of chunk c are made once chunk c + 1's
-// prefixes are there.  The suffix is scanned in registers, seeded with the
-// fold of the whole blocks.
+// prefixes are there.  The whole blocks are folded by warp-shuffle doubling
+// over the two chunks' totals (from the ring for short windows), and the
+// suffix is scanned in registers, seeded with that fold.
 //
 // 8-bit pixels are widened by duplicating each byte into both halves of its
 // 16-bit lane (p * 257), which min/max.u16x2 preserve; the transposes do the
@@ -391,6 +392,9 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
       for (int i = 6; i >= 0; --i) S[i] = rv_op<OP, RR>(Vold[i], S[i + 1]);
       const int bq = (k + q) & (kRvRing - 1), bq1 = (k + q + 1) & (kRvRing - 1);
       const V Tq = rv_lds(&pb[7 * kRvRing + bq]);
+      // (a branch-free form -- one ring load per output and a select of Tq
+      // or the identity -- measured 6% slower on the GB300: the extra
+      // operation per output costs more than the branches it removes)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int n = r + i;
