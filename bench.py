@@ -231,6 +231,51 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def measure_small_images(torch, morph, reps: int = 7) -> dict:
+    """The small single-image workloads, as CUDA-graph replays of 32 calls
+    over 8 input buffers: a 640 x 480 u8 uniform image eroded by 3 x 3
+    (latency-bound: 0.3 MB), and the 1920 x 1080 u8 document-like page eroded
+    and dilated by 3, 7, 15, 31 and 61 square windows."""
+    def time_calls(img, wx, wy, op):
+        h, w = img.shape
+        srcs = [torch.from_numpy(img).cuda() for _ in range(8)]
+        dsts = [torch.empty_like(srcs[0]) for _ in range(8)]
+
+        def calls():
+            sh = torch.cuda.current_stream().cuda_stream
+            for i in range(32):
+                rc = morph.morph_apply(srcs[i % 8].data_ptr(), w, dsts[i % 8].data_ptr(), w, w, h, morph.MORPH_U8, op,
+                                       wx, wy, wx // 2, wy // 2, sh)
+                if rc != 0:
+                    raise morph.MorphError("morph_apply", rc)
+        calls()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            calls()
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3 / 32)
+        us = sorted(ts)[len(ts) // 2]
+        return {"us_per_call": round(us, 2), "gpix_s": round(w * h / us / 1e3, 1)}
+
+    out = {"640x480_u8_erode_3x3": time_calls(synth.uniform_image(640, 480, np.uint8, seed=1), 3, 3,
+                                               morph.MORPH_ERODE)}
+    doc = synth.document_image(1920, 1080, seed=2)
+    for k in (3, 7, 15, 31, 61):
+        for op, name in ((morph.MORPH_ERODE, "erode"), (morph.MORPH_DILATE, "dilate")):
+            out["1920x1080_doc_%s_%dx%d" % (name, k, k)] = time_calls(doc, k, k, op)
+    return out
+
+
 def measure_composite(torch, morph, reps: int = 7) -> dict:
     """Opening, closing and gradient of a 4096 x 4096 image (u8 and u16,
     21 x 51 and 127 x 127) as one morph_composite call, against the same
@@ -611,6 +656,7 @@ def run_gpu(args):
     if not args.no_extras:
         extras["batched"] = measure_batched(torch, morph)
         extras["composite"] = measure_composite(torch, morph)
+        extras["small_images"] = measure_small_images(torch, morph)
         extras["serving"] = measure_serving(torch, rates=args.serving_rates,
                                             duration_s=args.serving_seconds)
         extras["serving_host_copies"] = measure_serving(torch, rates=args.serving_rates,
@@ -657,9 +703,9 @@ def main(argv=None):
                     help="skip the CPU oracle sample (for profiler runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and serving measurements (for profiler runs)")
-    ap.add_argument("--serving-rates", type=float, nargs="+", default=[5000.0],
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[1000.0, 5000.0, 20000.0],
                     help="request rates of the serving measurement (req/s)")
-    ap.add_argument("--serving-seconds", type=float, default=3.0,
+    ap.add_argument("--serving-seconds", type=float, default=2.0,
                     help="length of each serving run after warm-up")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
