@@ -126,3 +126,23 @@ def test_tuning_arguments():
     assert m.morph_set_split_order(2) == -10 and m.morph_set_split_order(1) == 0
     assert m.morph_set_split_pdl(2) == -10 and m.morph_set_split_pdl(1) == 0
     assert m.morph_reset_tuning() == 0
+
+
+def test_composite_and_copy_arguments():
+    """Argument checks of morph_composite and morph_copy_2d come before any
+    CUDA call (no GPU needed)."""
+    u8 = m.MORPH_U8
+    assert m.morph_composite(FAKE, 640, FAKE2, 640, 640, 480, u8, 3, 3, 3, 1, 1, 0) == -10   # unknown kind
+    assert m.morph_composite(FAKE, 640, FAKE2, 640, 640, 480, u8, -1, 3, 3, 1, 1, 0) == -10
+    assert m.morph_composite(None, 640, FAKE2, 640, 640, 480, u8, 0, 3, 3, 1, 1, 0) == -1    # null
+    assert m.morph_composite(FAKE, 640, FAKE2, 640, 640, 480, u8, 1, 0, 3, 0, 1, 0) == -3    # window
+    assert m.morph_composite(FAKE, 640, FAKE2, 640, 640, 480, u8, 2, 3, 3, 3, 1, 0) == -4    # anchor
+    assert m.morph_composite(FAKE, 600, FAKE2, 640, 640, 480, u8, 0, 3, 3, 1, 1, 0) == -5    # pitch
+    assert m.morph_composite(FAKE, 640, FAKE + 640, 640, 640, 480, u8, 0, 3, 3, 1, 1, 0) == -6  # overlap
+    assert m.morph_composite(FAKE, 640, FAKE2, 640, 640, 0, u8, 0, 3, 3, 1, 1, 0) == -2      # size
+    assert m.morph_composite(FAKE, 640, FAKE2, 640, 640, 480, 7, 0, 3, 3, 1, 1, 0) == -9     # dtype
+    assert m.morph_copy_2d(None, 64, FAKE, 64, 64, 2, 0) == -1
+    assert m.morph_copy_2d(FAKE2, 64, None, 64, 64, 2, 0) == -1
+    assert m.morph_copy_2d(FAKE2, 64, FAKE, 64, 64, 0, 0) == -2
+    assert m.morph_copy_2d(FAKE2, 32, FAKE, 64, 64, 2, 0) == -5
+    assert m.morph_copy_2d(FAKE2, 64, FAKE, 32, 64, 2, 0) == -5
