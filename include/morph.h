@@ -406,9 +406,21 @@ long long morph_launch_count(void);
 
 /*
  * Reads and clears the device error word that kernels set when a bounded wait
- * gives up (0 = none).  Synchronises the device.
+ * gives up (0 = none; 1 = a wait for a TMA load gave up).  Synchronises the
+ * device.
  */
 int morph_device_error(void);
+
+/*
+ * Self-test of that failure detection: launches one warp that waits, with
+ * the kernels' bounded wait (2 s of the GPU's global timer), on an mbarrier
+ * phase that nothing completes.  The wait gives up, the warp records error 1
+ * in the device error word and returns, and the context stays usable: once
+ * the stream reaches it (about 2 s later) morph_device_error() returns 1.
+ * No fault, trap or unbounded wait is involved.  Returns MORPH_OK when the
+ * launch was queued, MORPH_ERR_CUDA otherwise.
+ */
+int morph_selftest_wait_timeout(void *stream);
 
 #ifdef __cplusplus
 }

@@ -442,6 +442,10 @@ int morph_copy_2d(void* dst, size_t dst_pitch, const void* src, size_t src_pitch
              : MORPH_ERR_CUDA;
 }
 
+int morph_selftest_wait_timeout(void* stream) {
+  return selftest_wait_timeout(static_cast<cudaStream_t>(stream)) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+}
+
 int morph_erode(const uint8_t* src, int width, int height, size_t pitch, int wx, int wy, int anchor_x,
                 int anchor_y, uint8_t* dst, void* stream) {
   return morph_apply(src, pitch, dst, pitch, width, height, MORPH_U8, MORPH_ERODE, wx, wy, anchor_x, anchor_y,

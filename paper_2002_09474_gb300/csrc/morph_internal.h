@@ -124,6 +124,10 @@ cudaError_t cols_launch(const FusedLaunch& L, cudaStream_t stream);
 cudaError_t sub_launch(void* dst, long long dp, const void* sub, long long sp, int row_bytes, int H, int esz,
                        cudaStream_t stream);
 
+// One warp waits, bounded, on an mbarrier phase nothing completes, and
+// records kDevErrTmaTimeout when the wait gives up (selftest.cu).
+cudaError_t selftest_wait_timeout(cudaStream_t stream);
+
 // The register-blocked van Herk/Gil-Werman kernel of the pass along x
 // (9 <= wx <= 256, rows aligned to 8 * esz bytes; rowv_fits).
 bool rowv_fits(const FusedLaunch& L);

@@ -64,6 +64,7 @@ _SIGS = {
     "morph_apply": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_composite": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_copy_2d": [_vp, _sz, _vp, _sz, _sz, _i32, _vp],
+    "morph_selftest_wait_timeout": [_vp],
     "morph_apply_host": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_release_staging": [],
     "morph_apply_host_batch": [ctypes.POINTER(MorphDesc), _i32, _vp],
@@ -149,6 +150,10 @@ def morph_composite(src, src_pitch, dst, dst_pitch, width, height, dtype, kind, 
                     anchor_x, anchor_y, stream=0):
     return _lib.morph_composite(src, src_pitch, dst, dst_pitch, width, height, dtype, kind, wx, wy,
                                 anchor_x, anchor_y, stream)
+
+
+def morph_selftest_wait_timeout(stream=0):
+    return _lib.morph_selftest_wait_timeout(stream)
 
 
 def morph_copy_2d(dst, dst_pitch, src, src_pitch, width_bytes, height, stream=0):

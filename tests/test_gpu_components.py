@@ -228,3 +228,25 @@ def test_host_batch_pipeline_matches_single_calls(lib):
     assert lib.morph_apply_host_batch(bad, 1, 0) == -3  # MORPH_ERR_WINDOW
     lib.morph_release_staging()
     lib.check_device_error()
+
+
+def test_bounded_wait_gives_up_and_context_survives(lib):
+    """Failure detection on the GPU without a fault: a warp waits, bounded,
+    on an mbarrier phase nothing completes; after the limit it records error
+    1, which morph_device_error() reports once (then 0), and the next call on
+    the same context is exact."""
+    import time
+    torch = need_cuda()
+    assert lib.morph_device_error() == 0
+    t0 = time.perf_counter()
+    assert lib.morph_selftest_wait_timeout(0) == 0
+    assert lib.morph_device_error() == 1  # synchronises: the wait has given up
+    waited = time.perf_counter() - t0
+    assert 1.5 < waited < 30.0, waited
+    assert lib.morph_device_error() == 0
+    img = synth.uniform_image(300, 200, np.uint8, seed=230)
+    s = torch.from_numpy(img).cuda()
+    o = torch.empty_like(s)
+    lib.apply(s, o, 9, 7, op=0)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(o.cpu().numpy(), oracle.morph(img, 9, 7, 4, 3, "erode"))
