@@ -287,15 +287,18 @@ int morph_set_split(int mode);
 int morph_set_split_order(int order);
 
 /*
- * Whether the second launch of that form uses programmatic dependent launch
- * (1): it may then be scheduled while the first finishes, its CTAs waiting
- * in griddepcontrol.wait before touching memory.  0 (default) launches it
- * after the first has finished.  On the GB300, 1 saved about 1% on one
- * stream but cost 12% when independent calls ran on two streams (the
- * waiting CTAs hold SMs the other stream could use).  A GPU scheduling
+ * Whether the kernels of single-image calls are launched with programmatic
+ * stream serialisation (1) or not (0).  With it a kernel may be scheduled
+ * while the previous kernel on its stream drains: that kernel lets its
+ * successor in once each of its CTAs has finished its work, and the
+ * successor's CTAs wait (griddepcontrol.wait) for the predecessor to finish
+ * and flush its memory before touching global memory, so the launch gap
+ * between consecutive calls overlaps the previous call's tail.  On by
+ * default: on the GB300 at 4096^2 it made single-stream calls 0-4% faster
+ * and two streams of independent calls 2% faster.  A GPU scheduling
  * choice; the result never changes.  MORPH_ERR_ARG for another value.
  */
-int morph_set_split_pdl(int on);
+int morph_set_pdl(int on);
 
 /*
  * Launch form of the fused kernel for single-image calls (no counterpart in
@@ -323,32 +326,21 @@ int morph_set_column_kernel(int mode);
 /*
  * Kernel of the pass along y (1 x wy windows, and the first launch of the
  * two-launch form): van Herk/Gil-Werman with blocks of wy rows (section
- * 5.1.1), one warp per tile 128 bytes wide and `rows` output rows tall, the
- * block suffix kept in place of the input rows it replaces.  mode 1: this
- * kernel for every wy >= 2 whose warp tile fits in shared memory; -1
- * (default): wherever the van Herk/Gil-Werman method is chosen (wy above the
- * crossover of section 5.3; measured faster than the column kernel there);
- * 0: never (the column kernel of morph_set_column_kernel instead); 2: as 1,
- * but for wy > 32 and TMA-loadable rows a shared-tile form in which the
- * warps of a CTA share one input tile and keep the block suffix of their 32
- * or 64 output rows in registers (measured slower on the GB300, so not a
- * default); 4: as 1, with strips 256 bytes wide, each lane owning two
- * words (two independent scan chains per lane); 5: as 1, but for 9 <= wy
- * <= 256 and TMA-loadable rows the strip-streaming form: 8-row blocks, the
- * whole blocks inside a window folded from their totals, the rows wy - 1
- * behind read a second time, so shared memory does not grow with wy (rows
- * is then the band height per warp, rounded up to a multiple of 8); 6: as
- * 1, but where rows are TMA-loadable the ring form: the tile's rows cycle
- * through ceil((wy + 39) / 32) + 1 boxes, each refilled once the scan has
- * passed it (rows: the tile height; 0: a multiple of wy).  Modes 2, 4, 5
- * and 6 were measured slower than 1 on the GB300 at the bench's windows.  rows: output rows per
- * warp tile, 1 to 1024, or 0 for the measured default (a multiple of wy
- * filling one or two 32-row input boxes below 32 rows; else wy or 2 wy up
- * to 256, or 64, with 64 or 32 where those tiles would leave the GPU's
- * SMs short of warps).  The result never changes.  MORPH_ERR_ARG for
- * another mode or rows.
+ * 5.1.1), one warp per strip of 32 lanes x lane_bytes bytes and `rows`
+ * output rows, the block suffix kept in place of the input rows it
+ * replaces.  mode 1: this kernel for every wy >= 2 whose warp tile fits in
+ * shared memory; -1 (default): wherever the van Herk/Gil-Werman method is
+ * chosen (wy above the crossover of section 5.3; measured faster than the
+ * column kernel there); 0: never (the column kernel of
+ * morph_set_column_kernel instead).  rows: output rows per warp tile, 1 to
+ * 1024, or 0 for the measured default (a multiple of wy filling one or two
+ * 32-row input boxes below 32 rows; else wy or 2 wy up to 256, or 64, with
+ * 64 or 32 where those tiles would leave the GPU's SMs short of warps).
+ * lane_bytes: 4 (strips 128 bytes wide), 8 (256 bytes, two independent scan
+ * chains per lane), or 0 for the built-in rule.  The result never changes.  MORPH_ERR_ARG for another
+ * mode, rows or lane_bytes.
  */
-int morph_set_colv(int mode, int rows);
+int morph_set_colv(int mode, int rows, int lane_bytes);
 
 /*
  * Kernel of the pass along x (wx x 1 windows, and the second launch of the

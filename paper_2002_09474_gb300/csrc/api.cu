@@ -93,13 +93,8 @@ bool use_rowv(const FusedLaunch& L) {
 
 int launch_one(FusedLaunch L, cudaStream_t stream) {
   if (!plan_single(&L)) return MORPH_ERR_WINDOW;
+  if (tuning().pdl_mode == 1) L.pdl = true;
   if (L.wx == 1 && L.wy > 1 && use_colv(L)) {
-    // mode 2: the shared-tile form where it applies
-    if (tuning().colv_mode == 2 && colw_fits(L))
-      return colw_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
-    // mode 5: the strip-streaming form where it applies
-    if (tuning().colv_mode == 5 && cols_fits(L))
-      return cols_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
     return colv_launch(L, stream) == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
   }
   if (L.wx == 1 && L.wy > 1 && tuning().col_mode != 0)
@@ -167,7 +162,6 @@ int launch_planned(FusedLaunch L, cudaStream_t stream) {
   Scratch tmp;
   if (!tmp.alloc(static_cast<size_t>(L.W) * L.esz, L.H, stream)) return MORPH_ERR_NOMEM;
   FusedLaunch A = L, B = L;
-  B.pdl = tuning().split_pdl != 0;  // the second pass may be scheduled while the first finishes
   if (tuning().split_order == 1) {  // the pass along x first
     A.wy = 1;
     A.ay = 0;
@@ -612,9 +606,9 @@ int morph_set_split_order(int order) {
   return MORPH_OK;
 }
 
-int morph_set_split_pdl(int on) {
+int morph_set_pdl(int on) {
   if (on < 0 || on > 1) return MORPH_ERR_ARG;
-  tuning().split_pdl = on;
+  tuning().pdl_mode = on;
   return MORPH_OK;
 }
 
@@ -644,10 +638,13 @@ int morph_set_row_kernel(int mode) {
   return MORPH_OK;
 }
 
-int morph_set_colv(int mode, int rows) {
-  if (mode < -1 || mode > 6 || mode == 3 || rows < 0 || rows > 1024) return MORPH_ERR_ARG;
+int morph_set_colv(int mode, int rows, int lane_bytes) {
+  if (mode < -1 || mode > 1 || rows < 0 || rows > 1024 ||
+      (lane_bytes != 0 && lane_bytes != 4 && lane_bytes != 8))
+    return MORPH_ERR_ARG;
   tuning().colv_mode = mode;
   tuning().colv_rows = rows;
+  tuning().colv_lb = lane_bytes;
   return MORPH_OK;
 }
 

@@ -16,7 +16,6 @@ __global__ void __launch_bounds__(kColThreads, 4) col_kernel(const __grid_consta
                                                              const ColArgs a) {
   __shared__ __align__(8) uint64_t bars[kColMaxBoxes];
   extern __shared__ __align__(128) uint8_t csmem[];
-  pdl_launch_dependents();
   if (a.tma_ld && threadIdx.x == 0) {
     for (int b = 0; b < kColMaxBoxes; ++b) mbar_init(&bars[b], 1);
     fence_barrier_init();
@@ -24,6 +23,7 @@ __global__ void __launch_bounds__(kColThreads, 4) col_kernel(const __grid_consta
   __syncthreads();
   pdl_wait();
   col_tile<T, OP, BLK>(a, &tin, blockIdx.x, csmem, reinterpret_cast<uint32_t*>(csmem + kColBytes * a.ihp), bars);
+  pdl_launch_dependents();
 }
 
 namespace {

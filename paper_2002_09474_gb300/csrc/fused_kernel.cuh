@@ -13,7 +13,6 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(const __grid_constan
                                                             const ImgArgs a, const Geom g) {
   __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(128) uint4 smem[];
-  pdl_launch_dependents();
   if (a.tma_ld && threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
@@ -22,6 +21,7 @@ __global__ void __launch_bounds__(kThreads, 4) fused_kernel(const __grid_constan
   pdl_wait();
   uint32_t phase = 0;
   run_tile<T, OP, TX, TY>(a, &tin, &tout, blockIdx.x * TX, blockIdx.y * TY, g, smem, &bar, phase, a.err);
+  pdl_launch_dependents();
 }
 
 // Persistent form: a grid of (SMs x resident CTAs) CTAs walks the tiles in
@@ -36,7 +36,6 @@ __global__ void __launch_bounds__(kThreads, 3) fused_pipe_kernel(const __grid_co
                                                                  int ntiles) {
   __shared__ __align__(8) uint64_t bar[2];
   extern __shared__ __align__(128) uint4 smem[];
-  pdl_launch_dependents();
   if (static_cast<int>(blockIdx.x) >= ntiles) return;  // whole CTA
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -46,6 +45,7 @@ __global__ void __launch_bounds__(kThreads, 3) fused_pipe_kernel(const __grid_co
   __syncthreads();
   pdl_wait();
   run_tiles_pipelined<T, OP, TX, TY>(a, &tin, &tout, g, smem, bar, ntx, ntiles, blockIdx.x, gridDim.x);
+  pdl_launch_dependents();
 }
 
 template <typename T, int OP>

@@ -162,10 +162,11 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialisation may start while the previous kernel on its stream is still
-// running.  Each kernel of this library lets its successor start as soon as
-// all its CTAs have started (launch_dependents), and waits for its
-// predecessor to finish and flush its memory (wait) before touching global
-// memory; without such a launch both are no-ops.
+// running.  Each kernel of this library lets its successor be scheduled once
+// every one of its CTAs has finished its work (launch_dependents at the end,
+// so the successor's CTAs take SMs only as this grid drains), and waits for
+// its predecessor to finish and flush its memory (wait) before touching
+// global memory; without such a launch both are no-ops.
 __device__ __forceinline__ void pdl_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }

@@ -110,14 +110,6 @@ cudaError_t col_launch(const FusedLaunch& L, bool blocked, cudaStream_t stream);
 // when its warp tile fits in shared memory (colv_fits).
 bool colv_fits(const FusedLaunch& L);
 cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream);
-// Its shared-tile form for wy > 32 (warps of a CTA share one TMA-loaded tile
-// and keep the block suffix in registers; colw_fits).
-bool colw_fits(const FusedLaunch& L);
-cudaError_t colw_launch(const FusedLaunch& L, cudaStream_t stream);
-// Its strip-streaming form (8-row blocks, the rows w - 1 behind read a
-// second time; 9 <= wy <= 256 and TMA-loadable rows; cols_fits).
-bool cols_fits(const FusedLaunch& L);
-cudaError_t cols_launch(const FusedLaunch& L, cudaStream_t stream);
 
 // dst -= sub for row_bytes bytes of each of H rows (pixels of esz bytes; the
 // gradient's dilation minus erosion, which never wraps).

@@ -89,12 +89,13 @@ void reset_tuning_defaults() {
   }
   g_tuning.split_mode = -1;
   g_tuning.split_order = 1;
-  g_tuning.split_pdl = 0;
+  g_tuning.pdl_mode = 1;
   g_tuning.pipe_mode = -1;
   g_tuning.col_mode = -1;
   g_tuning.row_mode = -1;
   g_tuning.colv_mode = -1;
   g_tuning.colv_rows = 0;
+  g_tuning.colv_lb = 0;
   g_tuning.rowv_mode = -1;
   g_tuning.rowv_seg = 0;
   g_tuning.rowv_rr[0] = g_tuning.rowv_rr[1] = 0;

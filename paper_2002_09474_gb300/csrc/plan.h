@@ -14,13 +14,14 @@ struct Tuning {
   int forced_cfg[2];              // [esz-1]: tile configuration to use when it fits (-1: cost model)
   int split_mode;                 // 2-D windows as two 1-D launches: -1 auto, 0 never, 1 always
   int split_order;                // their order: 0 pass along y first, 1 (default) pass along x first
-  int split_pdl;                  // their second launch with programmatic stream serialisation (0, default: no)
+  int pdl_mode;                   // single-image launches with programmatic stream serialisation: 1 (default) or 0
   int pipe_mode;                  // persistent input-prefetching kernel: -1 auto, 0 never, 1 always
   int xpass_transpose[2];         // [esz-1]: pass along x through the transpose kernels (1) or fused (0)
   int col_mode;                   // 1 x wy windows by the column kernel: -1 auto (yes), 0 never, 1 always
   int row_mode;                   // wx x 1 windows by the row kernel: -1 auto (yes), 0 never, 1 always
   int colv_mode;                  // 1 x wy passes by the warp-tiled vHGW kernel: -1 auto, 0 never, 1 always
   int colv_rows;                  // its output rows per warp tile (0: launch-shape model)
+  int colv_lb;                    // its bytes per lane (0: built-in rule; 4 or 8)
   int rowv_mode;                  // wx x 1 passes by the register-blocked vHGW kernel: -1 auto, 0 never, 1 always
   int rowv_seg;                   // its output columns per warp segment (0: launch-shape model)
   int rowv_rr[2];                 // [esz-1]: rows per warp of the pass along x (0: built-in, 2)

@@ -13,7 +13,6 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_kernel(const __grid_consta
                                                              const RowArgs a, const RowGeom g) {
   __shared__ __align__(8) uint64_t bar;
   extern __shared__ __align__(128) uint8_t rsmem[];
-  pdl_launch_dependents();
   if (a.tma_ld && threadIdx.x == 0) {
     mbar_init(&bar, 1);
     fence_barrier_init();
@@ -22,6 +21,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) row_kernel(const __grid_consta
   pdl_wait();
   uint32_t phase = 0;
   row_tile<T, OP, BLK>(a, &tin, blockIdx.x, g, rsmem, &bar, phase);
+  pdl_launch_dependents();
 }
 
 namespace {

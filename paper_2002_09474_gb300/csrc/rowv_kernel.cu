@@ -18,12 +18,12 @@ constexpr int kRvWarps = 4;  // warps per CTA
 template <typename T, int OP, int RR>
 __global__ void __launch_bounds__(32 * kRvWarps, RR == 8 ? 4 : RR == 4 ? 6 : 8) rowv_kernel(const RowvArgs a) {
   extern __shared__ __align__(128) uint8_t rvsmem[];
-  pdl_launch_dependents();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int task = blockIdx.x * kRvWarps + warp;
   if (task >= a.ntask) return;
   pdl_wait();
   rowv_task<T, OP, RR>(a, task, lane, rvsmem + warp * rv_warp_smem(sizeof(T), RR));
+  pdl_launch_dependents();
 }
 
 namespace {

@@ -81,11 +81,11 @@ _SIGS = {
     "morph_reset_tuning": [],
     "morph_set_split": [_i32],
     "morph_set_split_order": [_i32],
-    "morph_set_split_pdl": [_i32],
+    "morph_set_pdl": [_i32],
     "morph_set_pipeline": [_i32],
     "morph_set_column_kernel": [_i32],
     "morph_set_row_kernel": [_i32],
-    "morph_set_colv": [_i32, _i32],
+    "morph_set_colv": [_i32, _i32, _i32],
     "morph_set_rowv": [_i32, _i32],
     "morph_set_xpass": [_i32, _i32],
     "morph_device_error": [],
@@ -218,8 +218,8 @@ def morph_set_split_order(order):
     return _lib.morph_set_split_order(order)
 
 
-def morph_set_split_pdl(on):
-    return _lib.morph_set_split_pdl(on)
+def morph_set_pdl(on):
+    return _lib.morph_set_pdl(on)
 
 
 def morph_set_pipeline(mode):
@@ -234,8 +234,8 @@ def morph_set_row_kernel(mode):
     return _lib.morph_set_row_kernel(mode)
 
 
-def morph_set_colv(mode, rows=0):
-    return _lib.morph_set_colv(mode, rows)
+def morph_set_colv(mode, rows=0, lane_bytes=0):
+    return _lib.morph_set_colv(mode, rows, lane_bytes)
 
 
 def morph_launch_count():

@@ -1,7 +1,9 @@
 """Runs one erosion/dilation class a few times through the C ABI, for
-profiler captures of a single kernel (e.g. under ``ncu -k regex:fused -c 1``).
+profiler captures of a single kernel, e.g.
 
-  python -m paper_2002_09474_gb300.profile_case --dtype u8 --wx 127 --wy 127 --op erode --reps 3
+  python profile_case.py --dtype u8 --wx 1 --wy 101 --op erode --reps 3
+  ncu --clock-control none -k regex:ystream -s 2 -c 1 --set full -o prof \
+      python profile_case.py --dtype u8 --wx 1 --wy 101 --reps 3
 
 Inputs are seeded uniform images; nothing is checked or printed except a
 one-line summary (launch count, mean event time of the launches).
@@ -14,7 +16,7 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -35,6 +37,8 @@ def main(argv=None):
                     help="force the warp-tiled pass along y with this many rows per tile (0: model)")
     ap.add_argument("--rowv", type=int, default=-1,
                     help="force the register-blocked pass along x with this segment (0: model)")
+    ap.add_argument("--colv-lanes", type=int, default=0,
+                    help="bytes per lane of the warp-tiled pass along y (0: built-in rule; 2, 4, 8)")
     args = ap.parse_args(argv)
 
     import torch
@@ -45,8 +49,8 @@ def main(argv=None):
     dt = np.uint8 if args.dtype == "u8" else np.uint16
     code = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
     morph.morph_set_tuning(code, args.cross_row, args.cross_col, args.tile)
-    if args.colv >= 0:
-        morph.morph_set_colv(1, args.colv)
+    if args.colv >= 0 or args.colv_lanes:
+        morph.morph_set_colv(1, max(args.colv, 0), args.colv_lanes)
     if args.rowv >= 0:
         morph.morph_set_rowv(1, args.rowv)
     img = synth.uniform_image(args.width, args.height, dt, seed=1)

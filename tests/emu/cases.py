@@ -6,10 +6,8 @@ pitch and offset) also appears in the persistent two-slot form (kern 1), and
 every 1 x wy case (wy > 1) also through the column kernel (kern 2), every
 wx x 1 case (wx > 1) also through the row kernel (kern 3), and every 1 x wy
 case also through the warp-tiled van Herk/Gil-Werman kernel of the pass
-along y (kern 4); kern 5 is the register-blocked pass along x, kern 6 the
-shared-tile pass along y, kern 7 the strip-streaming pass along y, kern 8
-the ring form of the warp-tiled pass along y.  --only K keeps the cases of
-kernel K."""
+along y (kern 4, its strip width varying with the seed); kern 5 is the
+register-blocked pass along x.  --only K keeps the cases of kernel K."""
 import itertools
 import sys
 
@@ -139,50 +137,6 @@ def cases(full=True):
                         seed += 1
     for c in rowv:
         both.append(c + (5,))
-    # the shared-tile pass along y (wy > 32, TMA-loadable rows): tall and
-    # ragged images, every anchor extreme
-    colw = []
-    for esz in (1, 2):
-        for (w, h) in ((128, 1000), (300, 2100), (64, 700), (257, 333), (190, 41), (1000, 64)):
-            for wy in (33, 40, 63, 64, 65, 101, 127, 255, 700):
-                for ay in sorted({0, wy // 2, wy - 1}):
-                    for op in (0, 1):
-                        pad = aligned_pad(w, esz)
-                        dpad, doff = (pad, 0) if (wy + ay) % 2 else (esz, 3 * esz)
-                        colw.append((esz, op, w, h, pad, 0, dpad, doff, 1, wy, 0, ay, -1, -1, -1, seed))
-                        seed += 1
-    for c in colw:
-        both.append(c + (6,))
-    # the strip-streaming pass along y (9 <= wy <= 256, TMA-loadable rows):
-    # the warp-tiled kernel's cases, plus tall, short and ragged images,
-    # windows around the block and box sizes, every anchor extreme
-    cols = [c for c in colv if 9 <= c[9] <= 256]
-    for esz in (1, 2):
-        for (w, h) in ((128, 1000), (300, 2100), (64, 700), (257, 333), (190, 41), (1000, 64), (130, 16), (640, 17)):
-            for wy in (9, 10, 15, 16, 17, 24, 33, 64, 65, 101, 127, 256):
-                for ay in sorted({0, wy // 2, wy - 1}):
-                    for op in (0, 1):
-                        pad = aligned_pad(w, esz)
-                        dpad, doff = (pad, 0) if (wy + ay + op) % 2 else (esz, 3 * esz)
-                        cols.append((esz, op, w, h, pad, 0, dpad, doff, 1, wy, 0, ay, -1, -1, -1, seed))
-                        seed += 1
-    for c in cols:
-        both.append(c + (7,))
-    # the ring form of the warp-tiled pass along y (TMA-loadable rows): tall
-    # images, windows from 2 to 700 rows, every anchor extreme, tile heights
-    # forced (even seeds) or planned, so that most tiles wrap their ring
-    ring = []
-    for esz in (1, 2):
-        for (w, h) in ((128, 1000), (300, 2100), (64, 700), (257, 333), (190, 41), (1000, 64), (130, 200)):
-            for wy in (2, 9, 17, 31, 33, 51, 64, 101, 127, 200, 255, 700):
-                for ay in sorted({0, wy // 2, wy - 1}):
-                    for op in (0, 1):
-                        pad = aligned_pad(w, esz)
-                        dpad, doff = (pad, 0) if (wy + ay + op) % 2 else (esz, 3 * esz)
-                        ring.append((esz, op, w, h, pad, 0, dpad, doff, 1, wy, 0, ay, -1, -1, -1, seed))
-                        seed += 1
-    for c in ring:
-        both.append(c + (8,))
     return both
 
 

@@ -23,9 +23,8 @@
 // SMs on odd seeds and 3 SMs on even ones, 5 = the register-blocked van
 // Herk/Gil-Werman kernel of the pass along x for wx x 1 windows, when the
 // source rows allow it, its segment planned for 152 SMs on odd seeds and 3
-// SMs on even ones, 6 = the shared-tile form of the pass along y for
-// 1 x wy windows with wy > 32 and TMA-loadable rows, its warps per CTA
-// planned for 152 SMs on odd seeds and 3 SMs on even ones).
+// SMs on even ones; the warp-tiled kernel's strip width varies with the
+// seed: 4 or 8 bytes per lane).
 // Output: one line per case, "OK ..." or "FAIL ...".
 #define MORPH_HOST_EMU 1
 
@@ -133,6 +132,10 @@ static inline unsigned int __byte_perm(unsigned int x, unsigned int y, unsigned 
   }
   return r;
 }
+template <typename T>
+static inline T __ldg(const T* p) {
+  return *p;
+}
 static inline int atomicExch(int* p, int v) { return __atomic_exchange_n(p, v, __ATOMIC_SEQ_CST); }
 static inline unsigned int __funnelshift_r(unsigned int lo, unsigned int hi, unsigned int s) {
   const uint64_t v = (static_cast<uint64_t>(hi) << 32) | lo;
@@ -144,7 +147,6 @@ static inline unsigned int __funnelshift_r(unsigned int lo, unsigned int hi, uns
 #include "morph_row.cuh"
 #include "morph_colv.cuh"
 #include "morph_rowv.cuh"
-#include "morph_cols.cuh"
 
 // ---- TMA / mbarrier model ------------------------------------------------------
 struct EmuMap {
@@ -534,17 +536,14 @@ int main() {
       }
       a.tma_ld = c.tma_ld;
     }
-    const bool use_colv = (kern == 4 || kern == 8) && L.wx == 1 && L.wy > 1 &&
-                          (kern == 4 || tma_ok(src, sp, kCvBytes / esz, kCvBox));
+    const bool use_colv = kern == 4 && L.wx == 1 && L.wy > 1;
     if (use_colv) {
-      // the warp-tiled pass along y, planned and launched as colv_launch does
-      const int nwl = kern == 8 ? 1 : (seed / 2) % 2 ? 2 : 1;  // words per lane
-      // the ring form: kernel 8, and half the one-word cases of kernel 4
-      // whose rows TMA can load
-      const bool ring = kern == 8 || (nwl == 1 && (seed / 4) % 2 == 1 && tma_ok(src, sp, kCvBytes / esz, kCvBox));
+      // the warp-tiled pass along y, planned and launched as colv_launch does;
+      // bytes per lane by seed: 4 or 8
+      const int lb = (seed / 2) % 2 ? 8 : 4;
+      const int sbytes = colv_strip_bytes(lb);
       const int forced = (seed & 1) ? 0 : 1 + static_cast<int>(seed % 200);
-      const ColvPlan p = ring ? colv_ring_plan(esz, W, H, L.wy, kMaxSmemBytes, forced, (seed % 3) ? 152 : 3)
-                              : colv_plan(esz, W, H, L.wy, kMaxSmemBytes, forced, nwl, 152);
+      const ColvPlan p = colv_plan(esz, W, H, L.wy, kMaxSmemBytes, forced, lb, (seed % 3) ? 152 : 3);
       if (!p.ok) {
         printf("FAIL case %d: no colv plan\n", cases);
         ++failures;
@@ -562,31 +561,27 @@ int main() {
       c.a = L.ay;
       c.L = p.L;
       c.nbox = p.nbox;
-      c.ns = cdiv(W * esz, kCvBytes * nwl);
+      c.ns = cdiv(W * esz, sbytes);
       c.ntask = p.ntask;
       c.wpc = p.wpc;
-      c.ld_vec = a.ld_vec;
-      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % (4 * nwl) == 0) && (dp % (4 * nwl) == 0);
+      c.ld_vec = (reinterpret_cast<uintptr_t>(src) % lb == 0) && (sp % lb == 0);
+      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % lb == 0) && (dp % lb == 0);
       c.err = &errword;
-      c.tma_ld = tma_ok(src, sp, kCvBytes * nwl / esz, kCvBox);
-      c.nring = ring ? p.nbox : 0;
-      c.ring_mul = ring ? ((1 << 20) + p.nbox - 1) / p.nbox : 0;
-      EmuMap mc{src, nullptr, esz, W, H, sp, kCvBytes * nwl / esz, kCvBox};
+      c.tma_ld = tma_ok(src, sp, sbytes / esz, kCvBox);
+      EmuMap mc{src, nullptr, esz, W, H, sp, sbytes / esz, kCvBox};
       CUtensorMap tc{};
       memcpy(&tc, &mc, sizeof(mc));
       using VFn = bool (*)(const ColvArgs&, const CUtensorMap*, int, int, uint8_t*, uint64_t*);
-      VFn vf = ring ? (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 1, true> : colv_tile<uint8_t, 1, 1, true>)
-                                : (op == 0 ? colv_tile<uint16_t, 0, 1, true> : colv_tile<uint16_t, 1, 1, true>))
-               : nwl == 2 ? (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 2> : colv_tile<uint8_t, 1, 2>)
-                                    : (op == 0 ? colv_tile<uint16_t, 0, 2> : colv_tile<uint16_t, 1, 2>))
-                        : (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 1> : colv_tile<uint8_t, 1, 1>)
-                                    : (op == 0 ? colv_tile<uint16_t, 0, 1> : colv_tile<uint16_t, 1, 1>));
+      VFn vf = lb == 8 ? (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 8> : colv_tile<uint8_t, 1, 8>)
+                                   : (op == 0 ? colv_tile<uint16_t, 0, 8> : colv_tile<uint16_t, 1, 8>))
+                         : (esz == 1 ? (op == 0 ? colv_tile<uint8_t, 0, 4> : colv_tile<uint8_t, 1, 4>)
+                                     : (op == 0 ? colv_tile<uint16_t, 0, 4> : colv_tile<uint16_t, 1, 4>));
       const int nthr = 32 * c.wpc;
       for (int blk = 0; blk < cdiv(c.ntask, c.wpc); ++blk) {
         EmuCta cta;
         std::barrier<> bar(nthr);
         cta.bar = &bar;
-        std::barrier<>* wbv[8] = {};  // per warp (__syncwarp, __all_sync of the ring form)
+        std::barrier<>* wbv[8] = {};  // per warp (__syncwarp)
         for (int wi = 0; wi < c.wpc; ++wi) cta.wbar[wi] = wbv[wi] = new std::barrier<>(32);
         uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (p.smem + 127) / 128 * 128));
         cta.smem = sm;
@@ -597,8 +592,8 @@ int main() {
               emu_threadIdx = make_uint3(tid, 0, 0);
               const int warp = tid >> 5, lane = tid & 31, task = blk * c.wpc + warp;
               if (task >= c.ntask) return;
-              uint8_t* tile = sm + warp * colv_tile_bytes(c.nbox, nwl);
-              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.wpc * colv_tile_bytes(c.nbox, nwl)) + warp * c.nbox;
+              uint8_t* tile = sm + warp * colv_tile_bytes(c.nbox, lb);
+              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.wpc * colv_tile_bytes(c.nbox, lb)) + warp * c.nbox;
               if (c.tma_ld && lane == 0)
                 for (int b = 0; b < c.nbox; ++b) mbar_init(&bars[b], 1);
               // lanes wait on the barriers only after lane 0 initialised them
@@ -677,186 +672,7 @@ int main() {
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
     }
-    const int lw = L.wy > 64 ? 64 : L.wy > 32 ? 32 : 0;
-    const bool use_colw = kern == 6 && L.wx == 1 && lw && tma_ok(src, sp, kCvBytes / esz, kCvBox);
-    if (use_colw) {
-      const ColwPlan p = colw_plan(esz, W, H, L.wy, lw, (seed & 1) ? 152 : 3, kMaxSmemBytes, 16);
-      col_ty = p.nw;
-      ColwArgs c{};
-      c.src = src;
-      c.dst = dst;
-      c.sp = sp;
-      c.dp = dp;
-      c.W = W;
-      c.H = H;
-      c.w = L.wy;
-      c.a = L.ay;
-      c.nw = p.nw;
-      c.nbox = p.nbox;
-      c.ns = cdiv(W * esz, kCvBytes);
-      c.ntile = p.ntile;
-      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
-      c.err = &errword;
-      a.tma_ld = 1;
-      EmuMap mc{src, nullptr, esz, W, H, sp, kCvBytes / esz, kCvBox};
-      CUtensorMap tc{};
-      memcpy(&tc, &mc, sizeof(mc));
-      using WFn = bool (*)(const ColwArgs&, int, int, int, const uint8_t*, uint64_t*);
-      WFn wf = lw == 64 ? (esz == 1 ? (op == 0 ? colw_warp<uint8_t, 0, 64> : colw_warp<uint8_t, 1, 64>)
-                                    : (op == 0 ? colw_warp<uint16_t, 0, 64> : colw_warp<uint16_t, 1, 64>))
-                        : (esz == 1 ? (op == 0 ? colw_warp<uint8_t, 0, 32> : colw_warp<uint8_t, 1, 32>)
-                                    : (op == 0 ? colw_warp<uint16_t, 0, 32> : colw_warp<uint16_t, 1, 32>));
-      const int nthr = 32 * c.nw;
-      for (int t = 0; t < c.ntile; ++t) {
-        EmuCta cta;
-        std::barrier<> bar(nthr);
-        cta.bar = &bar;
-        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (p.smem + 127) / 128 * 128));
-        cta.smem = sm;
-        cta.smem_size = p.smem;
-        pool_run(
-            [&](int tid) {
-              g_cta = &cta;
-              emu_threadIdx = make_uint3(tid, 0, 0);
-              uint64_t* bars = reinterpret_cast<uint64_t*>(sm + c.nbox * kCvBoxBytes);
-              if (tid == 0) {
-                for (int b = 0; b < c.nbox; ++b) mbar_init(&bars[b], 1);
-                const int s = t % c.ns;
-                const int ysc = (t / c.ns) * (c.nw * lw) - c.a;
-                for (int b = 0; b < c.nbox; ++b) {
-                  mbar_arrive_expect_tx(&bars[b], static_cast<uint32_t>(kCvBoxBytes));
-                  tma_load_2d(sm + b * kCvBoxBytes, &tc, &bars[b], s * (kCvBytes / esz), ysc + b * kCvBox);
-                }
-              }
-              __syncthreads();
-              wf(c, t, tid >> 5, tid & 31, sm, bars);
-              if (tid == 0)
-                for (int b = 0; b < c.nbox; ++b) mbar_wait_bounded(&bars[b], 0);
-            },
-            nthr);
-        free(sm);
-        errors += cta.errors.load();
-        if (cta.errors.load() && first.empty()) first = cta.first_error;
-      }
-    }
-    const bool use_cols = kern == 7 && L.wx == 1 && L.wy >= 9 && L.wy <= kCsMaxW &&
-                          tma_ok(src, sp, 128 / esz, kCsBox);
-    if (use_cols) {
-      // the strip-streaming pass along y, planned as cols_launch does (forced
-      // band heights on even seeds; few SMs on odd seeds of 3)
-      const int sms = seed % 3 == 0 ? 3 : 152;
-      const ColsPlan p = cols_plan(esz, W, H, L.wy, kMaxSmemBytes, sms, (seed / 2) % 2 ? 28 : 64,
-                                   (seed & 1) ? 0 : 1 + static_cast<int>(seed % 300));
-      if (!p.ok) {
-        printf("FAIL case %d: no cols plan\n", cases);
-        ++failures;
-        continue;
-      }
-      col_ty = p.Lo;
-      ColsArgs c{};
-      c.dst = dst;
-      c.dp = dp;
-      c.W = W;
-      c.H = H;
-      c.w = L.wy;
-      c.a = L.ay;
-      c.Lo = p.Lo;
-      c.ns = cdiv(W * esz, 128);
-      c.ntask = p.ntask;
-      c.wpc = p.wpc;
-      c.rs = p.rs;
-      c.st_vec = (reinterpret_cast<uintptr_t>(dst) % 4 == 0) && (dp % 4 == 0);
-      c.err = &errword;
-      a.tma_ld = 1;
-      EmuMap mc{src, nullptr, esz, W, H, sp, 128 / esz, kCsBox};
-      CUtensorMap tc{};
-      memcpy(&tc, &mc, sizeof(mc));
-      using SFn = bool (*)(const ColsArgs&, const CUtensorMap*, int, int, uint8_t*);
-      SFn sf = esz == 1 ? (op == 0 ? cols_task<uint8_t, 0> : cols_task<uint8_t, 1>)
-                        : (op == 0 ? cols_task<uint16_t, 0> : cols_task<uint16_t, 1>);
-      const int nthr = 32 * c.wpc;
-      const int wsz = cols_warp_smem(c.rs);
-      for (int blk = 0; blk < cdiv(c.ntask, c.wpc); ++blk) {
-        EmuCta cta;
-        std::barrier<> bar(nthr);
-        cta.bar = &bar;
-        std::barrier<>* wb[8] = {};
-        for (int wi = 0; wi < c.wpc; ++wi) wb[wi] = new std::barrier<>(32);
-        for (int wi = 0; wi < c.wpc; ++wi) cta.wbar[wi] = wb[wi];
-        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (p.smem + 127) / 128 * 128));
-        cta.smem = sm;
-        cta.smem_size = p.smem;
-        pool_run(
-            [&](int tid) {
-              g_cta = &cta;
-              emu_threadIdx = make_uint3(tid, 0, 0);
-              const int warp = tid >> 5, lane = tid & 31, task = blk * c.wpc + warp;
-              // a warp whose task is past the end returns at once in the
-              // kernel; here its lanes still meet the warp barrier count
-              if (task >= c.ntask) return;
-              uint8_t* ws = sm + warp * wsz;
-              uint64_t* bars = cols_bars(ws, c.rs);
-              if (lane == 0)
-                for (int b = 0; b < 2 * kCsSlots; ++b) mbar_init(&bars[b], 1);
-              __syncwarp();
-              sf(c, &tc, task, lane, ws);
-            },
-            nthr);
-        for (int wi = 0; wi < c.wpc; ++wi) delete wb[wi];
-        free(sm);
-        errors += cta.errors.load();
-        if (cta.errors.load() && first.empty()) first = cta.first_error;
-      }
-    }
-    if (use_row) {
-      // the row kernel, launched as row_launch does
-      const bool blk = L.vhgw_row && L.wx >= 9;
-      RowArgs ra{};
-      ra.src = src;
-      ra.dst = dst;
-      ra.sp = sp;
-      ra.dp = dp;
-      ra.W = W;
-      ra.H = H;
-      ra.w = L.wx;
-      ra.a = L.ax;
-      ra.ntx = cdiv(W, rg.txp);
-      ra.nty = cdiv(H, rg.ty);
-      ra.blocked = blk;
-      ra.ld_vec = a.ld_vec;
-      ra.st_vec = (reinterpret_cast<uintptr_t>(dst) % (8 * esz) == 0) && (dp % (8 * esz) == 0);
-      ra.err = &errword;
-      ra.tma_ld = tma_ok(src, sp, 128 / esz, rg.ty);
-      EmuMap mr{src, nullptr, esz, W, H, sp, 128 / esz, rg.ty};
-      CUtensorMap tr{};
-      memcpy(&tr, &mr, sizeof(mr));
-      RowFnE rf = esz == 1 ? (op == 0 ? pick_row<uint8_t, 0>(blk) : pick_row<uint8_t, 1>(blk))
-                           : (op == 0 ? pick_row<uint16_t, 0>(blk) : pick_row<uint16_t, 1>(blk));
-      for (int t = 0; t < ra.ntx * ra.nty; ++t) {
-        EmuCta cta;
-        std::barrier<> bar(kRowThreads);
-        cta.bar = &bar;
-        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (rg.smem + 127) / 128 * 128));
-        cta.smem = sm;
-        cta.smem_size = rg.smem;
-        uint64_t mbar = 0;
-        pool_run(
-            [&](int tid) {
-              g_cta = &cta;
-              emu_threadIdx = make_uint3(tid, 0, 0);
-              uint32_t phase = 0;
-              if (tid == 0) mbar_init(&mbar, 1);
-              __syncthreads();
-              rf(ra, &tr, t, rg, sm, &mbar, phase);
-            },
-            kRowThreads);
-        free(sm);
-        errors += cta.errors.load();
-        if (cta.errors.load() && first.empty()) first = cta.first_error;
-      }
-      a.tma_ld = ra.tma_ld;
-    }
-    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv || use_colw || use_cols ? 0 : ncta); ++c) {
+    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv ? 0 : ncta); ++c) {
       const int bx = c % gx, by = c / gx;
       EmuCta cta;
       std::barrier<> bar(kThreads);
@@ -904,7 +720,7 @@ int main() {
     printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
            "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_cols ? 7 : use_colw ? 6 : use_rowv ? 5 : use_colv ? kern : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_rowv ? 5 : use_colv ? kern : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);

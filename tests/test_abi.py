@@ -119,12 +119,13 @@ def test_tuning_arguments():
     assert m.morph_set_xpass(0, 1) == 0 and m.morph_set_xpass(0, 0) == 0
     assert m.morph_set_column_kernel(3) == -10 and m.morph_set_column_kernel(-1) == 0
     assert m.morph_set_row_kernel(-3) == -10 and m.morph_set_row_kernel(-1) == 0
-    assert m.morph_set_colv(3, 0) == -10 and m.morph_set_colv(7, 0) == -10 and m.morph_set_colv(-1, -1) == -10
-    assert m.morph_set_colv(-1, 2000) == -10 and m.morph_set_colv(-1, 0) == 0
+    assert m.morph_set_colv(2, 0, 0) == -10 and m.morph_set_colv(-2, 0, 0) == -10
+    assert m.morph_set_colv(-1, -1, 0) == -10 and m.morph_set_colv(-1, 0, 2) == -10
+    assert m.morph_set_colv(-1, 2000, 0) == -10 and m.morph_set_colv(-1, 0, 0) == 0
     assert m.morph_set_rowv(5, 0) == -10 and m.morph_set_rowv(-1, -2) == -10
     assert m.morph_set_rowv(-1, 0) == 0
     assert m.morph_set_split_order(2) == -10 and m.morph_set_split_order(1) == 0
-    assert m.morph_set_split_pdl(2) == -10 and m.morph_set_split_pdl(1) == 0
+    assert m.morph_set_pdl(2) == -10 and m.morph_set_pdl(1) == 0 and m.morph_set_pdl(0) == 0
     assert m.morph_reset_tuning() == 0
 
 
