@@ -13,14 +13,19 @@ Reported (one JSON line on rank 0):
   roofline     the dominant kernel class: algorithmic bytes (read + write one
                image) / its mean CUDA-event launch time, against the measured
                HBM copy bandwidth
-  e2e          the same step through morph_apply_host with pinned host buffers
+  e2e          the same step through morph_apply_host_batch with pinned host buffers
                (host->device and device->host copies inside the timed region)
-  cpu_baseline the brute-force CPU oracle on a bounded sample of the step
+  cpu_baseline the brute-force CPU oracle on a bounded sample of the step,
+               and (separable) the oracle's separable van Herk/Gil-Werman
+               checker on the whole step, all cores and one core
   breakdown    per (dtype, window) class: mean us per call, Gpixel/s, GB/s
   batched      2000 uneven u8 images (sides 64..2048, windows 1..63): images/s
-               of one CUDA-graph persistent launch vs 2000 per-image calls
-  serving      Poisson request stream through the continuous-batching server
-               (4 GB admission budget): p50/p99 latency and throughput
+               of the batch plan (one CUDA graph) vs the 2000 per-image calls
+               captured in a CUDA graph
+  transposes   transpose_u8/u16 of a 4096x4096 image: Gpixel/s, HBM fraction
+  serving      Poisson request streams (1k, 2k, 5k, 10k, 20k req/s, 10 s each)
+               through the continuous-batching server (4 GB admission
+               budget): p50/p99 latency and throughput
 ``--impl reference`` times the CPU oracle alone (the reference arm).
 """
 from __future__ import annotations
@@ -198,6 +203,45 @@ def oracle_sample(images, target_ops: float = 1.5e9, seed: int = 7):
     return step_px / est_step_s / 1e9, oracle.num_threads(), spent, desc
 
 
+PAPER_ARM_CONTEXT = ("paper's own ratios, Samsung Exynos 5422 (ARM, one thread, gcc with NEON intrinsics), "
+                     "context only: NEON erosion/dilation 3x its scalar van Herk/Gil-Werman; NEON 8x8 u16 "
+                     "transpose 5.7x scalar (114 -> 20 ns), 16x16 u8 transpose 12x (565 -> 47 ns)")
+
+
+def separable_sample(images):
+    """The fair CPU speed baseline: the oracle's separable van Herk/Gil-Werman
+    checker (sections 5 and 5.1.1: two 1-D passes, O(1) operations per pixel
+    and pass, whatever the window) on the step's own full-size images.  All
+    cores: every call of the step; one core: one call per window class (u8
+    and u16 uniform erosion), extrapolated by pixel count.  Returns a dict
+    for cpu_baseline."""
+    import oracle
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    for (dt, kind, (wx, wy), op) in step_runs():
+        oracle.sep_vhgw(images[(dt, kind)], wx, wy, wx // 2, wy // 2, op)
+    t_all = time.perf_counter() - t0
+    step_px = len(step_runs()) * SIDE * SIDE
+    prev = oracle.set_threads(1)
+    try:
+        t1, n1 = 0.0, 0
+        for dt in DTYPES:
+            for (wx, wy) in WINDOWS:
+                t = time.perf_counter()
+                oracle.sep_vhgw(images[(dt, "uniform")], wx, wy, wx // 2, wy // 2, 0)
+                t1 += time.perf_counter() - t
+                n1 += 1
+    finally:
+        oracle.set_threads(prev)
+    one_core = n1 * SIDE * SIDE / t1 / 1e9
+    return {"value": round(step_px / t_all / 1e9, 5), "unit": UNIT, "cores": cores,
+            "kind": "oracle (separable van Herk/Gil-Werman checker)",
+            "single_core_value": round(one_core, 5), "seconds": round(t_all + t1, 1),
+            "sample": "all cores: the full step (32 calls at 4096x4096); one core: %d calls (each window "
+                      "class, u8 and u16, uniform image, erosion)" % n1,
+            "paper_context": PAPER_ARM_CONTEXT}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -351,9 +395,62 @@ def measure_composite(torch, morph, reps: int = 7) -> dict:
     return out
 
 
+def measure_transposes(torch, morph, peak: float, peak_kind: str, reps: int = 9) -> dict:
+    """transpose_u8 / transpose_u16 (section 4) of a 4096 x 4096 image, as
+    CUDA-graph replays of 8 calls over 8 input copies (inputs larger than L2
+    in total): us per call, Gpixel/s and the fraction of the HBM roofline
+    (algorithmic bytes: read and write the image once).  The output is
+    checked against torch's transpose first.  The paper's Table 1 figures are
+    quoted beside them as context."""
+    out = {}
+    for dt, tdt, fn, name in ((np.uint8, torch.uint8, morph.transpose_u8, "u8"),
+                              (np.uint16, torch.uint16, morph.transpose_u16, "u16")):
+        esz = np.dtype(dt).itemsize
+        base = torch.from_numpy(synth.uniform_image(SIDE, SIDE, dt, seed=970)).cuda()
+        srcs = [base] + [base.clone() for _ in range(7)]
+        dsts = [torch.empty_like(base) for _ in range(2)]
+        pitch = SIDE * esz
+
+        def calls():
+            sh = torch.cuda.current_stream().cuda_stream
+            for i in range(8):
+                rc = fn(srcs[i].data_ptr(), SIDE, SIDE, pitch, dsts[i % 2].data_ptr(), pitch, sh)
+                if rc != 0:
+                    raise morph.MorphError(fn.__name__, rc)
+        calls()
+        torch.cuda.synchronize()
+        if not torch.equal(dsts[1], srcs[7].t()):
+            raise RuntimeError("%s differs from torch's transpose" % fn.__name__)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            calls()
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3 / 8)
+        us = sorted(ts)[len(ts) // 2]
+        gbs = 2 * esz * SIDE * SIDE / (us * 1e-6) / 1e9
+        out["%s_4096x4096" % name] = {"us_per_call": round(us, 2), "gpix_s": round(SIDE * SIDE / us / 1e3, 1),
+                                      "gb_s": round(gbs, 1), "frac_of_%s_hbm" % peak_kind: round(gbs / peak, 3)}
+        del srcs, dsts, base, g
+    out["paper_context"] = ("Table 1, Samsung Exynos 5422 (ARM NEON): 8x8 u16 transpose 114 -> 20 ns "
+                            "(5.7x over scalar), 16x16 u8 transpose 565 -> 47 ns (12x); a single 8x8 or "
+                            "16x16 block, not a whole image")
+    return out
+
+
 def measure_batched(torch, morph, reps: int = 5) -> dict:
-    """2000 uneven u8 images: one CUDA-graph persistent launch against 2000
-    per-image morph_apply calls on one stream (inputs 2.2 GB, larger than L2).
+    """2000 uneven u8 images (inputs 2.2 GB, larger than L2): one batch plan
+    (its launches captured once in a CUDA graph) against the same 2000
+    images as per-image morph_apply calls, also captured once in a CUDA
+    graph, both replayed on one stream; plus morph_batch called directly.
     Rows are pitched to 128 bytes, as a pitched allocation lays them out.
     Identical output is checked on every image before timing."""
     import ctypes
@@ -375,13 +472,13 @@ def measure_batched(torch, morph, reps: int = 5) -> dict:
         d.wx, d.wy, d.anchor_x, d.anchor_y, d.op = sp.wx, sp.wy, sp.ax, sp.ay, sp.op
         d.dtype = morph.MORPH_U8
     stream = torch.cuda.current_stream()
-    sh = stream.cuda_stream
     plan = ctypes.c_void_p()
     rc = morph.morph_batch_plan_create(arr, len(specs), ctypes.byref(plan))
     if rc != 0:
         raise morph.MorphError("morph_batch_plan_create", rc)
 
-    def per_image():
+    def per_image_calls():
+        sh = torch.cuda.current_stream().cuda_stream
         for s, a, sp, pt in zip(srcs, alone, specs, pitches):
             rc = morph.morph_apply(s.data_ptr(), pt, a.data_ptr(), pt, sp.width, sp.height,
                                    morph.MORPH_U8, sp.op, sp.wx, sp.wy, sp.ax, sp.ay, sh)
@@ -389,12 +486,12 @@ def measure_batched(torch, morph, reps: int = 5) -> dict:
                 raise morph.MorphError("morph_apply", rc)
 
     def graph():
-        rc = morph.morph_batch_plan_launch(plan, sh)
+        rc = morph.morph_batch_plan_launch(plan, stream.cuda_stream)
         if rc != 0:
             raise morph.MorphError("morph_batch_plan_launch", rc)
 
     def batch_call():
-        rc = morph.morph_batch(arr, len(specs), sh)
+        rc = morph.morph_batch(arr, len(specs), stream.cuda_stream)
         if rc != 0:
             raise morph.MorphError("morph_batch", rc)
 
@@ -412,12 +509,18 @@ def measure_batched(torch, morph, reps: int = 5) -> dict:
 
     try:
         graph()
-        per_image()
+        per_image_calls()
         torch.cuda.synchronize()
         same = all(torch.equal(o[:, :sp.width], a[:, :sp.width]) for o, a, sp in zip(outs, alone, specs))
-        t_img = timed(per_image)
+        n0 = morph.morph_launch_count()
+        g_img = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_img):
+            per_image_calls()
+        per_image_launches = morph.morph_launch_count() - n0
+        t_img = timed(g_img.replay)
         t_graph = timed(graph)
         t_batch = timed(batch_call)
+        del g_img
     finally:
         morph.morph_batch_plan_destroy(plan)
     morph.check_device_error()
@@ -432,7 +535,10 @@ def measure_batched(torch, morph, reps: int = 5) -> dict:
             "graph_gpix_s": round(px / (t_graph * 1e-3) / 1e9, 2),
             "per_image_gpix_s": round(px / (t_img * 1e-3) / 1e9, 2),
             "graph_vs_per_image": round(t_img / t_graph, 3),
-            "ms": {"graph": round(t_graph, 3), "per_image": round(t_img, 3), "morph_batch": round(t_batch, 3)}}
+            "per_image_form": "the 2000 morph_apply calls captured once in a CUDA graph (%d kernel launches), "
+                              "replayed" % per_image_launches,
+            "ms": {"graph": round(t_graph, 3), "per_image_graph": round(t_img, 3),
+                   "morph_batch": round(t_batch, 3)}}
 
 
 def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0, host_copies: bool = False) -> list:
@@ -443,16 +549,18 @@ def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0, host_copies
     (HostCopyExecutor).  A short run at the same rate warms the pools first."""
     from paper_2002_09474_gb300 import serve
     if host_copies:
-        pool_img, pool_dev = serve.host_source_pool(torch, seed=6)
+        pool_img, pool_dev = serve.host_arena(torch, seed=6)
         ex = serve.HostCopyExecutor(n_streams=4)
+        make = serve.make_host_requests
     else:
         pool_img, pool_dev = serve.source_pool(torch, seed=6)
         ex = serve.GpuExecutor(n_streams=4)
+        make = serve.make_requests
     out = []
     for rate in rates:
-        warm = serve.make_requests(rate, min(0.5, duration_s), pool_img, pool_dev, seed=60)
+        warm = make(rate, min(0.5, duration_s), pool_img, pool_dev, seed=60)
         serve.Server(ex, budget_bytes=4 << 30).run(warm, timeout_s=300)
-        rs = serve.make_requests(rate, duration_s, pool_img, pool_dev, seed=6)
+        rs = make(rate, duration_s, pool_img, pool_dev, seed=6)
         st = serve.Server(ex, budget_bytes=4 << 30).run(rs, timeout_s=300)
         torch.cuda.synchronize()
         d = st.summary()
@@ -654,6 +762,7 @@ def run_gpu(args):
 
     extras = {}
     if not args.no_extras:
+        extras["transposes"] = measure_transposes(torch, morph, peak, peak_kind)
         extras["batched"] = measure_batched(torch, morph)
         extras["composite"] = measure_composite(torch, morph)
         extras["small_images"] = measure_small_images(torch, morph)
@@ -686,7 +795,8 @@ def run_gpu(args):
         if not args.no_cpu_baseline:
             v, cores, spent, desc = oracle_sample(host_imgs)
             line["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": cores,
-                                    "kind": "oracle", "sample": desc, "seconds": round(spent, 1)}
+                                    "kind": "oracle", "sample": desc, "seconds": round(spent, 1),
+                                    "separable": separable_sample(host_imgs)}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -703,9 +813,10 @@ def main(argv=None):
                     help="skip the CPU oracle sample (for profiler runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and serving measurements (for profiler runs)")
-    ap.add_argument("--serving-rates", type=float, nargs="+", default=[1000.0, 5000.0, 20000.0],
+    ap.add_argument("--serving-rates", type=float, nargs="+",
+                    default=[1000.0, 2000.0, 5000.0, 10000.0, 20000.0],
                     help="request rates of the serving measurement (req/s)")
-    ap.add_argument("--serving-seconds", type=float, default=2.0,
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of each serving run after warm-up")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":

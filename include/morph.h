@@ -21,7 +21,12 @@
  * and a pass along y with a 1 x wy element, each by the direct ("linear")
  * method of sections 5.1.2/5.2.2 for small windows or by van Herk/Gil-Werman
  * (sections 5.1.1/5.2.1) for large ones, switched at a crossover window
- * (section 5.3) measured on this GPU.  Both passes run fused in one kernel.
+ * (section 5.3) measured on this GPU.  Small windows (both passes direct) and
+ * small images run both passes fused in one kernel; a 1-D window above the
+ * crossover runs on the single-pass kernel of its axis; a 2-D window whose
+ * passes both take van Herk/Gil-Werman, on images of at least 2 Mpixels,
+ * runs as two launches, the pass along x into an intermediate image and the
+ * pass along y from it (see morph_set_split).
  *
  * Conventions for every entry point below
  *  - Image pointers are DEVICE pointers (cudaMalloc / torch CUDA memory)
@@ -39,9 +44,12 @@
  *    (the window is clipped to the image).
  *  - Single-image calls allocate nothing, except the two-launch form of
  *    2-D windows (see morph_set_split) and the transpose form of the pass
- *    along x (see morph_set_xpass), which take their intermediate images
- *    from the stream-ordered allocator (cudaMallocAsync on the call's
- *    stream; such calls can be captured into a CUDA graph).
+ *    along x (see morph_set_xpass), which take their intermediate image
+ *    per call from the stream-ordered allocator (cudaMallocAsync and
+ *    cudaFreeAsync on the call's stream: the device's default memory pool
+ *    serves it without a device synchronisation, calls on different
+ *    streams never share it, and such calls can be captured into a CUDA
+ *    graph).  morph_batch_noalloc allocates nothing at all.
  */
 #ifndef MORPH_H
 #define MORPH_H
@@ -137,6 +145,22 @@ enum { MORPH_OPEN = 0, MORPH_CLOSE = 1, MORPH_GRADIENT = 2 };
  */
 int morph_copy_2d(void *dst, size_t dst_pitch, const void *src, size_t src_pitch,
                   size_t width_bytes, int height, void *stream);
+
+/*
+ * n contiguous copies between host and device memory in the order of
+ * `stream`, one cudaMemcpyAsync each (direction from the pointers), issued in
+ * one call so that a caller moving many small images (the serving loop's
+ * micro-batches) pays one call instead of n.  No counterpart in the paper.
+ * Every entry is checked first (MORPH_ERR_NULL for a null pointer with a
+ * non-zero size, MORPH_ERR_ARG for n < 0); nothing is queued then.
+ * MORPH_ERR_CUDA when a copy cannot be queued (the earlier ones are).
+ */
+typedef struct {
+    void *dst;
+    const void *src;
+    uint64_t bytes;
+} morph_copy_desc;
+int morph_copy_batch(const morph_copy_desc *copies, int n, void *stream);
 int morph_composite(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
                     int width, int height, int dtype, int kind,
                     int wx, int wy, int anchor_x, int anchor_y, void *stream);
@@ -170,10 +194,18 @@ typedef struct {
 } morph_desc;
 
 /*
- * Runs all n images in one persistent kernel launch on `stream`.  The
- * descriptor array is on the host; the call copies it (and the derived tile
- * list) to device memory owned by the library, so descs may be reused as soon
- * as the call returns.  Asynchronous.
+ * Runs all n images on `stream` in at most six launches: images whose
+ * windows take the direct method (or too small for the single-pass kernels)
+ * in one persistent launch of the fused kernel; the passes along x of 1-D
+ * windows and of 2-D windows above the crossover in one batched launch of
+ * the pass-along-x kernel (the 2-D ones into intermediate images); the
+ * passes along y of 1-D windows and of those 2-D windows in batched
+ * launches of the pass-along-y kernel (one per tile-size class).  Each image
+ * gets exactly the bytes of its single call.  The descriptor array is on the
+ * host; the call copies it (and the derived records) to a stream-ordered
+ * device block (cudaMallocAsync on `stream`, which also holds the
+ * intermediates) through the library's pinned staging buffers, so descs may
+ * be reused as soon as the call returns.  Asynchronous.
  */
 int morph_batch(const morph_desc *descs_host, int n, void *stream);
 
@@ -195,10 +227,12 @@ int morph_apply_host_batch(const morph_desc *descs, int n, void *stream);
 
 /*
  * Graph form of morph_batch: plan_create validates the descriptors, builds the
- * tile list in device memory at fixed addresses and captures the persistent
- * launch in a CUDA graph; plan_launch replays it on `stream` (one
- * cudaGraphLaunch).  The image buffers must stay alive and at the same
- * addresses until plan_destroy.
+ * records (and the intermediates) in device memory at fixed addresses, which
+ * the plan owns, and captures the batch's launches in a CUDA graph;
+ * plan_launch replays it on `stream` (one cudaGraphLaunch).  The image
+ * buffers must stay alive and at the same addresses until plan_destroy.
+ * Replays of one plan must not overlap on the GPU (they share the
+ * intermediates and the tile counter).
  */
 int morph_batch_plan_create(const morph_desc *descs_host, int n, void **plan);
 int morph_batch_plan_launch(void *plan, void *stream);
@@ -209,19 +243,25 @@ int morph_batch_plan_destroy(void *plan);
  * may not allocate device memory at all -- code whose device memory is owned
  * by another allocator or memory pool, real-time loops where cudaMalloc's
  * implicit synchronisation is not allowed, or plug-in hosts that hand over
- * only pre-allocated image buffers.  It runs the same batched persistent
- * kernel as morph_batch, but its scratch (per-image records, tensor maps, the
- * tile counter) lives in a fixed array in the library's device memory image,
- * which every GPU that loads the library keeps until the process exits.  It
- * calls no cudaMalloc/cudaFree and no allocating routine.
+ * only pre-allocated image buffers.  It runs every image in the batched
+ * persistent fused kernel (morph_batch sends 2-D windows above the crossover
+ * through an intermediate image instead, which would need image-sized
+ * scratch); its scratch (per-image records, tensor maps, the tile counter)
+ * lives in a fixed array in the library's device memory image, which every
+ * GPU that loads the library keeps until the process exits.  It calls no
+ * cudaMalloc/cudaFree and no allocating routine.
  *
  * At most MORPH_NOALLOC_MAX_IMAGES images per call (MORPH_ERR_LIMIT beyond).
- * The first call on a device looks up the array's device address (the
- * set-up), so make that first call before any stream capture.  All calls
- * share the one array and its host-side staging copy: calls that overlap on
- * the GPU, or run concurrently from several host threads, race.  The counter
- * the kernel schedules tiles with is reset on every call.  Asynchronous on
- * `stream`; descs_host may be reused when the call returns.
+ * The first call on a device looks up the array's device address and
+ * page-locks the library's host-side staging copy of the records
+ * (cudaHostRegister of memory the library already holds; the set-up), so make
+ * that first call before any stream capture.  The records then reach the
+ * device by an asynchronous copy on `stream` that reads the staging copy when
+ * it runs; before rewriting the staging copy, a call waits until the
+ * previous call's copy has run.  All calls share the one array and the one
+ * staging copy: calls that overlap on the GPU, or run concurrently from
+ * several host threads, race.  The counter the kernel schedules tiles with
+ * is reset on every call.  descs_host may be reused when the call returns.
  */
 #define MORPH_NOALLOC_MAX_IMAGES 256
 int morph_batch_noalloc(const morph_desc *descs_host, int n, void *stream);
@@ -262,127 +302,10 @@ int morph_set_tuning(int dtype, int cross_row, int cross_col, int tile_cfg);
 int morph_reset_tuning(void);
 
 /*
- * Form of single-image calls with a 2-D window (section 5: the element is
- * separable, so erosion by wx x wy is erosion by 1 x wy followed by wx x 1).
- * mode -1 (default): two launches through an intermediate image the
- * library allocates stream-ordered for images of at least 2 Mpixels when
- * both passes take the van Herk/Gil-Werman method (both window sides above
- * the crossovers of morph_set_tuning; there the single-pass kernels were
- * measured faster than the fused kernel on the GB300), or when the fused
- * tile is so large that fewer than 3 CTAs fit on an SM; otherwise both
- * passes fused in one kernel.  0: always fused; 1:
- * always two launches.  The result never
- * changes.
+ * Switches that force a particular kernel, launch form or order (for tests,
+ * profiling and measurement) are declared in morph_tuning.h; none of them
+ * changes a result.
  */
-int morph_set_split(int mode);
-
-/*
- * Order of the two launches of that form (section 5: the passes commute):
- * 1 (default) the pass along x first, 0 the pass along y first.  On the
- * GB300 the pass along x first was measured 6-13% faster (at 4096^2, 15 x 15
- * to 127 x 127): the pass along y then reads the intermediate image while it
- * is still in L2.  The result never changes.  MORPH_ERR_ARG for another
- * order.
- */
-int morph_set_split_order(int order);
-
-/*
- * Whether the kernels of single-image calls are launched with programmatic
- * stream serialisation (1) or not (0).  With it a kernel may be scheduled
- * while the previous kernel on its stream drains: that kernel lets its
- * successor in once each of its CTAs has finished its work, and the
- * successor's CTAs wait (griddepcontrol.wait) for the predecessor to finish
- * and flush its memory before touching global memory, so the launch gap
- * between consecutive calls overlaps the previous call's tail.  On by
- * default: on the GB300 at 4096^2 it made single-stream calls 0-4% faster
- * and two streams of independent calls 2% faster.  A GPU scheduling
- * choice; the result never changes.  MORPH_ERR_ARG for another value.
- */
-int morph_set_pdl(int on);
-
-/*
- * Launch form of the fused kernel for single-image calls (no counterpart in
- * the paper: a GPU scheduling choice).  mode 1: a persistent grid (resident
- * CTAs x SMs) whose CTAs walk the tiles in turn, with two input buffers per
- * CTA so that the TMA load of a CTA's next tile overlaps the computation of
- * its current one; 0: one CTA per tile; -1 (default): the persistent form
- * when the image has at least two tiles per resident CTA and its doubled
- * input buffer fits in shared memory.  Images whose rows are not 16-byte
- * aligned always take one CTA per tile.  The result never changes.
- * Returns MORPH_ERR_ARG for another mode.
- */
-int morph_set_pipeline(int mode);
-
-/*
- * Kernel for single-image calls whose window is 1 x wy (wy > 1), including
- * the first launch of the two-launch form: mode -1 (default) or 1: the
- * column kernel (one pass along y per CTA tile 128 bytes wide and as tall as
- * fills whole waves of the GPU; outputs stored from registers); 0: the
- * fused two-pass tile kernel.  The result never changes.  MORPH_ERR_ARG for
- * another mode.
- */
-int morph_set_column_kernel(int mode);
-
-/*
- * Kernel of the pass along y (1 x wy windows, and the first launch of the
- * two-launch form): van Herk/Gil-Werman with blocks of wy rows (section
- * 5.1.1), one warp per strip of 32 lanes x lane_bytes bytes and `rows`
- * output rows, the block suffix kept in place of the input rows it
- * replaces.  mode 1: this kernel for every wy >= 2 whose warp tile fits in
- * shared memory; -1 (default): wherever the van Herk/Gil-Werman method is
- * chosen (wy above the crossover of section 5.3; measured faster than the
- * column kernel there); 0: never (the column kernel of
- * morph_set_column_kernel instead).  rows: output rows per warp tile, 1 to
- * 1024, or 0 for the measured default (a multiple of wy filling one or two
- * 32-row input boxes below 32 rows; else wy or 2 wy up to 256, or 64, with
- * 64 or 32 where those tiles would leave the GPU's SMs short of warps).
- * lane_bytes: 4 (strips 128 bytes wide), 8 (256 bytes, two independent scan
- * chains per lane), or 0 for the built-in rule.  The result never changes.  MORPH_ERR_ARG for another
- * mode, rows or lane_bytes.
- */
-int morph_set_colv(int mode, int rows, int lane_bytes);
-
-/*
- * Kernel of the pass along x (wx x 1 windows, and the second launch of the
- * two-launch form): van Herk/Gil-Werman with blocks of 8 pixels (section
- * 5.1.1's decomposition; the whole blocks inside a window folded from their
- * totals), one warp per 2 (default), 4 or 8 rows and a segment of `seg`
- * output columns, each lane's block transposed in registers (section 4) so
- * that one packed min/max handles 2 rows.  Accepts 9 <= wx <= 256 when the
- * source rows are aligned to 8 bytes (u8) or 16 bytes (u16).  mode 1: this
- * kernel wherever it accepts the call; 2, 3 and 4: the same with 8, 4 and 2
- * rows per warp; -1 (default): wherever the van Herk/Gil-Werman method is
- * chosen (measured faster than the row kernel of morph_set_row_kernel
- * there); 0: never.  seg: output columns per warp task,
- * rounded up to a multiple of 256, or 0 for the shortest segment whose
- * tasks fit in one wave of resident warps.  The result never changes.
- * MORPH_ERR_ARG for another mode or seg.
- */
-int morph_set_rowv(int mode, int seg);
-
-/*
- * Kernel for single-image calls whose window is wx x 1 (wx > 1), including
- * the second launch of the two-launch form: mode -1 (default) or 1: the row
- * kernel (tiles 256 bytes wide; 8 x 8-pixel blocks transposed once in
- * registers into a column-major shared-memory copy, the pass along x run on
- * it, outputs transposed back and stored from registers) when its tile fits
- * in shared memory; 0: the fused two-pass tile kernel.  The result never
- * changes.  MORPH_ERR_ARG for another mode.
- */
-int morph_set_row_kernel(int mode);
-
-/*
- * Form of the pass along x for dtype (MORPH_U8/MORPH_U16).  mode 0 (default):
- * inside the fused kernel, whose 8x8-pixel register transposes turn it into a
- * pass along y (section 1's "transpose, pass, transpose" without leaving the
- * chip); 1: the paper's baseline form of section 5.2.1 through HBM --
- * transpose_u8/u16 into a scratch image, the pass along y, transpose back --
- * with a 2-D window's 1 x wy pass run first.  Scratch images come from the
- * stream-ordered allocator.  morph_autotune measures both and keeps the
- * faster.  The result never changes.  MORPH_ERR_DTYPE / MORPH_ERR_ARG for a
- * bad dtype or mode.
- */
-int morph_set_xpass(int dtype, int mode);
 
 /* Text for a morph_status value (static storage). */
 const char *morph_status_string(int status);

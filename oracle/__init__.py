@@ -73,9 +73,10 @@ def _load():
         lib.oracle_line_wedge.argtypes = [vp, i64, i32, i32, i32, i32, vp]
         lib.oracle_transpose.argtypes = [vp, i32, i32, i32, i64, vp, i64]
         lib.oracle_num_threads.argtypes = []
+        lib.oracle_set_threads.argtypes = [i32]
         for f in (lib.oracle_morph, lib.oracle_morph_points, lib.oracle_sep_vhgw,
                   lib.oracle_line_wedge, lib.oracle_transpose,
-                  lib.oracle_num_threads):
+                  lib.oracle_num_threads, lib.oracle_set_threads):
             f.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -177,6 +178,11 @@ def transpose(src: np.ndarray) -> np.ndarray:
 def num_threads() -> int:
     """OpenMP threads the oracle's parallel loops use."""
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> int:
+    """Sets the OpenMP threads of later calls; returns the previous count."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def reflect_anchor(w: int, a: int) -> int:

@@ -324,3 +324,17 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Sets the OpenMP threads of later calls (n >= 1); for timing the oracle on
+ * one core against all.  Returns the previous count. */
+int oracle_set_threads(int n)
+{
+    const int prev = oracle_num_threads();
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return prev;
+}

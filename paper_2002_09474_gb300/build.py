@@ -1,4 +1,5 @@
-"""Builds libmorph.so (the C-ABI library of include/morph.h) in-tree with
+"""Builds libmorph.so (the C-ABI library of include/morph.h and
+include/morph_tuning.h) in-tree with
 nvcc for sm_103a.  Translation units compile in parallel; cudart is linked
 statically, so the library depends on nothing but the CUDA driver."""
 from __future__ import annotations
@@ -25,7 +26,7 @@ def sources() -> list[str]:
 
 def _deps() -> list[str]:
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + \
-        [os.path.join(ROOT, "include", "morph.h"), __file__]
+        [os.path.join(ROOT, "include", h) for h in ("morph.h", "morph_tuning.h")] + [__file__]
 
 
 def up_to_date() -> bool:

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/morph.h"
+#include "../../include/morph_tuning.h"
 #include "batch.h"
 #include "morph_internal.h"
 #include "plan.h"
@@ -311,66 +312,73 @@ void release_pipelines() {
   cudaSetDevice(cur);
 }
 
-// Validates and plans every descriptor of a batch.  Besides the single-image
-// checks, no destination may overlap any other image's source or
-// destination (images of one launch run concurrently).
 int plan_batch(const morph_desc* d, int n, std::vector<BatchImageIn>* out) {
   if (!d) return MORPH_ERR_NULL;
   if (n < 1) return MORPH_ERR_ARG;
   out->resize(n);
-  struct Range {
-    uintptr_t lo, hi;
-    int img, is_dst;
-  };
-  std::vector<Range> ranges;
-  ranges.reserve(2 * static_cast<size_t>(n));
-  for (int i = 0; i < n; ++i) {
-    const morph_desc& e = d[i];
-    if (e.src_pitch < 0 || e.dst_pitch < 0) return MORPH_ERR_PITCH;
-    const int rc = validate(e.src, static_cast<size_t>(e.src_pitch), e.dst, static_cast<size_t>(e.dst_pitch),
-                            e.width, e.height, e.dtype, e.op, e.wx, e.wy, e.anchor_x, e.anchor_y);
-    if (rc != MORPH_OK) return rc;
-    FusedLaunch& L = (*out)[i].L;
-    L = FusedLaunch();
-    L.esz = esz_of(e.dtype);
-    L.op = e.op;
-    L.src = e.src;
-    L.dst = e.dst;
-    L.sp = e.src_pitch;
-    L.dp = e.dst_pitch;
-    L.W = e.width;
-    L.H = e.height;
-    clip_window(e.width, e.wx, e.anchor_x, &L.wx, &L.ax);
-    clip_window(e.height, e.wy, e.anchor_y, &L.wy, &L.ay);
-    if (!plan_single(&L)) return MORPH_ERR_WINDOW;
-    const uintptr_t s0 = reinterpret_cast<uintptr_t>(e.src), d0 = reinterpret_cast<uintptr_t>(e.dst);
-    const uintptr_t row = static_cast<uintptr_t>(e.width) * L.esz;
-    ranges.push_back({s0, s0 + static_cast<uintptr_t>(e.height - 1) * e.src_pitch + row, i, 0});
-    ranges.push_back({d0, d0 + static_cast<uintptr_t>(e.height - 1) * e.dst_pitch + row, i, 1});
-  }
-  std::sort(ranges.begin(), ranges.end(), [](const Range& a, const Range& b) { return a.lo < b.lo; });
-  // sweep: a destination may not overlap any range that starts before it ends
-  uintptr_t reach_any = 0, reach_dst = 0;
-  for (const Range& r : ranges) {
-    if (r.lo < reach_dst) return MORPH_ERR_ALIAS;            // overlaps an earlier destination
-    if (r.is_dst && r.lo < reach_any) return MORPH_ERR_ALIAS;  // a destination overlaps anything earlier
-    reach_any = std::max(reach_any, r.hi);
-    if (r.is_dst) reach_dst = std::max(reach_dst, r.hi);
-  }
-  return MORPH_OK;
+  std::vector<BatchRange> ranges(2 * static_cast<size_t>(n));
+  return plan_batch_into(d, n, out->data(), ranges.data());
 }
 
-// Device layout of a batch: tensor maps (64-byte aligned), image records.
-struct BatchDev {
-  size_t maps_off, imgs_off, counter_off, bytes;
+// Pinned host staging of batch records, per device: a few slots used in
+// turn, each with the event of the copy that last read it, so records travel
+// by truly asynchronous copies (a copy from pageable memory would wait for
+// the stream's earlier work and stall the caller).  A slot is reused once
+// its previous copy has run; it grows on demand.
+constexpr int kStageSlots = 8;
+struct RecordStage {
+  std::mutex mu;
+  void* buf[kStageSlots] = {};
+  size_t cap[kStageSlots] = {};
+  cudaEvent_t ev[kStageSlots] = {};
+  int next = 0;
 };
-BatchDev batch_dev_layout(const BatchHost& h) {
-  BatchDev L;
-  L.maps_off = 0;
-  L.imgs_off = (h.maps.size() * sizeof(CUtensorMap) + 255) / 256 * 256;
-  L.counter_off = (L.imgs_off + h.imgs.size() * sizeof(BatchImage) + 255) / 256 * 256;
-  L.bytes = L.counter_off + 256;
-  return L;
+RecordStage g_rstage[kMaxDevices];
+
+// Copies `bytes` of host records at `src` to device `dst` on `st` through
+// the pinned staging slots.
+cudaError_t stage_records(void* dst, const void* const* parts, const size_t* sizes, const size_t* offs, int nparts,
+                          size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  RecordStage& rs = g_rstage[dev];
+  std::lock_guard<std::mutex> lock(rs.mu);
+  const int k = rs.next;
+  rs.next = (k + 1) % kStageSlots;
+  if (!rs.ev[k]) {
+    e = cudaEventCreateWithFlags(&rs.ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  } else {
+    e = cudaEventSynchronize(rs.ev[k]);  // the slot's previous copy has run
+    if (e != cudaSuccess) return e;
+  }
+  if (rs.cap[k] < bytes) {
+    if (rs.buf[k]) cudaFreeHost(rs.buf[k]);
+    rs.buf[k] = nullptr;
+    rs.cap[k] = 0;
+    const size_t want = bytes < (1u << 16) ? (1u << 16) : bytes * 2;
+    e = cudaHostAlloc(&rs.buf[k], want, cudaHostAllocDefault);
+    if (e != cudaSuccess) return e;
+    rs.cap[k] = want;
+  }
+  uint8_t* h = static_cast<uint8_t*>(rs.buf[k]);
+  for (int i = 0; i < nparts; ++i)
+    if (sizes[i]) memcpy(h + offs[i], parts[i], sizes[i]);
+  e = cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(rs.ev[k], st);
+}
+
+// The records of a prepared batch into its device block (layout L) on `st`.
+cudaError_t upload_batch(const BatchHost& h, const BatchDev& L, uint8_t* base, cudaStream_t st) {
+  const void* parts[5] = {h.maps.data(), h.imgs.data(), h.rows.data(), h.col_maps.data(), h.cols.data()};
+  const size_t sizes[5] = {h.maps.size() * sizeof(CUtensorMap), h.imgs.size() * sizeof(BatchImage),
+                           h.rows.size() * sizeof(BatchRowv), h.col_maps.size() * sizeof(CUtensorMap),
+                           h.cols.size() * sizeof(BatchColv)};
+  const size_t offs[5] = {L.maps_off, L.imgs_off, L.rows_off, L.col_maps_off, L.cols_off};
+  return stage_records(base, parts, sizes, offs, 5, L.inter_off, st);
 }
 
 struct BatchPlan {
@@ -434,6 +442,21 @@ int morph_copy_2d(void* dst, size_t dst_pitch, const void* src, size_t src_pitch
                            static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? MORPH_OK
              : MORPH_ERR_CUDA;
+}
+
+int morph_copy_batch(const morph_copy_desc* copies, int n, void* stream) {
+  if (n < 0) return MORPH_ERR_ARG;
+  if (n > 0 && !copies) return MORPH_ERR_NULL;
+  for (int i = 0; i < n; ++i)
+    if (copies[i].bytes && (!copies[i].dst || !copies[i].src)) return MORPH_ERR_NULL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n; ++i) {
+    if (!copies[i].bytes) continue;
+    if (cudaMemcpyAsync(copies[i].dst, copies[i].src, static_cast<size_t>(copies[i].bytes), cudaMemcpyDefault, st) !=
+        cudaSuccess)
+      return MORPH_ERR_CUDA;
+  }
+  return MORPH_OK;
 }
 
 int morph_selftest_wait_timeout(void* stream) {
@@ -503,20 +526,15 @@ int morph_batch(const morph_desc* descs_host, int n, void* stream) {
   if (batch_configure(&h) != cudaSuccess) return MORPH_ERR_CUDA;
   const BatchDev L = batch_dev_layout(h);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // Stream-ordered scratch: allocated and freed in the stream's order, so
-  // concurrent batches on different streams never share it.
+  // Stream-ordered scratch (records, then the 2-D images' intermediates):
+  // allocated and freed in the stream's order, so concurrent batches on
+  // different streams never share it.
   void* dmem = nullptr;
   if (cudaMallocAsync(&dmem, L.bytes, st) != cudaSuccess) return MORPH_ERR_NOMEM;
   uint8_t* base = static_cast<uint8_t*>(dmem);
-  cudaError_t e = cudaMemcpyAsync(base + L.maps_off, h.maps.data(), h.maps.size() * sizeof(CUtensorMap),
-                                  cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + L.imgs_off, h.imgs.data(), h.imgs.size() * sizeof(BatchImage),
-                        cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = batch_enqueue(h, reinterpret_cast<const BatchImage*>(base + L.imgs_off),
-                      reinterpret_cast<const CUtensorMap*>(base + L.maps_off),
-                      reinterpret_cast<int*>(base + L.counter_off), st);
+  batch_bind_intermediates(base + L.inter_off, &h);
+  cudaError_t e = upload_batch(h, L, base, st);
+  if (e == cudaSuccess) e = batch_enqueue(h, base, L, st);
   cudaFreeAsync(dmem, st);
   return e == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
 }
@@ -543,19 +561,15 @@ int morph_batch_plan_create(const morph_desc* descs_host, int n, void** plan) {
     return MORPH_ERR_NOMEM;
   }
   uint8_t* base = static_cast<uint8_t*>(p->dmem);
-  cudaError_t e = cudaMemcpy(base + L.maps_off, p->host.maps.data(), p->host.maps.size() * sizeof(CUtensorMap),
-                             cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(base + L.imgs_off, p->host.imgs.data(), p->host.imgs.size() * sizeof(BatchImage),
-                   cudaMemcpyHostToDevice);
-  // Capture the counter reset and the persistent kernel into a graph.
+  batch_bind_intermediates(base + L.inter_off, &p->host);
+  // Records at fixed addresses, then the launches captured into a graph.
   cudaStream_t cs = nullptr;
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = upload_batch(p->host, L, base, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t le = batch_enqueue(p->host, reinterpret_cast<const BatchImage*>(base + L.imgs_off),
-                                   reinterpret_cast<const CUtensorMap*>(base + L.maps_off),
-                                   reinterpret_cast<int*>(base + L.counter_off), cs);
+    cudaError_t le = batch_enqueue(p->host, base, L, cs);
     e = cudaStreamEndCapture(cs, &p->graph);
     if (le != cudaSuccess) e = le;
   }

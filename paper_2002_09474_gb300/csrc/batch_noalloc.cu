@@ -12,10 +12,6 @@
 
 namespace morph {
 
-int validate(const void* src, size_t sp, const void* dst, size_t dp, int W, int H, int dtype, int op, int wx,
-             int wy, int ax, int ay);
-void clip_window(int n, int w, int a, int* w_out, int* a_out);
-
 namespace {
 
 constexpr int kMaxImages = MORPH_NOALLOC_MAX_IMAGES;
@@ -32,70 +28,43 @@ struct NoallocScratch {
 // symbol; its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
 
-// Host-side working storage of one call (shared by all calls).
-NoallocScratch g_stage;
+// Host-side working storage of one call (shared by all calls).  The staged
+// records are page-locked once per process (cudaHostRegister pins memory the
+// library already has; it allocates none), so their copy to the device is
+// truly asynchronous; a call waits, before overwriting them, for the copy of
+// the previous call to have run (g_stage_done).
+alignas(4096) NoallocScratch g_stage;
 BatchImageIn g_in[kMaxImages];
-struct Range {
-  uintptr_t lo, hi;
-  int is_dst;
-};
-Range g_ranges[2 * kMaxImages];
+const FusedLaunch* g_lp[kMaxImages];
+BatchRange g_ranges[2 * kMaxImages];
+bool g_stage_pinned = false;
+cudaEvent_t g_stage_done[64] = {};
+int g_stage_dev = -1;  // device of the last call's copy (its event)
 
 // Device address of g_noalloc_scratch per device, looked up once per device
-// with that device current.
+// with that device current; the staging copy is page-locked on the first
+// call, and each device's event created on its first call.
 void* g_scratch_ptr[64] = {};
 std::mutex g_setup_mu;
 
-void* scratch_for_current_device() {
+void* scratch_for_current_device(int* dev_out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    if (cudaEventCreateWithFlags(&g_stage_done[dev], cudaEventDisableTiming) != cudaSuccess) return nullptr;
     g_scratch_ptr[dev] = ptr;
   }
+  if (!g_stage_pinned) {
+    // a failure leaves the staging pageable: the copy then waits for the
+    // stream's earlier work, but the results are the same
+    g_stage_pinned = cudaHostRegister(&g_stage, sizeof(g_stage), cudaHostRegisterDefault) == cudaSuccess;
+    if (!g_stage_pinned) cudaGetLastError();
+  }
+  *dev_out = dev;
   return g_scratch_ptr[dev];
-}
-
-int esz_code(int dtype) { return dtype == MORPH_U8 ? 1 : dtype == MORPH_U16 ? 2 : 0; }
-
-// Same checks and plan as the allocating morph_batch, on fixed arrays.
-int plan_fixed(const morph_desc* d, int n) {
-  for (int i = 0; i < n; ++i) {
-    const morph_desc& e = d[i];
-    if (e.src_pitch < 0 || e.dst_pitch < 0) return MORPH_ERR_PITCH;
-    const int rc = validate(e.src, static_cast<size_t>(e.src_pitch), e.dst, static_cast<size_t>(e.dst_pitch),
-                            e.width, e.height, e.dtype, e.op, e.wx, e.wy, e.anchor_x, e.anchor_y);
-    if (rc != MORPH_OK) return rc;
-    FusedLaunch& L = g_in[i].L;
-    L = FusedLaunch();
-    L.esz = esz_code(e.dtype);
-    L.op = e.op;
-    L.src = e.src;
-    L.dst = e.dst;
-    L.sp = e.src_pitch;
-    L.dp = e.dst_pitch;
-    L.W = e.width;
-    L.H = e.height;
-    clip_window(e.width, e.wx, e.anchor_x, &L.wx, &L.ax);
-    clip_window(e.height, e.wy, e.anchor_y, &L.wy, &L.ay);
-    if (!plan_single(&L)) return MORPH_ERR_WINDOW;
-    const uintptr_t s0 = reinterpret_cast<uintptr_t>(e.src), d0 = reinterpret_cast<uintptr_t>(e.dst);
-    const uintptr_t row = static_cast<uintptr_t>(e.width) * L.esz;
-    g_ranges[2 * i] = {s0, s0 + static_cast<uintptr_t>(e.height - 1) * e.src_pitch + row, 0};
-    g_ranges[2 * i + 1] = {d0, d0 + static_cast<uintptr_t>(e.height - 1) * e.dst_pitch + row, 1};
-  }
-  std::sort(g_ranges, g_ranges + 2 * n, [](const Range& a, const Range& b) { return a.lo < b.lo; });
-  uintptr_t reach_any = 0, reach_dst = 0;
-  for (int i = 0; i < 2 * n; ++i) {
-    const Range& r = g_ranges[i];
-    if (r.lo < reach_dst) return MORPH_ERR_ALIAS;
-    if (r.is_dst && r.lo < reach_any) return MORPH_ERR_ALIAS;
-    reach_any = std::max(reach_any, r.hi);
-    if (r.is_dst) reach_dst = std::max(reach_dst, r.hi);
-  }
-  return MORPH_OK;
 }
 
 }  // namespace
@@ -107,58 +76,29 @@ extern "C" int morph_batch_noalloc(const morph_desc* descs_host, int n, void* st
   if (!descs_host) return MORPH_ERR_NULL;
   if (n < 1) return MORPH_ERR_ARG;
   if (n > kMaxImages) return MORPH_ERR_LIMIT;
-  uint8_t* scratch = static_cast<uint8_t*>(scratch_for_current_device());
+  int dev = 0;
+  uint8_t* scratch = static_cast<uint8_t*>(scratch_for_current_device(&dev));
   if (!scratch) return MORPH_ERR_CUDA;
-  int rc = plan_fixed(descs_host, n);
+  // the same checks and plan as morph_batch, into the fixed arrays
+  int rc = plan_batch_into(descs_host, n, g_in, g_ranges);
   if (rc != MORPH_OK) return rc;
-  // tile shape shared by the batch: the cheapest that fits every image
-  static const int cfgs[] = {kTile128x64, kTile64x64, kTile32x32};
-  int cfg = -1, smem = 0;
-  double best = 1e300;
-  for (int c : cfgs) {
-    double cost = 0;
-    int need = 0;
-    bool fits = true;
-    for (int i = 0; i < n && fits; ++i) {
-      FusedLaunch L = g_in[i].L;
-      L.cfg = c;
-      const int b = fused_smem_bytes(L);
-      if (b <= 0 || b > kMaxSmemBytes) fits = false;
-      need = need > b ? need : b;
-      cost += tile_cost(L, c);
-    }
-    if (fits && cost < best) {
-      best = cost;
-      cfg = c;
-      smem = need;
-    }
-  }
-  if (cfg < 0) return MORPH_ERR_WINDOW;
-  const int TX = tile_tx(cfg), TY = tile_ty(cfg);
-  int tiles = 0;
-  for (int i = 0; i < n; ++i) {
-    const FusedLaunch& L = g_in[i].L;
-    BatchImage& b = g_stage.imgs[i];
-    memset(&b, 0, sizeof(b));
-    b.esz = L.esz;
-    b.op = L.op;
-    b.g = make_geom(L.esz, TX, TY, L.wx, L.wy, L.ax, L.vhgw_col, L.vhgw_row);
-    fill_img_args(L, b.g, TX, TY, &b.a, &g_stage.maps[2 * i], &g_stage.maps[2 * i + 1]);
-    b.tiles_x = cdiv(L.W, TX);
-    b.tile0 = tiles;
-    tiles += b.tiles_x * cdiv(L.H, TY);
-  }
-  BatchHost h;  // default-constructed: its containers stay empty (no allocation)
-  h.cfg = cfg;
-  h.smem = smem;
-  h.ntiles = tiles;
-  if (batch_configure(&h) != cudaSuccess) return MORPH_ERR_CUDA;
-  NoallocScratch* dev = reinterpret_cast<NoallocScratch*>(scratch);
+  // the previous call's copy of g_stage must have run before it is rewritten
+  if (g_stage_dev >= 0 && cudaEventSynchronize(g_stage_done[g_stage_dev]) != cudaSuccess) return MORPH_ERR_CUDA;
+  // every image in the fused persistent kernel (no intermediate images: the
+  // single-pass kernels' two-launch form would need scratch of image size)
+  for (int i = 0; i < n; ++i) g_lp[i] = &g_in[i].L;
+  int cfg = -1, smem = 0, tiles = 0;
+  if (batch_prepare_fused(g_lp, n, &cfg, &smem, &tiles, g_stage.imgs, g_stage.maps) != 0) return MORPH_ERR_WINDOW;
+  int grid = 0;
+  int* err = nullptr;
+  if (batch_fused_grid(cfg, smem, tiles, &grid, &err) != cudaSuccess) return MORPH_ERR_CUDA;
+  NoallocScratch* d = reinterpret_cast<NoallocScratch*>(scratch);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(dev->maps, g_stage.maps, sizeof(CUtensorMap) * 2 * n, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(d->maps, g_stage.maps, sizeof(CUtensorMap) * 2 * n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(dev->imgs, g_stage.imgs, sizeof(BatchImage) * n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = batch_enqueue_raw(cfg, smem, h.grid, h.err, n, tiles, dev->imgs, dev->maps, &dev->counter, st);
+    e = cudaMemcpyAsync(d->imgs, g_stage.imgs, sizeof(BatchImage) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(g_stage_done[dev], st);
+  if (e == cudaSuccess) g_stage_dev = dev;
+  if (e == cudaSuccess) e = batch_enqueue_raw(cfg, smem, grid, err, n, tiles, d->imgs, d->maps, &d->counter, st);
   return e == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
 }

@@ -1,4 +1,5 @@
-"""Python binding of the C ABI in include/morph.h (ctypes).
+"""Python binding of the C ABI in include/morph.h and include/morph_tuning.h
+(ctypes).
 
 Argument marshalling only: every function forwards to the entry point of the
 same name in libmorph.so, and every pixel is computed by that library's CUDA
@@ -17,7 +18,7 @@ import re
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmorph.so")
-HEADER = os.path.join(os.path.dirname(_PKG), "include", "morph.h")
+HEADERS = [os.path.join(os.path.dirname(_PKG), "include", h) for h in ("morph.h", "morph_tuning.h")]
 
 MORPH_OK = 0
 MORPH_U8, MORPH_U16 = 0, 1
@@ -45,6 +46,11 @@ class MorphDesc(ctypes.Structure):
                 ("pad", ctypes.c_uint8 * 2)]
 
 
+class MorphCopyDesc(ctypes.Structure):
+    """morph_copy_desc of include/morph.h (one contiguous copy)."""
+    _fields_ = [("dst", ctypes.c_void_p), ("src", ctypes.c_void_p), ("bytes", ctypes.c_uint64)]
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -64,6 +70,7 @@ _SIGS = {
     "morph_apply": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_composite": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_copy_2d": [_vp, _sz, _vp, _sz, _sz, _i32, _vp],
+    "morph_copy_batch": [ctypes.POINTER(MorphCopyDesc), _i32, _vp],
     "morph_selftest_wait_timeout": [_vp],
     "morph_apply_host": [_vp, _sz, _vp, _sz, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32, _vp],
     "morph_release_staging": [],
@@ -101,8 +108,8 @@ for _name, _args in _SIGS.items():
 
 
 def declared_functions() -> list[str]:
-    """Names of the functions include/morph.h declares."""
-    text = open(HEADER).read()
+    """Names of the functions the headers in include/ declare."""
+    text = "\n".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:long\s+long|[a-z_0-9]+)\s*\*?\s*([a-z_0-9]+)\s*\(",
                                  text, flags=re.M)))
@@ -158,6 +165,10 @@ def morph_selftest_wait_timeout(stream=0):
 
 def morph_copy_2d(dst, dst_pitch, src, src_pitch, width_bytes, height, stream=0):
     return _lib.morph_copy_2d(dst, dst_pitch, src, src_pitch, width_bytes, height, stream)
+
+
+def morph_copy_batch(copies, n, stream=0):
+    return _lib.morph_copy_batch(copies, n, stream)
 
 
 def morph_apply_host(src, src_pitch, dst, dst_pitch, width, height, dtype, op, wx, wy,

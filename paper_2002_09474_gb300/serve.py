@@ -13,11 +13,13 @@ completion.
 With ``GpuExecutor`` inputs are pre-staged in device memory (requests point
 into a resident source pool), so host-to-device copies are not part of the
 latency; the budget still charges each request its input bytes as if
-staged.  With ``HostCopyExecutor`` requests hold pinned HOST images: each
-micro-batch's stream copies its inputs to device buffers, runs the batch and
-copies the results back to pinned host buffers, so the latency (arrival to
-the results in host memory) includes both copies, and the copies of one
-micro-batch overlap the filtering of others on the other streams.
+staged, its output buffer and the library's scratch (an intermediate image
+for a 2-D window).  With ``HostCopyExecutor`` requests hold pinned HOST
+images (dense, as a client's own buffer would be): each micro-batch's stream
+copies its inputs to device buffers, runs the batch and copies the results
+back to pinned host buffers, so the latency (arrival to the results in host
+memory) includes both copies, and the copies of one micro-batch overlap the
+filtering of others on the other streams.
 
 The scheduling logic is independent of CUDA: it talks to an executor
 (``GpuExecutor`` here; tests use a host-only fake).
@@ -45,6 +47,7 @@ class ServeRequest:
     dtype_size: int = 1           # bytes per pixel (1: u8, 2: u16)
     src: object = None            # executor-specific input handle (pre-staged)
     origin: tuple = (0, 0)        # (x0, y0) of the input in its source pool
+    offset: int = -1              # or, for a dense image in a host arena, its byte offset
     # filled by the server
     admitted_s: float = -1.0
     done_s: float = -1.0
@@ -194,10 +197,18 @@ class GpuExecutor:
     def size_class(nbytes: int) -> int:
         return max(1 << 16, 1 << (int(nbytes) - 1).bit_length())
 
+    @staticmethod
+    def scratch_bytes(r: ServeRequest) -> int:
+        """The library's scratch for the request: a 2-D window may run as two
+        passes through an intermediate image (16-byte pitched rows)."""
+        if r.wx <= 1 or r.wy <= 1:
+            return 0
+        return (r.width * r.dtype_size + 15) // 16 * 16 * r.height
+
     def charge(self, r: ServeRequest) -> int:
-        """Input bytes plus the output buffer's size class."""
+        """Input bytes, the output buffer's size class and the scratch."""
         n = r.width * r.height * r.dtype_size
-        return n + self.size_class(n)
+        return n + self.size_class(n) + self.scratch_bytes(r)
 
     def alloc_out(self, r: ServeRequest):
         n = r.width * r.height * r.dtype_size
@@ -253,101 +264,181 @@ class GpuExecutor:
         time.sleep(0.00005)
 
 
+class RingArena:
+    """Blocks of one preallocated buffer, handed out in order and freed in
+    any order: the free space is the span from the newest block's end round
+    to the oldest live block's start.  ``take`` returns None when a block
+    does not fit (the caller then allocates elsewhere)."""
+
+    def __init__(self, buf):
+        self.buf = buf
+        self.cap = buf.numel()
+        self.head = 0
+        self.live = collections.deque()  # [start, end, freed]
+
+    def take(self, n: int):
+        n = (n + 255) // 256 * 256
+        if n > self.cap:
+            return None
+        if not self.live:
+            start = 0
+        else:
+            tail = self.live[0][0]
+            if self.head > tail:  # live span [tail, head): free [head, cap) and [0, tail)
+                start = self.head if self.head + n <= self.cap else (0 if n <= tail else None)
+            else:  # live span wraps: free [head, tail)
+                start = self.head if self.head + n <= tail else None
+        if start is None:
+            return None
+        blk = [start, start + n, False]
+        self.live.append(blk)
+        self.head = start + n
+        return blk
+
+    def view(self, blk):
+        return self.buf[blk[0]:blk[1]]
+
+    def give(self, blk) -> None:
+        blk[2] = True
+        while self.live and self.live[0][2]:
+            self.live.popleft()
+
+
 class HostCopyExecutor(GpuExecutor):
-    """GpuExecutor for requests whose ``src`` is a pinned HOST image (a 2-D
-    CPU tensor, rows may be strided).  Each request takes a device input and
-    a device output buffer (both pooled in power-of-two size classes, both
-    charged to the budget) and a pinned host output buffer (pooled the same
-    way); ``launch`` queues, on the micro-batch's stream, the copies in
-    (morph_copy_2d), the persistent launch (morph_batch) and the copies out,
-    then records the completion event."""
+    """GpuExecutor for requests whose ``src`` is a pinned HOST image (a dense
+    2-D CPU tensor).  A micro-batch takes one device block for its inputs,
+    one for its outputs and one pinned host block for its results, each
+    request at a 256-byte aligned offset, from arenas allocated once (a
+    device arena the size of the budget, a pinned host arena of half of it),
+    so a warm server allocates nothing.  ``launch`` queues on the
+    micro-batch's stream the copies in (one morph_copy_batch call for all
+    requests), the batch (morph_batch), one copy of the whole output block
+    back to the host block, and the completion event; the blocks return to
+    their arenas when the batch's last request finishes."""
 
     def __init__(self, device="cuda", n_streams: int = 4, pool_cap: int = 4 << 30,
-                 host_pool_cap: int = 4 << 30):
+                 host_pool_cap: int = 4 << 30, arena_bytes: int = 4 << 30):
         super().__init__(device=device, n_streams=n_streams, pool_cap=pool_cap)
-        self.host_free = collections.defaultdict(list)
-        self.host_pooled = 0
-        self.host_pool_cap = host_pool_cap
+        torch = self.torch
+        self.dev_arena = RingArena(torch.empty(arena_bytes, dtype=torch.uint8, device=self.device))
+        self.host_arena = RingArena(torch.empty(arena_bytes // 2, dtype=torch.uint8, pin_memory=True))
+        self.blocks = {}  # batch id -> [blocks (arena, block or tensor), requests not finished]
+        self.next_batch = 0
+        self.fallbacks = 0  # micro-batches whose blocks did not fit an arena
+
+    @staticmethod
+    def _padded(r: ServeRequest) -> int:
+        return (r.width * r.height * r.dtype_size + 255) // 256 * 256
 
     def charge(self, r: ServeRequest) -> int:
-        """Device input and output buffers' size classes."""
-        return 2 * self.size_class(r.width * r.height * r.dtype_size)
-
-    def _dev(self, c):
-        if self.free[c]:
-            self.pooled -= c
-            return self.free[c].pop()
-        return self.torch.empty(c, dtype=self.torch.uint8, device=self.device)
-
-    def _host(self, c):
-        if self.host_free[c]:
-            self.host_pooled -= c
-            return self.host_free[c].pop()
-        return self.torch.empty(c, dtype=self.torch.uint8).pin_memory()
-
-    def _view(self, buf, r):
-        v = buf[:r.width * r.height * r.dtype_size]
-        if r.dtype_size == 2:
-            v = v.view(self.torch.uint16)
-        return v.view(r.height, r.width)
+        """Device input and output bytes (256-byte padded) and the scratch."""
+        return 2 * self._padded(r) + self.scratch_bytes(r)
 
     def alloc_out(self, r: ServeRequest):
-        c = self.size_class(r.width * r.height * r.dtype_size)
-        din, dout, hout = self._dev(c), self._dev(c), self._host(c)
-        return (self._view(hout, r), (din, dout, hout))
+        return None  # the micro-batch's blocks are taken in launch()
+
+    def _take(self, arena, n, host):
+        blk = arena.take(n)
+        if blk is not None:
+            return arena.view(blk), (arena, blk)
+        self.fallbacks += 1
+        t = (self.torch.empty(n, dtype=self.torch.uint8, pin_memory=True) if host
+             else self.torch.empty(n, dtype=self.torch.uint8, device=self.device))
+        return t, (None, t)
 
     def finish(self, r: ServeRequest) -> None:
-        out, (din, dout, hout) = r.out
+        out, bid = r.out
         if self.keep is not None:
             self.keep[r.rid] = out.clone()  # host memory, complete at the event
-        c = din.numel()
-        for b in (din, dout):
-            if self.pooled + c <= self.pool_cap:
-                self.free[c].append(b)
-                self.pooled += c
-        if self.host_pooled + c <= self.host_pool_cap:
-            self.host_free[c].append(hout)
-            self.host_pooled += c
+        entry = self.blocks[bid]
+        entry[1] -= 1
+        if entry[1] == 0:
+            for arena, blk in entry[0]:
+                if arena is not None:
+                    arena.give(blk)
+            del self.blocks[bid]
         r.out = None
 
     def launch(self, reqs, stream_index: int):
-        m = self.morph
+        m, torch = self.morph, self.torch
         s = self.streams[stream_index]
         sh = s.cuda_stream
-        descs = (m.MorphDesc * len(reqs))()
-        for d, r in zip(descs, reqs):
-            _, (din, dout, _) = r.out
+        offs, total = [], 0
+        for r in reqs:
+            offs.append(total)
+            total += self._padded(r)
+        din, hin = self._take(self.dev_arena, total, False)
+        dout, hout_d = self._take(self.dev_arena, total, False)
+        hout, hh = self._take(self.host_arena, total, True)
+        bid = self.next_batch
+        self.next_batch += 1
+        self.blocks[bid] = [(hin, hout_d, hh), len(reqs)]
+        n = len(reqs)
+        copies = (m.MorphCopyDesc * n)()
+        descs = (m.MorphDesc * n)()
+        di, do = din.data_ptr(), dout.data_ptr()
+        code = {1: m.MORPH_U8, 2: m.MORPH_U16}
+        for c, d, r, off in zip(copies, descs, reqs, offs):
             row = r.width * r.dtype_size
-            src = r.src
-            rc = m.morph_copy_2d(din.data_ptr(), row, src.data_ptr(), src.stride(0) * src.element_size(), row,
-                                 r.height, sh)
-            if rc != 0:
-                raise m.MorphError("morph_copy_2d", rc)
-            d.src, d.dst = din.data_ptr(), dout.data_ptr()
+            c.dst, c.src, c.bytes = di + off, r.src.data_ptr(), row * r.height
+            d.src, d.dst = di + off, do + off
             d.width, d.height = r.width, r.height
             d.src_pitch = d.dst_pitch = row
             d.wx, d.wy, d.anchor_x, d.anchor_y = r.wx, r.wy, r.ax, r.ay
             d.op = r.op
-            d.dtype = m.MORPH_U8 if r.dtype_size == 1 else m.MORPH_U16
-        rc = m.morph_batch(descs, len(reqs), sh)
+            d.dtype = code[r.dtype_size]
+        rc = m.morph_copy_batch(copies, n, sh)
+        if rc != 0:
+            raise m.MorphError("morph_copy_batch", rc)
+        rc = m.morph_batch(descs, n, sh)
         if rc != 0:
             raise m.MorphError("morph_batch", rc)
-        for r in reqs:
-            out, (_, dout, _) = r.out
-            row = r.width * r.dtype_size
-            rc = m.morph_copy_2d(out.data_ptr(), row, dout.data_ptr(), row, row, r.height, sh)
-            if rc != 0:
-                raise m.MorphError("morph_copy_2d", rc)
-        ev = self.torch.cuda.Event()
+        rc = m.morph_copy_2d(hout.data_ptr(), total, do, total, total, 1, sh)
+        if rc != 0:
+            raise m.MorphError("morph_copy_2d", rc)
+        for r, off in zip(reqs, offs):
+            v = hout[off:off + r.width * r.height * r.dtype_size]
+            if r.dtype_size == 2:
+                v = v.view(torch.uint16)
+            r.out = (v.view(r.height, r.width), bid)
+        ev = torch.cuda.Event()
         ev.record(s)
         return ev
 
 
-def host_source_pool(torch, width: int = 4096, height: int = 4096, seed: int = 6):
-    """The u8 source pool as a pinned host tensor (and its numpy copy)."""
+def host_arena(torch, nbytes: int = 256 << 20, seed: int = 6):
+    """A pinned host arena of uniform u8 bytes (and its numpy copy): request
+    images are dense slices of it, as a client's own image buffer would be."""
     from paper_2002_09474_gb300 import synth
-    img = synth.uniform_image(width, height, np.uint8, seed=seed)
-    return img, torch.from_numpy(img.copy()).pin_memory()
+    raw = synth.uniform_image(nbytes // 4096, 4096, np.uint8, seed=seed).reshape(-1)
+    return raw, torch.from_numpy(raw.copy()).pin_memory()
+
+
+def make_host_requests(rate_per_s: float, duration_s: float, arena_np, arena_pinned, seed: int = 6,
+                       area_hi: int = 4096 * 4096) -> list[ServeRequest]:
+    """The serving workload of make_requests with pinned host inputs: each
+    request's image is a dense (pitch = width) slice of the arena at a seeded
+    offset."""
+    from paper_2002_09474_gb300 import synth
+    specs = synth.serving_requests(rate_per_s, duration_s, seed=seed, area_hi=area_hi)
+    g = synth.rng(seed + 77)
+    n = arena_np.size
+    out = []
+    for i, s in enumerate(specs):
+        w, h = min(s.width, 4096), min(s.height, 4096)
+        off = int(g.integers(0, n - w * h + 1))
+        out.append(ServeRequest(i, s.arrival_s, w, h, s.wx, s.wy, s.ax, s.ay, s.op, 1,
+                                src=arena_pinned[off:off + w * h].view(h, w), offset=off))
+    return out
+
+
+def request_image(r: ServeRequest, pool_img) -> np.ndarray:
+    """The request's input as a numpy image (from the numpy copy of its
+    source pool or arena)."""
+    if r.offset >= 0:
+        return pool_img[r.offset:r.offset + r.width * r.height].reshape(r.height, r.width)
+    x0, y0 = r.origin
+    return pool_img[y0:y0 + r.height, x0:x0 + r.width]
 
 
 def source_pool(torch, width: int = 4096, height: int = 4096, seed: int = 6, device="cuda"):

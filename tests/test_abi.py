@@ -1,5 +1,5 @@
-"""The C-ABI library loads, exports every entry point include/morph.h
-declares, and rejects bad arguments before touching a GPU (CPU only: every
+"""The C-ABI library loads, exports every entry point include/morph.h and
+include/morph_tuning.h declare, and rejects bad arguments before touching a GPU (CPU only: every
 call below fails validation, so no CUDA work is issued)."""
 import ctypes
 
@@ -13,7 +13,7 @@ FAKE2 = 0x7000000
 
 def test_every_declared_symbol_is_exported():
     decl = m.declared_functions()
-    assert len(decl) >= 18
+    assert len(decl) >= 30 and "morph_set_colv" in decl and "morph_copy_batch" in decl
     missing = [f for f in decl if not m.exported(f)]
     assert not missing, missing
 
@@ -147,3 +147,11 @@ def test_composite_and_copy_arguments():
     assert m.morph_copy_2d(FAKE2, 64, FAKE, 64, 64, 0, 0) == -2
     assert m.morph_copy_2d(FAKE2, 32, FAKE, 64, 64, 2, 0) == -5
     assert m.morph_copy_2d(FAKE2, 64, FAKE, 32, 64, 2, 0) == -5
+    # the batched copy: every entry checked before anything is queued
+    cps = (m.MorphCopyDesc * 2)()
+    cps[0].dst, cps[0].src, cps[0].bytes = FAKE2, FAKE, 64
+    cps[1].dst, cps[1].src, cps[1].bytes = None, FAKE, 64
+    assert m.morph_copy_batch(cps, 2, 0) == -1
+    assert m.morph_copy_batch(cps, -1, 0) == -10
+    assert m.morph_copy_batch(None, 1, 0) == -1
+    assert m.morph_copy_batch(None, 0, 0) == 0

@@ -34,6 +34,68 @@ def check_sample(img, got, wx, wy, ax, ay, op, seed):
     np.testing.assert_array_equal(got[ys, xs], oracle.morph_points(img, wx, wy, ax, ay, OPS[op], xs, ys))
 
 
+def test_batch_every_form(env):
+    """One batch whose images take every form: the fused kernel (direct-method
+    windows, small images), the pass along x alone (wx x 1), the pass along y
+    alone (1 x wy), and both through an intermediate (2-D windows above the
+    crossovers) -- u8 and u16, tight and padded pitches, anchor extremes --
+    each compared with the oracle, through morph_batch and the graph plan."""
+    torch, morph = env
+    g = synth.rng(71)
+    cases = []
+    for dt in (np.uint8, np.uint16):
+        esz = np.dtype(dt).itemsize
+        for (w, h) in ((300, 200), (257, 129), (64, 40), (1000, 33), (130, 700), (5, 3)):
+            for (wx, wy) in ((3, 3), (1, 51), (51, 1), (21, 51), (127, 127), (9, 200), (40, 9), (17, 1)):
+                ax, ay = [int(g.integers(0, k)) for k in (wx, wy)]
+                op = int(g.integers(0, 2))
+                pad = (16 - (w * esz) % 16) % 16 if (w + wx) % 2 else 3 * esz
+                cases.append((dt, w, h, wx, wy, ax, ay, op, pad))
+    imgs, srcs, outs = [], [], []
+    arr = (morph.MorphDesc * len(cases))()
+    for d, (dt, w, h, wx, wy, ax, ay, op, pad) in zip(arr, cases):
+        esz = np.dtype(dt).itemsize
+        img = synth.uniform_image(w, h, dt, gen=g)
+        pitch = w * esz + pad
+        src = torch.zeros(h * pitch + 64, dtype=torch.uint8, device="cuda")
+        view = src[:h * pitch].view(h, pitch)[:, :w * esz]
+        view.copy_(torch.from_numpy(img.view(np.uint8).reshape(h, w * esz)).cuda())
+        out = torch.full((h * pitch + 64,), 0x5A, dtype=torch.uint8, device="cuda")
+        d.src, d.dst, d.width, d.height = src.data_ptr(), out.data_ptr(), w, h
+        d.src_pitch = d.dst_pitch = pitch
+        d.wx, d.wy, d.anchor_x, d.anchor_y, d.op = wx, wy, ax, ay, op
+        d.dtype = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
+        imgs.append(img)
+        srcs.append(src)
+        outs.append(out)
+
+    def check():
+        torch.cuda.synchronize()
+        assert morph.morph_device_error() == 0
+        for (dt, w, h, wx, wy, ax, ay, op, pad), img, out in zip(cases, imgs, outs):
+            esz = np.dtype(dt).itemsize
+            pitch = w * esz + pad
+            host = out.cpu().numpy()
+            got = host[:h * pitch].reshape(h, pitch)[:, :w * esz].copy().view(dt)
+            want = oracle.morph(img, wx, wy, ax, ay, OPS[op])
+            assert np.array_equal(got, want), (dt.__name__, w, h, wx, wy, ax, ay, op, pad)
+            rest = host[:h * pitch].reshape(h, pitch)[:, w * esz:]
+            assert (rest == 0x5A).all() and (host[h * pitch:] == 0x5A).all(), "wrote outside the image"
+            out.fill_(0x5A)
+
+    assert morph.morph_batch(arr, len(cases), 0) == 0
+    check()
+    plan = ctypes.c_void_p()
+    rc = morph.morph_batch_plan_create(arr, len(cases), ctypes.byref(plan))
+    assert rc == 0, morph.status_string(rc)
+    try:
+        for _ in range(2):
+            assert morph.morph_batch_plan_launch(plan, 0) == 0
+            check()
+    finally:
+        assert morph.morph_batch_plan_destroy(plan) == 0
+
+
 def test_batch_2000_images_graph_plan(env):
     torch, morph = env
     specs = synth.batch_specs(2000, seed=5)
@@ -125,8 +187,8 @@ def test_serving_with_host_copies(env):
     the oracle, and the budget (device input and output buffers) holds."""
     torch, morph = env
     from paper_2002_09474_gb300 import serve
-    pool_img, pool_host = serve.host_source_pool(torch, seed=8)
-    rs = serve.make_requests(3000.0, 0.1, pool_img, pool_host, seed=8)
+    pool_img, pool_host = serve.host_arena(torch, seed=8)
+    rs = serve.make_host_requests(3000.0, 0.1, pool_img, pool_host, seed=8)
     assert len(rs) > 150
     ex = serve.HostCopyExecutor(n_streams=4)
     ex.keep = {}
@@ -145,6 +207,5 @@ def test_serving_with_host_copies(env):
         assert torch.equal(alone.cpu(), res), r
     for i in synth.rng(88).choice(len(rs), 16, replace=False):
         r = rs[int(i)]
-        x0, y0 = r.origin
-        img = pool_img[y0:y0 + r.height, x0:x0 + r.width]
+        img = serve.request_image(r, pool_img)
         check_sample(img, ex.keep[r.rid].numpy(), r.wx, r.wy, r.ax, r.ay, r.op, 800 + int(i))

@@ -250,3 +250,40 @@ def test_bounded_wait_gives_up_and_context_survives(lib):
     lib.apply(s, o, 9, 7, op=0)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(o.cpu().numpy(), oracle.morph(img, 9, 7, 4, 3, "erode"))
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_typed_entry_points(lib, dtype):
+    """The typed single-image entry points (morph_erode, morph_dilate,
+    morph_erode_u16, morph_dilate_u16: one pitch for source and destination)
+    against the oracle, on every form a call takes: fused small windows, the
+    single-pass kernels of 1-D windows, and the two-launch form of a 2-D
+    window on an image of 2 Mpixels; guard bytes around the destination."""
+    torch = need_cuda()
+    g = synth.rng(910)
+    esz = np.dtype(dtype).itemsize
+    fns = {(np.uint8, "erode"): lib.morph_erode, (np.uint8, "dilate"): lib.morph_dilate,
+           (np.uint16, "erode"): lib.morph_erode_u16, (np.uint16, "dilate"): lib.morph_dilate_u16}
+    for (w, h, wx, wy) in ((300, 200, 3, 5), (1000, 300, 1, 101), (1000, 300, 101, 1), (2048, 1024, 21, 51),
+                           (77, 33, 127, 127)):
+        img = synth.uniform_image(w, h, dtype, gen=g)
+        pad = (16 - (w * esz) % 16) % 16
+        for op in ("erode", "dilate"):
+            ax, ay = int(g.integers(0, wx)), int(g.integers(0, wy))
+            src = DeviceImage(torch, h, w, dtype, pad=pad, fill=img)
+            dst = DeviceImage(torch, h, w, dtype, pad=pad)
+            assert src.pitch == dst.pitch
+            rc = fns[(dtype, op)](src.ptr, w, h, src.pitch, wx, wy, ax, ay, dst.ptr, 0)
+            assert rc == 0, lib.status_string(rc)
+            torch.cuda.synchronize()
+            assert lib.morph_device_error() == 0
+            assert dst.untouched_outside()
+            got = dst.read()
+            if w * h <= 400000:
+                want = oracle.morph(img, wx, wy, ax, ay, op)
+            else:
+                want = oracle.sep_vhgw(img, wx, wy, ax, ay, op)
+                xs = g.integers(0, w, 300).astype(np.int32)
+                ys = g.integers(0, h, 300).astype(np.int32)
+                np.testing.assert_array_equal(got[ys, xs], oracle.morph_points(img, wx, wy, ax, ay, op, xs, ys))
+            np.testing.assert_array_equal(got, want, err_msg="%s %s %dx%d %dx%d" % (dtype.__name__, op, w, h, wx, wy))

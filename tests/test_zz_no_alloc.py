@@ -18,12 +18,12 @@ pytestmark = pytest.mark.gpu
 OPS = ("erode", "dilate")
 
 
-def _make_batch(lib, torch, g, n):
+def _make_batch(lib, torch, g, n, side=400):
     srcs, refs, outs, specs = [], [], [], []
     d_ref, d_out = [], []
     for _ in range(n):
         dt = (np.uint8, np.uint16)[int(g.integers(0, 2))]
-        w, h = int(g.integers(1, 400)), int(g.integers(1, 300))
+        w, h = int(g.integers(1, side)), int(g.integers(1, 3 * side // 4))
         wx, wy = int(g.integers(1, 64)), int(g.integers(1, 64))
         op = int(g.integers(0, 2))
         img = synth.uniform_image(w, h, dt, gen=g)
@@ -63,6 +63,29 @@ def test_no_alloc_batch_matches_allocating_batch_twice():
             if i < 5:  # and a few of them against the oracle directly
                 np.testing.assert_array_equal(
                     out.cpu().numpy(), oracle.morph(img, wx, wy, wx // 2, wy // 2, OPS[op]))
+
+
+def test_no_alloc_largest_batch_on_a_side_stream():
+    """The largest accepted batch (MORPH_NOALLOC_MAX_IMAGES small images,
+    which fills the fixed records to their end), on a non-default stream, two
+    calls in a row, against the allocating morph_batch on the same stream."""
+    torch = need_cuda()
+    from paper_2002_09474_gb300 import morph as lib
+    g = synth.rng(301)
+    s = torch.cuda.Stream()
+    n = lib.MORPH_NOALLOC_MAX_IMAGES
+    for call in range(2):
+        srcs, refs, outs, specs, arr_ref, arr_out = _make_batch(lib, torch, g, n, side=48)
+        torch.cuda.synchronize()
+        assert lib.morph_batch(arr_ref, n, s.cuda_stream) == 0
+        rc = lib.morph_batch_noalloc(arr_out, n, s.cuda_stream)
+        assert rc == 0, lib.status_string(rc)
+        s.synchronize()
+        assert lib.morph_device_error() == 0
+        for i, (ref, out) in enumerate(zip(refs, outs)):
+            assert torch.equal(ref, out), (call, i)
+        img, wx, wy, op = specs[-1]  # the last record, against the oracle
+        np.testing.assert_array_equal(outs[-1].cpu().numpy(), oracle.morph(img, wx, wy, wx // 2, wy // 2, OPS[op]))
 
 
 def test_no_alloc_rejects_more_than_the_maximum():
