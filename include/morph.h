@@ -128,8 +128,8 @@ int morph_apply(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
  * step's).  The library allocates one scratch image of width x height pixels
  * (pitch rounded to 16 bytes) with cudaMallocAsync on the stream and frees it
  * there, so the intermediate stays in L2 where it fits; the call is safe to
- * capture in a CUDA graph.  The gradient's subtraction is a separate
- * elementwise kernel.  Errors as morph_apply; MORPH_ERR_ARG for another kind,
+ * capture in a CUDA graph.  The gradient's subtraction is an elementwise
+ * pass after the dilation.  Errors as morph_apply; MORPH_ERR_ARG for another kind,
  * MORPH_ERR_NOMEM when the scratch cannot be allocated.
  */
 enum { MORPH_OPEN = 0, MORPH_CLOSE = 1, MORPH_GRADIENT = 2 };

@@ -64,8 +64,17 @@ int colv_lane_bytes(const FusedLaunch& L) {
   return 4;
 }
 
+// Tile height: forced by the tuning, else the one the autotuner measured
+// for this pixel type and window class (on images of at least 12 Mpixels:
+// it measures at 16 Mpixels), else the built-in rule.
 ColvPlan colv_plan_for(const FusedLaunch& L) {
-  return colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, tuning().colv_rows, colv_lane_bytes(L), sm_count_v());
+  const Tuning& t = tuning();
+  int rows = t.colv_rows;
+  if (rows == 0 && static_cast<long long>(L.W) * L.H >= (12ll << 20)) {
+    const int fam = t.colv_fam_tuned[L.esz - 1][colv_tune_class(L.wy)];
+    if (fam > 0) rows = colv_family_rows(fam, L.wy);
+  }
+  return colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, rows, colv_lane_bytes(L), sm_count_v());
 }
 
 bool colv_fits(const FusedLaunch& L) { return L.wy >= 2 && colv_plan_for(L).ok; }

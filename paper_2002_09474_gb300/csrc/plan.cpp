@@ -99,8 +99,31 @@ void reset_tuning_defaults() {
   g_tuning.rowv_mode = -1;
   g_tuning.rowv_seg = 0;
   g_tuning.rowv_rr[0] = g_tuning.rowv_rr[1] = 0;
+  for (int e = 0; e < 2; ++e) {
+    for (int c = 0; c < 4; ++c) g_tuning.fused_cfg_tuned[e][c] = -1;
+    for (int c = 0; c < 5; ++c) g_tuning.colv_fam_tuned[e][c] = -1;
+  }
   g_tuning.from_autotune = 0;
   g_init = true;
+}
+
+int fused_tune_class(int wx, int wy) {
+  const int m = wx > wy ? wx : wy;
+  return m <= 3 ? 0 : m <= 5 ? 1 : m <= 7 ? 2 : m <= 9 ? 3 : -1;
+}
+
+int colv_tune_class(int wy) { return wy <= 24 ? 0 : wy <= 40 ? 1 : wy <= 76 ? 2 : wy <= 114 ? 3 : 4; }
+
+int colv_family_rows(int fam, int wy) {
+  switch (fam) {
+    case 1: return wy;
+    case 2: return 2 * wy;
+    case 3: return 3 * wy;
+    case 4: return 64;
+    case 5: return 128;
+    case 6: return 256;
+  }
+  return 0;  // the built-in rule
 }
 
 Tuning& tuning() {
@@ -137,6 +160,18 @@ bool plan_single(FusedLaunch* L) {
   L->vhgw_row = L->wx > t.cross_row[e] && L->wx >= 8;
   if (t.forced_cfg[e] >= 0) {
     L->cfg = t.forced_cfg[e];
+    const int b = fused_smem_bytes(*L);
+    if (b > 0 && b <= kMaxSmemBytes) {
+      set_pipe(L);
+      return true;
+    }
+  }
+  // the tile shape the autotuner measured for this pixel type and window
+  // class (direct-method windows on images of at least 1 Mpixel)
+  const int fc = fused_tune_class(L->wx, L->wy);
+  if (fc >= 0 && !L->vhgw_col && !L->vhgw_row && static_cast<long long>(L->W) * L->H >= (1ll << 20) &&
+      t.fused_cfg_tuned[e][fc] >= 0) {
+    L->cfg = t.fused_cfg_tuned[e][fc];
     const int b = fused_smem_bytes(*L);
     if (b > 0 && b <= kMaxSmemBytes) {
       set_pipe(L);

@@ -25,8 +25,21 @@ struct Tuning {
   int rowv_mode;                  // wx x 1 passes by the register-blocked vHGW kernel: -1 auto, 0 never, 1 always
   int rowv_seg;                   // its output columns per warp segment (0: launch-shape model)
   int rowv_rr[2];                 // [esz-1]: rows per warp of the pass along x (0: built-in, 2)
+  int fused_cfg_tuned[2][4];      // [esz-1][window class]: measured tile shape of the fused kernel, -1 none
+  int colv_fam_tuned[2][5];       // [esz-1][window class]: measured tile-height choice of the pass along y, -1 none
   int from_autotune;              // 1 once measured or loaded from a cache
 };
+
+// Window classes of the measured fused tile shapes: the larger window side
+// up to 3, 5, 7 or 9 (direct-method windows; -1 outside).
+int fused_tune_class(int wx, int wy);
+// Window classes of the measured tile heights of the pass along y: wy up to
+// 24, 40, 76, 114, above (representatives 15, 31, 51, 101, 127).
+int colv_tune_class(int wy);
+// Tile-height choices the autotuner measures for the pass along y: 0 the
+// built-in rule, 1..3 that many windows, 4..6 64, 128 or 256 rows.
+constexpr int kColvFamilies = 7;
+int colv_family_rows(int fam, int wy);
 
 Tuning& tuning();
 void reset_tuning_defaults();

@@ -264,143 +264,91 @@ class GpuExecutor:
         time.sleep(0.00005)
 
 
-class RingArena:
-    """Blocks of one preallocated buffer, handed out in order and freed in
-    any order: the free space is the span from the newest block's end round
-    to the oldest live block's start.  ``take`` returns None when a block
-    does not fit (the caller then allocates elsewhere)."""
-
-    def __init__(self, buf):
-        self.buf = buf
-        self.cap = buf.numel()
-        self.head = 0
-        self.live = collections.deque()  # [start, end, freed]
-
-    def take(self, n: int):
-        n = (n + 255) // 256 * 256
-        if n > self.cap:
-            return None
-        if not self.live:
-            start = 0
-        else:
-            tail = self.live[0][0]
-            if self.head > tail:  # live span [tail, head): free [head, cap) and [0, tail)
-                start = self.head if self.head + n <= self.cap else (0 if n <= tail else None)
-            else:  # live span wraps: free [head, tail)
-                start = self.head if self.head + n <= tail else None
-        if start is None:
-            return None
-        blk = [start, start + n, False]
-        self.live.append(blk)
-        self.head = start + n
-        return blk
-
-    def view(self, blk):
-        return self.buf[blk[0]:blk[1]]
-
-    def give(self, blk) -> None:
-        blk[2] = True
-        while self.live and self.live[0][2]:
-            self.live.popleft()
-
-
 class HostCopyExecutor(GpuExecutor):
     """GpuExecutor for requests whose ``src`` is a pinned HOST image (a dense
-    2-D CPU tensor).  A micro-batch takes one device block for its inputs,
-    one for its outputs and one pinned host block for its results, each
-    request at a 256-byte aligned offset, from arenas allocated once (a
-    device arena the size of the budget, a pinned host arena of half of it),
-    so a warm server allocates nothing.  ``launch`` queues on the
-    micro-batch's stream the copies in (one morph_copy_batch call for all
-    requests), the batch (morph_batch), one copy of the whole output block
-    back to the host block, and the completion event; the blocks return to
-    their arenas when the batch's last request finishes."""
+    2-D CPU tensor).  Each request takes a device input and a device output
+    buffer and a pinned host output buffer, all pooled in power-of-two size
+    classes (a warm server allocates nothing); ``launch`` queues on the
+    micro-batch's stream the copies in (one morph_copy_batch call for the
+    whole micro-batch), the batch (morph_batch), the copies out (one more
+    morph_copy_batch call) and the completion event."""
 
     def __init__(self, device="cuda", n_streams: int = 4, pool_cap: int = 4 << 30,
-                 host_pool_cap: int = 4 << 30, arena_bytes: int = 4 << 30):
+                 host_pool_cap: int = 4 << 30):
         super().__init__(device=device, n_streams=n_streams, pool_cap=pool_cap)
-        torch = self.torch
-        self.dev_arena = RingArena(torch.empty(arena_bytes, dtype=torch.uint8, device=self.device))
-        self.host_arena = RingArena(torch.empty(arena_bytes // 2, dtype=torch.uint8, pin_memory=True))
-        self.blocks = {}  # batch id -> [blocks (arena, block or tensor), requests not finished]
-        self.next_batch = 0
-        self.fallbacks = 0  # micro-batches whose blocks did not fit an arena
-
-    @staticmethod
-    def _padded(r: ServeRequest) -> int:
-        return (r.width * r.height * r.dtype_size + 255) // 256 * 256
+        self.host_free = collections.defaultdict(list)
+        self.host_pooled = 0
+        self.host_pool_cap = host_pool_cap
 
     def charge(self, r: ServeRequest) -> int:
-        """Device input and output bytes (256-byte padded) and the scratch."""
-        return 2 * self._padded(r) + self.scratch_bytes(r)
+        """Device input and output buffers' size classes and the scratch."""
+        return 2 * self.size_class(r.width * r.height * r.dtype_size) + self.scratch_bytes(r)
+
+    def _dev(self, c):
+        if self.free[c]:
+            self.pooled -= c
+            return self.free[c].pop()
+        return self.torch.empty(c, dtype=self.torch.uint8, device=self.device)
+
+    def _host(self, c):
+        if self.host_free[c]:
+            self.host_pooled -= c
+            return self.host_free[c].pop()
+        return self.torch.empty(c, dtype=self.torch.uint8).pin_memory()
 
     def alloc_out(self, r: ServeRequest):
-        return None  # the micro-batch's blocks are taken in launch()
-
-    def _take(self, arena, n, host):
-        blk = arena.take(n)
-        if blk is not None:
-            return arena.view(blk), (arena, blk)
-        self.fallbacks += 1
-        t = (self.torch.empty(n, dtype=self.torch.uint8, pin_memory=True) if host
-             else self.torch.empty(n, dtype=self.torch.uint8, device=self.device))
-        return t, (None, t)
+        c = self.size_class(r.width * r.height * r.dtype_size)
+        return (None, (self._dev(c), self._dev(c), self._host(c)))
 
     def finish(self, r: ServeRequest) -> None:
-        out, bid = r.out
+        out, (din, dout, hout) = r.out
         if self.keep is not None:
             self.keep[r.rid] = out.clone()  # host memory, complete at the event
-        entry = self.blocks[bid]
-        entry[1] -= 1
-        if entry[1] == 0:
-            for arena, blk in entry[0]:
-                if arena is not None:
-                    arena.give(blk)
-            del self.blocks[bid]
+        c = din.numel()
+        for b in (din, dout):
+            if self.pooled + c <= self.pool_cap:
+                self.free[c].append(b)
+                self.pooled += c
+        if self.host_pooled + c <= self.host_pool_cap:
+            self.host_free[c].append(hout)
+            self.host_pooled += c
         r.out = None
 
     def launch(self, reqs, stream_index: int):
         m, torch = self.morph, self.torch
         s = self.streams[stream_index]
         sh = s.cuda_stream
-        offs, total = [], 0
-        for r in reqs:
-            offs.append(total)
-            total += self._padded(r)
-        din, hin = self._take(self.dev_arena, total, False)
-        dout, hout_d = self._take(self.dev_arena, total, False)
-        hout, hh = self._take(self.host_arena, total, True)
-        bid = self.next_batch
-        self.next_batch += 1
-        self.blocks[bid] = [(hin, hout_d, hh), len(reqs)]
         n = len(reqs)
-        copies = (m.MorphCopyDesc * n)()
+        cin = (m.MorphCopyDesc * n)()
+        cout = (m.MorphCopyDesc * n)()
         descs = (m.MorphDesc * n)()
-        di, do = din.data_ptr(), dout.data_ptr()
         code = {1: m.MORPH_U8, 2: m.MORPH_U16}
-        for c, d, r, off in zip(copies, descs, reqs, offs):
+        for ci, co, d, r in zip(cin, cout, descs, reqs):
+            _, (din, dout, hout) = r.out
             row = r.width * r.dtype_size
-            c.dst, c.src, c.bytes = di + off, r.src.data_ptr(), row * r.height
-            d.src, d.dst = di + off, do + off
+            nb = row * r.height
+            di, do = din.data_ptr(), dout.data_ptr()
+            ci.dst, ci.src, ci.bytes = di, r.src.data_ptr(), nb
+            co.dst, co.src, co.bytes = hout.data_ptr(), do, nb
+            d.src, d.dst = di, do
             d.width, d.height = r.width, r.height
             d.src_pitch = d.dst_pitch = row
             d.wx, d.wy, d.anchor_x, d.anchor_y = r.wx, r.wy, r.ax, r.ay
             d.op = r.op
             d.dtype = code[r.dtype_size]
-        rc = m.morph_copy_batch(copies, n, sh)
+            v = hout[:nb]
+            if r.dtype_size == 2:
+                v = v.view(torch.uint16)
+            r.out = (v.view(r.height, r.width), r.out[1])
+        rc = m.morph_copy_batch(cin, n, sh)
         if rc != 0:
             raise m.MorphError("morph_copy_batch", rc)
         rc = m.morph_batch(descs, n, sh)
         if rc != 0:
             raise m.MorphError("morph_batch", rc)
-        rc = m.morph_copy_2d(hout.data_ptr(), total, do, total, total, 1, sh)
+        rc = m.morph_copy_batch(cout, n, sh)
         if rc != 0:
-            raise m.MorphError("morph_copy_2d", rc)
-        for r, off in zip(reqs, offs):
-            v = hout[off:off + r.width * r.height * r.dtype_size]
-            if r.dtype_size == 2:
-                v = v.view(torch.uint16)
-            r.out = (v.view(r.height, r.width), bid)
+            raise m.MorphError("morph_copy_batch", rc)
         ev = torch.cuda.Event()
         ev.record(s)
         return ev

@@ -162,7 +162,7 @@ def test_autotune_and_cache(lib, tmp_path):
     assert lib.morph_autotune(path) == 0
     text = open(path).read()
     assert '"cross"' in text and '"device"' in text and '"xpass"' in text
-    assert '"rowv_rows"' in text
+    assert '"rowv_rows"' in text and '"fused_cfg"' in text and '"colv_family"' in text
     # a second call loads the cache; results stay exact either way
     assert lib.morph_autotune(path) == 0
     img = synth.uniform_image(300, 200, np.uint8, seed=221)
@@ -173,13 +173,18 @@ def test_autotune_and_cache(lib, tmp_path):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(o.cpu().numpy(), oracle.morph(img, wx, wy, wx // 2, wy // 2, "erode"))
     # the measured launch shapes, on an image large enough to use them
-    big = synth.uniform_image(2500, 2300, np.uint16, seed=222)
-    s = torch.from_numpy(big).cuda()
-    for (wx, wy) in ((1, 101), (101, 1), (21, 51), (127, 127)):
-        o = torch.empty_like(s)
-        lib.apply(s, o, wx, wy, op=1)
-        torch.cuda.synchronize()
-        np.testing.assert_array_equal(o.cpu().numpy(), oracle.sep_vhgw(big, wx, wy, wx // 2, wy // 2, "dilate"))
+    # (the tile heights of the pass along y in every window class, and the
+    # fused tile shapes of the direct-method window classes)
+    for dt in (np.uint8, np.uint16):
+        big = synth.uniform_image(4000, 3300, dt, seed=222)
+        s = torch.from_numpy(big).cuda()
+        for (wx, wy) in ((1, 15), (1, 31), (1, 51), (1, 101), (1, 127), (101, 1), (21, 51), (127, 127),
+                         (3, 3), (5, 5), (7, 7), (9, 9)):
+            o = torch.empty_like(s)
+            lib.apply(s, o, wx, wy, op=1)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(o.cpu().numpy(), oracle.sep_vhgw(big, wx, wy, wx // 2, wy // 2, "dilate"),
+                                          err_msg="%s %dx%d" % (dt.__name__, wx, wy))
     lib.morph_reset_tuning()
 
 

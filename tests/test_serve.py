@@ -117,37 +117,3 @@ def test_max_batch_respected():
     assert max(len(ids) for _, _, ids in ex.launches) <= 16
     assert sorted(i for _, _, ids in ex.launches for i in ids) == list(range(100))
 
-
-def test_ring_arena_blocks_never_overlap_live_ones():
-    """The host-copy executor's arena: blocks taken in order and given back
-    in any order never overlap a live block, and a freed span is reused."""
-    import numpy as np
-
-    from paper_2002_09474_gb300.serve import RingArena
-
-    class Buf:
-        def numel(self):
-            return 64 * 256
-
-        def __getitem__(self, sl):
-            return sl
-
-    a = RingArena(Buf())
-    g = np.random.default_rng(5)
-    live = []
-    for step in range(3000):
-        if live and (g.random() < 0.5 or len(live) > 20):
-            blk = live.pop(int(g.integers(0, len(live))))
-            a.give(blk)
-            continue
-        n = int(g.integers(1, 16)) * 256 - int(g.integers(0, 200))
-        blk = a.take(n)
-        if blk is None:
-            continue
-        assert blk[1] - blk[0] >= n and 0 <= blk[0] and blk[1] <= 64 * 256 and blk[0] % 256 == 0
-        for o in live:
-            assert blk[1] <= o[0] or o[1] <= blk[0], (blk, o)
-        live.append(blk)
-    for blk in live:
-        a.give(blk)
-    assert not a.live and a.take(64 * 256) is not None
