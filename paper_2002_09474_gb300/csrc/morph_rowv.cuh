@@ -41,9 +41,12 @@ constexpr int kRvRing = 64;    // prefix ring: two chunks of blocks
 // Input chunks in flight or in use per warp: 3 for u8 (copies run two
 // chunks ahead), 2 for u16 (one chunk ahead; each chunk is twice the bytes).
 __host__ __device__ constexpr int rv_slots(int esz) { return esz == 1 ? 3 : 2; }
-// Shared memory per warp: the prefix ring (8 prefixes x kRvRing blocks x
-// RR/2 words), then the input slots of RR rows x 33 entries of 8 pixels.
-__host__ __device__ constexpr int rv_raw_off(int rr) { return 8 * kRvRing * 2 * rr; }
+// Shared memory per warp: the prefix ring (kRvRing records, one per block:
+// its 8 prefixes of RR/2 words, padded by 16 bytes so that a quarter warp's
+// 16-byte accesses to consecutive records hit distinct banks), then the
+// input slots of RR rows x 33 entries of 8 pixels.
+__host__ __device__ constexpr int rv_rec_bytes(int rr) { return 16 * rr + 16; }
+__host__ __device__ constexpr int rv_raw_off(int rr) { return kRvRing * rv_rec_bytes(rr); }
 __host__ __device__ constexpr int rv_warp_smem(int esz, int rr) {
   return rv_raw_off(rr) + rv_slots(esz) * rr * 33 * 8 * esz;
 }
@@ -225,10 +228,47 @@ __device__ __forceinline__ void rv_store_block(const RowvArgs& a, int y0, int x,
   }
 }
 
+// Prefix n of a block's ring record.
+template <int RR>
+__device__ __forceinline__ RVec<RR> rv_rec_get(const uint8_t* rec, int n) {
+  return *reinterpret_cast<const RVec<RR>*>(rec + n * (RR / 2) * 4);
+}
+
+// Outputs of one block for a compile-time r: S (suffixes, seeded with the
+// fold of the whole blocks), rq and rq1 the records of blocks k+q and
+// k+q+1; output i is op(S[i], P_{k+q}[r+i]) or op(S[i], T_{k+q},
+// P_{k+q+1}[r+i-8]).  Each prefix is loaded where it is used, so few stay
+// live at once.
+template <int R, int OP, int RR>
+__device__ __forceinline__ void rv_combine_r(RVec<RR> (&S)[8], const uint8_t* rq, const uint8_t* rq1) {
+  RVec<RR> tq;
+  if (R > 0) tq = rv_rec_get<RR>(rq, 7);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (i + R < 8)
+      S[i] = rv_op<OP, RR>(S[i], rv_rec_get<RR>(rq, i + R));
+    else
+      S[i] = rv_op<OP, RR>(S[i], rv_op<OP, RR>(tq, rv_rec_get<RR>(rq1, i + R - 8)));
+  }
+}
+template <int OP, int RR>
+__device__ __forceinline__ void rv_combine(int r, RVec<RR> (&S)[8], const uint8_t* rq, const uint8_t* rq1) {
+  switch (r) {
+    case 0: rv_combine_r<0, OP, RR>(S, rq, rq1); break;
+    case 1: rv_combine_r<1, OP, RR>(S, rq, rq1); break;
+    case 2: rv_combine_r<2, OP, RR>(S, rq, rq1); break;
+    case 3: rv_combine_r<3, OP, RR>(S, rq, rq1); break;
+    case 4: rv_combine_r<4, OP, RR>(S, rq, rq1); break;
+    case 5: rv_combine_r<5, OP, RR>(S, rq, rq1); break;
+    case 6: rv_combine_r<6, OP, RR>(S, rq, rq1); break;
+    default: rv_combine_r<7, OP, RR>(S, rq, rq1); break;
+  }
+}
+
 // One warp task: rows RR * (task / nseg) .. +RR-1, output columns of segment
 // task % nseg.  ws: this warp's shared memory (rv_warp_smem bytes): the
-// prefix ring (slot n of block b at vector index n * kRvRing + b), then the
-// input slots.
+// prefix ring (the record of block b at b mod kRvRing), then the input
+// slots.
 //
 // Input chunks travel by per-lane asynchronous copies one (u16) or two (u8)
 // chunks ahead of use: lane l copies the 8 pixels at the aligned column of
@@ -241,8 +281,9 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
   constexpr int E = sizeof(T), EB = 8 * E;  // bytes per entry
   constexpr int NS = rv_slots(E), D = NS - 1;  // input slots, chunks copied ahead
   using V = RVec<RR>;
-  V* pb = reinterpret_cast<V*>(ws);
+  constexpr int RB = rv_rec_bytes(RR);
   uint8_t* raw = ws + rv_raw_off(RR);
+  auto rec = [&](int b) { return ws + (b & (kRvRing - 1)) * RB; };
   const int y0 = RR * (task / a.nseg);
   const int xs = (task % a.nseg) * a.seg;
   const int xe = xs + a.seg < a.W ? xs + a.seg : a.W;
@@ -252,39 +293,48 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
   const int q = (a.w - 1) >> 3, r = (a.w - 1) & 7;
   const bool rows_in = y0 + RR <= a.H;
 
-  auto entry = [&](int slot, int row, int e) { return raw + ((slot * RR + row) * 33 + e) * EB; };
-  auto fast_chunk = [&](int j) {
-    const int cs = X0 + kRvChunk * j - dl;
-    return rows_in && cs >= 0 && cs + kRvChunk + 8 <= a.W;
-  };
+  // The chunks whose copies stay inside the image form one interval
+  // [jf0, jf1] (the chunk start grows with j); the others load directly.
+  const int cs0 = X0 - dl;  // aligned input column of chunk 0's block 0
+  const int jf0 = cs0 >= 0 ? 0 : (-cs0 + kRvChunk - 1) / kRvChunk;
+  const int jf1 = rows_in ? (a.W - kRvChunk - 8 - cs0 >= 0 ? (a.W - kRvChunk - 8 - cs0) / kRvChunk : -1) : -1;
+  auto fast_chunk = [&](int j) { return j >= jf0 && j <= jf1; };
+  // this lane's entry in slot 0, row 0; slots and rows at fixed strides
+  constexpr int kRowStride = 33 * EB, kSlotStride = RR * kRowStride;
+  uint8_t* const ent = raw + lane * EB;
+  // this lane's source in chunk 0, row 0 (rows at the pitch; only chunks
+  // with every row inside the image are copied)
+  const uint8_t* const gsrc = a.src + static_cast<long long>(y0) * a.sp + static_cast<long long>(cs0 + 8 * lane) * E;
+  int slot_issue = 0, slot_build = 0;  // j mod NS of the next issue and build
   auto issue = [&](int j) {
     if (j <= nck && fast_chunk(j)) {
-      const int slot = j % NS, cs = X0 + kRvChunk * j - dl;
+      uint8_t* d = ent + slot_issue * kSlotStride;
+      const long long off = static_cast<long long>(kRvChunk) * j * E;
 #pragma unroll
       for (int rr = 0; rr < RR; ++rr) {
-        const uint8_t* row = a.src + static_cast<long long>(y0 + rr) * a.sp;
-        const uint8_t* g = row + static_cast<long long>(cs + 8 * lane) * E;
-        if (E == 1) cp_async8(entry(slot, rr, lane), g); else cp_async16(entry(slot, rr, lane), g);
+        const uint8_t* g = gsrc + off + rr * a.sp;
+        if (E == 1) cp_async8(d + rr * kRowStride, g); else cp_async16(d + rr * kRowStride, g);
         if (lane == 31) {
-          const uint8_t* t = row + static_cast<long long>(cs + kRvChunk) * E;
-          if (E == 1) cp_async8(entry(slot, rr, 32), t); else cp_async16(entry(slot, rr, 32), t);
+          if (E == 1) cp_async8(d + rr * kRowStride + EB, g + EB); else cp_async16(d + rr * kRowStride + EB, g + EB);
         }
       }
     }
     cp_async_commit();
+    slot_issue = slot_issue + 1 == NS ? 0 : slot_issue + 1;
   };
   // Block data of chunk j from its input slot: V[p] = pixel column p.
   auto build = [&](int j, V (&Vb)[8]) {
+    const int slot = slot_build;
+    slot_build = slot_build + 1 == NS ? 0 : slot_build + 1;
     if (!fast_chunk(j)) {
       rv_load_block<T, OP, RR>(a, y0, X0 + kRvChunk * j + 8 * lane, dl, Vb);
       return;
     }
-    const int slot = j % NS;
     uint32_t R[RR][4];
 #pragma unroll
     for (int rr = 0; rr < RR; ++rr) {
-      const uint8_t* p0 = entry(slot, rr, lane);
-      const uint8_t* p1 = entry(slot, rr, lane + 1);
+      const uint8_t* p0 = ent + slot * kSlotStride + rr * kRowStride;
+      const uint8_t* p1 = p0 + EB;
       if (E == 1) {
         const uint2 x = *reinterpret_cast<const uint2*>(p0), y = *reinterpret_cast<const uint2*>(p1);
         const int sh = 8 * (dl & 3);
@@ -319,13 +369,20 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
     rv_transpose_in<T, RR>(R, Vb);
   };
   auto prefixes = [&](const V (&Vb)[8], int k) {  // returns the block total
-    const int b = k & (kRvRing - 1);
+    // each 16-byte group of prefixes is stored as soon as it is complete
+    constexpr int NW = RR / 2, PG = 4 / NW > 0 ? 4 / NW : 1;  // prefixes per 16 bytes
+    uint4* out = reinterpret_cast<uint4*>(rec(k));
     V P = Vb[0];
-    pb[b] = P;
+    uint32_t g[4];
 #pragma unroll
-    for (int n = 1; n < 8; ++n) {
-      P = rv_op<OP, RR>(P, Vb[n]);
-      pb[n * kRvRing + b] = P;
+    for (int n = 0; n < 8; ++n) {
+      if (n) P = rv_op<OP, RR>(P, Vb[n]);
+#pragma unroll
+      for (int j = 0; j < NW; ++j) g[((n % PG) * NW + j) & 3] = P.w[j];
+      if (NW <= 4 && (n % PG) == PG - 1) {
+#pragma unroll
+        for (int c = 0; c < (NW > 4 ? NW / 4 : 1); ++c) out[n / PG] = make_uint4(g[0], g[1], g[2], g[3]);
+      }
     }
     return P;
   };
@@ -343,6 +400,16 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
   };
   const V ID = rv_ident<OP, RR>();
   V Tprev = ID;  // block totals of the previous chunk (lane l: block 32(j-1) + l)
+  // the fold's doubling levels (p = 1 .. 2^(nlev-1), the largest power of
+  // two p with 2p <= q - 1 reached) and the lanes its two gathers read
+  int nlev = 0, pmax = 1;
+  while (2 * pmax <= q - 1) {
+    pmax *= 2;
+    ++nlev;
+  }
+  if (nlev == 0) nlev = 1;  // q >= 5 always takes at least the first level
+  const int g1_src = (lane + 1) & 31, g2_src = (lane + q - pmax) & 31;
+  const bool g1_in = lane + 1 < 32, g2_in = lane + q - pmax < 32;
 
   // One step: chunk j's block data into Vnew (and its prefixes into the
   // ring), then the outputs of chunk j-1 from Vold.  Steps alternate the two
@@ -369,38 +436,34 @@ __device__ __forceinline__ void rowv_task(const RowvArgs& a, int task, int lane,
       V m = ID;
       if (q >= 5) {
         V lo = Tprev, hi = Tnew;
-        int p = 1;
-        for (; 2 * p <= q - 1; p *= 2) {
+        auto level = [&](int p) {
           const int src = (lane + p) & 31;
           const bool in = lane + p < 32;
           const V al = shfl(lo, src), ah = shfl(hi, src);
           lo = rv_op<OP, RR>(lo, pick(in, al, ah));
           hi = rv_op<OP, RR>(hi, pick(in, ah, ID));
-        }
-        auto gather = [&](int off) {
-          const int src = (lane + off) & 31;
-          const V al = shfl(lo, src), ah = shfl(hi, src);
-          return pick(lane + off < 32, al, ah);
         };
-        m = rv_op<OP, RR>(gather(1), gather(q - p));
+        // levels p = 1, 2, 4, 8 while 2p <= q - 1 (q <= 31: at most 4),
+        // unrolled: the level count is the same for the whole task
+        level(1);
+        if (nlev >= 2) level(2);
+        if (nlev >= 3) level(4);
+        if (nlev >= 4) level(8);
+        auto gather = [&](int src, bool in) {
+          const V al = shfl(lo, src), ah = shfl(hi, src);
+          return pick(in, al, ah);
+        };
+        m = rv_op<OP, RR>(gather(g1_src, g1_in), gather(g2_src, g2_in));
       } else {
-        for (int t = 1; t < q; ++t) m = rv_op<OP, RR>(m, rv_lds(&pb[7 * kRvRing + ((k + t) & (kRvRing - 1))]));
+        for (int t = 1; t < q; ++t) m = rv_op<OP, RR>(m, rv_rec_get<RR>(rec(k + t), 7));
       }
       V S[8];  // suffixes of block k, seeded with m
       S[7] = rv_op<OP, RR>(Vold[7], m);
 #pragma unroll
       for (int i = 6; i >= 0; --i) S[i] = rv_op<OP, RR>(Vold[i], S[i + 1]);
-      const int bq = (k + q) & (kRvRing - 1), bq1 = (k + q + 1) & (kRvRing - 1);
-      const V Tq = rv_lds(&pb[7 * kRvRing + bq]);
-      // (a branch-free form -- one ring load per output and a select of Tq
-      // or the identity -- measured 6% slower on the GB300: the extra
-      // operation per output costs more than the branches it removes)
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int n = r + i;
-        const V Pv = n < 8 ? rv_lds(&pb[n * kRvRing + bq]) : rv_op<OP, RR>(Tq, rv_lds(&pb[(n - 8) * kRvRing + bq1]));
-        S[i] = rv_op<OP, RR>(S[i], Pv);
-      }
+      // the prefixes of blocks k+q and k+q+1 (two records), combined
+      // by a compile-time offset r
+      rv_combine<OP, RR>(r, S, rec(k + q), rec(k + q + 1));
       const int x = xs + 8 * k;
       if (x < xe) rv_store_block<T, RR>(a, y0, x, xe, S);
     }
