@@ -45,11 +45,14 @@
  *  - Single-image calls allocate nothing, except the two-launch form of
  *    2-D windows (see morph_set_split) and the transpose form of the pass
  *    along x (see morph_set_xpass), which take their intermediate image
- *    per call from the stream-ordered allocator (cudaMallocAsync and
- *    cudaFreeAsync on the call's stream: the device's default memory pool
- *    serves it without a device synchronisation, calls on different
- *    streams never share it, and such calls can be captured into a CUDA
- *    graph).  morph_batch_noalloc allocates nothing at all.
+ *    per call from the stream-ordered allocator (cudaMallocFromPoolAsync
+ *    and cudaFreeAsync on the call's stream, from a memory pool the
+ *    library creates per device and that keeps freed memory for the next
+ *    call, so a warm caller maps no new memory; calls on different streams
+ *    never share a block; under stream capture the block is a node of the
+ *    graph, allocated by cudaMallocAsync).  morph_release_staging gives the
+ *    pool's unused memory back.  morph_batch_noalloc allocates nothing at
+ *    all.
  */
 #ifndef MORPH_H
 #define MORPH_H
@@ -126,9 +129,9 @@ int morph_apply(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
  *                   anchor (never negative)
  * Arguments as in morph_apply (kind replaces op; the anchor is the first
  * step's).  The library allocates one scratch image of width x height pixels
- * (pitch rounded to 16 bytes) with cudaMallocAsync on the stream and frees it
- * there, so the intermediate stays in L2 where it fits; the call is safe to
- * capture in a CUDA graph.  The gradient's subtraction is an elementwise
+ * (pitch rounded to 16 bytes) from the library's stream-ordered pool on the
+ * stream and frees it there, so the intermediate stays in L2 where it fits;
+ * the call is safe to capture in a CUDA graph.  The gradient's subtraction is an elementwise
  * pass after the dilation.  Errors as morph_apply; MORPH_ERR_ARG for another kind,
  * MORPH_ERR_NOMEM when the scratch cannot be allocated.
  */
@@ -176,6 +179,12 @@ int morph_composite(const void *src, size_t src_pitch, void *dst, size_t dst_pit
 int morph_apply_host(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
                      int width, int height, int dtype, int op,
                      int wx, int wy, int anchor_x, int anchor_y, void *stream);
+/*
+ * Frees the host-copy staging buffers and pipelines above and gives the
+ * unused memory of the library's stream-ordered scratch pools back to the
+ * driver (blocks of calls still queued stay valid).  Later calls recreate
+ * what they need.  Returns MORPH_OK.
+ */
 int morph_release_staging(void);
 
 /*
@@ -203,8 +212,8 @@ typedef struct {
  * launches of the pass-along-y kernel (one per tile-size class).  Each image
  * gets exactly the bytes of its single call.  The descriptor array is on the
  * host; the call copies it (and the derived records) to a stream-ordered
- * device block (cudaMallocAsync on `stream`, which also holds the
- * intermediates) through the library's pinned staging buffers, so descs may
+ * device block (from the library's stream-ordered pool on `stream`, which
+ * also holds the intermediates) through the library's pinned staging buffers, so descs may
  * be reused as soon as the call returns.  Asynchronous.
  */
 int morph_batch(const morph_desc *descs_host, int n, void *stream);

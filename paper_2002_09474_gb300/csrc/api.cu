@@ -59,6 +59,58 @@ void clip_window(int n, int w, int a, int* w_out, int* a_out) {
 
 namespace {
 
+constexpr int kMaxDevices = 64;
+
+// Stream-ordered scratch (intermediate images, batch records) comes from a
+// memory pool of the library's own per device, whose release threshold keeps
+// freed memory mapped for the next call.  The device's default pool gives
+// freed memory back to the driver at every synchronisation, after which the
+// next large allocation maps new pages on the calling thread: milliseconds
+// for a few hundred MB, and a stall of whatever loop issues the calls.
+// morph_release_staging trims the pools.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaError_t scratch_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+// Pool memory, freed with cudaFreeAsync.  Under stream capture the
+// allocation becomes a node of the graph (cudaMallocAsync), which owns it.
+cudaError_t scratch_malloc(void** p, size_t bytes, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusNone) return cudaMallocAsync(p, bytes, st);
+  cudaMemPool_t pool = nullptr;
+  e = scratch_pool(&pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
 // Stream-ordered scratch image of `rows` rows of `row_bytes` (pitch rounded
 // to 16 bytes so that TMA can describe it).
 struct Scratch {
@@ -68,7 +120,7 @@ struct Scratch {
   bool alloc(size_t row_bytes, int rows, cudaStream_t s) {
     st = s;
     pitch = (row_bytes + 15) / 16 * 16;
-    return cudaMallocAsync(&p, pitch * static_cast<size_t>(rows), s) == cudaSuccess;
+    return scratch_malloc(&p, pitch * static_cast<size_t>(rows), s) == cudaSuccess;
   }
   ~Scratch() {
     if (p) cudaFreeAsync(p, st);
@@ -215,7 +267,6 @@ struct Staging {
   void* out = nullptr;
   size_t bytes = 0;
 };
-constexpr int kMaxDevices = 64;
 Staging g_staging[kMaxDevices];
 std::mutex g_staging_mu;
 
@@ -320,18 +371,20 @@ int plan_batch(const morph_desc* d, int n, std::vector<BatchImageIn>* out) {
   return plan_batch_into(d, n, out->data(), ranges.data());
 }
 
-// Pinned host staging of batch records, per device: a few slots used in
-// turn, each with the event of the copy that last read it, so records travel
-// by truly asynchronous copies (a copy from pageable memory would wait for
-// the stream's earlier work and stall the caller).  A slot is reused once
-// its previous copy has run; it grows on demand.
-constexpr int kStageSlots = 8;
+// Pinned host staging of batch records, per device: slots used in turn, each
+// with the event of the copy that last read it, so records travel by truly
+// asynchronous copies (a copy from pageable memory would wait for the
+// stream's earlier work and stall the caller).  A call takes a slot whose
+// previous copy has run; while every slot is still queued behind other
+// work it adds one (up to kStageSlotsMax), and only then waits.  Slots grow
+// on demand.
+constexpr int kStageSlotsMax = 64;
 struct RecordStage {
   std::mutex mu;
-  void* buf[kStageSlots] = {};
-  size_t cap[kStageSlots] = {};
-  cudaEvent_t ev[kStageSlots] = {};
-  int next = 0;
+  void* buf[kStageSlotsMax] = {};
+  size_t cap[kStageSlotsMax] = {};
+  cudaEvent_t ev[kStageSlotsMax] = {};
+  int used = 0, next = 0;
 };
 RecordStage g_rstage[kMaxDevices];
 
@@ -345,15 +398,24 @@ cudaError_t stage_records(void* dst, const void* const* parts, const size_t* siz
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   RecordStage& rs = g_rstage[dev];
   std::lock_guard<std::mutex> lock(rs.mu);
-  const int k = rs.next;
-  rs.next = (k + 1) % kStageSlots;
-  if (!rs.ev[k]) {
-    e = cudaEventCreateWithFlags(&rs.ev[k], cudaEventDisableTiming);
+  int k = -1;
+  for (int i = 0; i < rs.used && k < 0; ++i) {
+    const int j = (rs.next + i) % rs.used;
+    e = cudaEventQuery(rs.ev[j]);
+    if (e == cudaSuccess) k = j;
+    else if (e != cudaErrorNotReady) return e;
+  }
+  if (k < 0 && rs.used < kStageSlotsMax) {
+    e = cudaEventCreateWithFlags(&rs.ev[rs.used], cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
-  } else {
+    k = rs.used++;
+  }
+  if (k < 0) {
+    k = rs.next % rs.used;
     e = cudaEventSynchronize(rs.ev[k]);  // the slot's previous copy has run
     if (e != cudaSuccess) return e;
   }
+  rs.next = (k + 1) % rs.used;
   if (rs.cap[k] < bytes) {
     if (rs.buf[k]) cudaFreeHost(rs.buf[k]);
     rs.buf[k] = nullptr;
@@ -531,11 +593,11 @@ int morph_batch(const morph_desc* descs_host, int n, void* stream) {
   if (batch_configure(&h) != cudaSuccess) return MORPH_ERR_CUDA;
   const BatchDev L = batch_dev_layout(h);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // Stream-ordered scratch (records, then the 2-D images' intermediates):
-  // allocated and freed in the stream's order, so concurrent batches on
-  // different streams never share it.
+  // Stream-ordered scratch from the library's pool (records, then the 2-D
+  // images' intermediates): allocated and freed in the stream's order, so
+  // concurrent batches on different streams never share it.
   void* dmem = nullptr;
-  if (cudaMallocAsync(&dmem, L.bytes, st) != cudaSuccess) return MORPH_ERR_NOMEM;
+  if (scratch_malloc(&dmem, L.bytes, st) != cudaSuccess) return MORPH_ERR_NOMEM;
   uint8_t* base = static_cast<uint8_t*>(dmem);
   batch_bind_intermediates(base + L.inter_off, &h);
   cudaError_t e = upload_batch(h, L, base, st);
@@ -761,6 +823,12 @@ int morph_apply_host_batch(const morph_desc* descs, int n, void* stream) {
 
 int morph_release_staging(void) {
   release_pipelines();
+  {
+    // unused pool memory back to the driver (blocks still in use stay)
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (int d = 0; d < kMaxDevices; ++d)
+      if (g_pool[d]) cudaMemPoolTrimTo(g_pool[d], 0);
+  }
   std::lock_guard<std::mutex> lock(g_staging_mu);
   int cur = 0;
   cudaGetDevice(&cur);

@@ -112,6 +112,9 @@ class Server:
         self.charge = getattr(executor, "charge", lambda r: r.nbytes)
         self.budget = Budget(budget_bytes)
         self.max_batch = max_batch
+        # bytes a request adds to a micro-batch, and the cap on their sum
+        self.batch_bytes = getattr(executor, "batch_bytes", lambda r: r.nbytes)
+        self.batch_cap = getattr(executor, "max_batch_bytes", None)
         self.max_in_flight = max_in_flight
 
     def run(self, requests: list[ServeRequest], timeout_s: float = 600.0,
@@ -147,10 +150,16 @@ class Server:
                 else:
                     still.append((token, reqs))
             in_flight = still
-            # admit in arrival order while the budget allows
+            # admit in arrival order while the budget (and the executor's
+            # micro-batch size, if it has one) allows
             batch = []
+            bbytes = 0
             if len(in_flight) < self.max_in_flight:
-                while waiting and len(batch) < self.max_batch and self.budget.try_take(self.charge(waiting[0])):
+                while (waiting and len(batch) < self.max_batch
+                       and (not batch or self.batch_cap is None
+                            or bbytes + self.batch_bytes(waiting[0]) <= self.batch_cap)
+                       and self.budget.try_take(self.charge(waiting[0]))):
+                    bbytes += self.batch_bytes(waiting[0])
                     r = waiting.popleft()
                     r.admitted_s = now
                     r.out = self.ex.alloc_out(r)
@@ -266,89 +275,102 @@ class GpuExecutor:
 
 class HostCopyExecutor(GpuExecutor):
     """GpuExecutor for requests whose ``src`` is a pinned HOST image (a dense
-    2-D CPU tensor).  Each request takes a device input and a device output
-    buffer and a pinned host output buffer, all pooled in power-of-two size
-    classes (a warm server allocates nothing); ``launch`` queues on the
-    micro-batch's stream the copies in (one morph_copy_batch call for the
-    whole micro-batch), the batch (morph_batch), the copies out (one more
-    morph_copy_batch call) and the completion event."""
+    2-D CPU tensor).  A micro-batch takes one device block for its inputs,
+    one for its outputs and one pinned host block for the results, each
+    request at a 256-byte aligned offset, from torch's caching allocators
+    (device blocks on the micro-batch's stream; pinned blocks from the host
+    cache, warmed at construction for the block sizes a micro-batch of at
+    most ``max_batch_bytes`` needs), so a warm server does not allocate.
+    ``launch`` queues on the micro-batch's stream the copies in (one
+    morph_copy_batch call for all requests), the batch (morph_batch), one
+    copy of the whole output block back to the host block, and the
+    completion event; the blocks go back to the caches when the batch's last
+    request finishes."""
 
     def __init__(self, device="cuda", n_streams: int = 4, pool_cap: int = 4 << 30,
-                 host_pool_cap: int = 4 << 30):
+                 max_batch_bytes: int = 256 << 20):
         super().__init__(device=device, n_streams=n_streams, pool_cap=pool_cap)
-        self.host_free = collections.defaultdict(list)
-        self.host_pooled = 0
-        self.host_pool_cap = host_pool_cap
+        self.max_batch_bytes = max_batch_bytes
+        self.blocks = {}  # batch id -> [tensors, requests not finished]
+        self.next_batch = 0
+        torch = self.torch
+        # the host cache keeps freed pinned blocks by power-of-two size:
+        # allocate (and free) a few of every size a micro-batch may take
+        warm = []
+        c = 1 << 16
+        while c <= 2 * max_batch_bytes:
+            warm += [torch.empty(c, dtype=torch.uint8, pin_memory=True) for _ in range(2 * n_streams)]
+            c *= 2
+        del warm
+
+    @staticmethod
+    def _padded(r: ServeRequest) -> int:
+        return (r.width * r.height * r.dtype_size + 255) // 256 * 256
 
     def charge(self, r: ServeRequest) -> int:
-        """Device input and output buffers' size classes and the scratch."""
-        return 2 * self.size_class(r.width * r.height * r.dtype_size) + self.scratch_bytes(r)
+        """Device input and output bytes (256-byte padded) and the scratch."""
+        return 2 * self._padded(r) + self.scratch_bytes(r)
 
-    def _dev(self, c):
-        if self.free[c]:
-            self.pooled -= c
-            return self.free[c].pop()
-        return self.torch.empty(c, dtype=self.torch.uint8, device=self.device)
-
-    def _host(self, c):
-        if self.host_free[c]:
-            self.host_pooled -= c
-            return self.host_free[c].pop()
-        return self.torch.empty(c, dtype=self.torch.uint8).pin_memory()
+    def batch_bytes(self, r: ServeRequest) -> int:
+        """What a request adds to a micro-batch's blocks."""
+        return self._padded(r)
 
     def alloc_out(self, r: ServeRequest):
-        c = self.size_class(r.width * r.height * r.dtype_size)
-        return (None, (self._dev(c), self._dev(c), self._host(c)))
+        return None  # the micro-batch's blocks are taken in launch()
 
     def finish(self, r: ServeRequest) -> None:
-        out, (din, dout, hout) = r.out
+        out, bid = r.out
         if self.keep is not None:
             self.keep[r.rid] = out.clone()  # host memory, complete at the event
-        c = din.numel()
-        for b in (din, dout):
-            if self.pooled + c <= self.pool_cap:
-                self.free[c].append(b)
-                self.pooled += c
-        if self.host_pooled + c <= self.host_pool_cap:
-            self.host_free[c].append(hout)
-            self.host_pooled += c
+        blk = self.blocks[bid]
+        blk[1] -= 1
+        if blk[1] == 0:
+            del self.blocks[bid]
         r.out = None
 
     def launch(self, reqs, stream_index: int):
         m, torch = self.morph, self.torch
         s = self.streams[stream_index]
         sh = s.cuda_stream
+        offs, total = [], 0
+        for r in reqs:
+            offs.append(total)
+            total += self._padded(r)
+        with torch.cuda.stream(s):
+            din = torch.empty(total, dtype=torch.uint8, device=self.device)
+            dout = torch.empty(total, dtype=torch.uint8, device=self.device)
+        hout = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+        bid = self.next_batch
+        self.next_batch += 1
+        self.blocks[bid] = [(din, dout, hout), len(reqs)]
         n = len(reqs)
-        cin = (m.MorphCopyDesc * n)()
-        cout = (m.MorphCopyDesc * n)()
+        copies = (m.MorphCopyDesc * n)()
         descs = (m.MorphDesc * n)()
+        di, do = din.data_ptr(), dout.data_ptr()
         code = {1: m.MORPH_U8, 2: m.MORPH_U16}
-        for ci, co, d, r in zip(cin, cout, descs, reqs):
-            _, (din, dout, hout) = r.out
+        for c, d, r, off in zip(copies, descs, reqs, offs):
             row = r.width * r.dtype_size
-            nb = row * r.height
-            di, do = din.data_ptr(), dout.data_ptr()
-            ci.dst, ci.src, ci.bytes = di, r.src.data_ptr(), nb
-            co.dst, co.src, co.bytes = hout.data_ptr(), do, nb
-            d.src, d.dst = di, do
+            c.dst, c.src, c.bytes = di + off, r.src.data_ptr(), row * r.height
+            d.src, d.dst = di + off, do + off
             d.width, d.height = r.width, r.height
             d.src_pitch = d.dst_pitch = row
             d.wx, d.wy, d.anchor_x, d.anchor_y = r.wx, r.wy, r.ax, r.ay
             d.op = r.op
             d.dtype = code[r.dtype_size]
-            v = hout[:nb]
-            if r.dtype_size == 2:
-                v = v.view(torch.uint16)
-            r.out = (v.view(r.height, r.width), r.out[1])
-        rc = m.morph_copy_batch(cin, n, sh)
+        rc = m.morph_copy_batch(copies, n, sh)
         if rc != 0:
             raise m.MorphError("morph_copy_batch", rc)
         rc = m.morph_batch(descs, n, sh)
         if rc != 0:
             raise m.MorphError("morph_batch", rc)
-        rc = m.morph_copy_batch(cout, n, sh)
+        rc = m.morph_copy_2d(hout.data_ptr(), total, do, total, total, 1, sh)
         if rc != 0:
-            raise m.MorphError("morph_copy_batch", rc)
+            raise m.MorphError("morph_copy_2d", rc)
+        for r, off in zip(reqs, offs):
+            v = hout[off:off + r.width * r.height * r.dtype_size]
+            if r.dtype_size == 2:
+                v = v.view(torch.uint16)
+            r.out = (v.view(r.height, r.width), bid)
         ev = torch.cuda.Event()
         ev.record(s)
         return ev
