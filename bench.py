@@ -546,7 +546,10 @@ def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0, host_copies
     admission budget.  Inputs pre-staged in device memory (host-to-device
     copies excluded), or, with host_copies, pinned host images copied in and
     results copied back to pinned host buffers inside each request's latency
-    (HostCopyExecutor).  A short run at the same rate warms the pools first."""
+    (HostCopyExecutor).  A short run at the same rate warms the pools first;
+    the timed requests are generated before it, so that the timed run starts
+    on a busy GPU (an idle GPU's clocks take tens of milliseconds to come
+    back up)."""
     from paper_2002_09474_gb300 import serve
     if host_copies:
         pool_img, pool_dev = serve.host_arena(torch, seed=6)
@@ -558,9 +561,9 @@ def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0, host_copies
         make = serve.make_requests
     out = []
     for rate in rates:
+        rs = make(rate, duration_s, pool_img, pool_dev, seed=6)
         warm = make(rate, min(0.5, duration_s), pool_img, pool_dev, seed=60)
         serve.Server(ex, budget_bytes=4 << 30).run(warm, timeout_s=300)
-        rs = make(rate, duration_s, pool_img, pool_dev, seed=6)
         st = serve.Server(ex, budget_bytes=4 << 30).run(rs, timeout_s=300)
         torch.cuda.synchronize()
         d = st.summary()

@@ -209,8 +209,13 @@ typedef struct {
  * windows and of 2-D windows above the crossover in one batched launch of
  * the pass-along-x kernel (the 2-D ones into intermediate images); the
  * passes along y of 1-D windows and of those 2-D windows in batched
- * launches of the pass-along-y kernel (one per tile-size class).  Each image
- * gets exactly the bytes of its single call.  The descriptor array is on the
+ * launches of the pass-along-y kernel (one per tile-size class).  An image
+ * whose pass above the crossover reads a source those kernels cannot load
+ * fast (rows not aligned to 8 pixels, base and pitch, for the pass along x;
+ * base or pitch not a multiple of 16 bytes for the pass along y) runs as
+ * its single call instead, after the batched launches, as do images above
+ * the size set by morph_set_batch_alone.  Each image gets exactly the bytes
+ * of its single call.  The descriptor array is on the
  * host; the call copies it (and the derived records) to a stream-ordered
  * device block (from the library's stream-ordered pool on `stream`, which
  * also holds the intermediates) through the library's pinned staging buffers, so descs may

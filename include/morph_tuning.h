@@ -143,6 +143,16 @@ int morph_set_row_kernel(int mode);
  */
 int morph_set_xpass(int dtype, int mode);
 
+/*
+ * Images of morph_batch and morph_batch_plan_create with at least
+ * min_pixels pixels run as their single call (morph_apply's launches, on the
+ * batch's stream after the batched launches), besides those that always do
+ * (see morph_batch); the rest share the batched launches.  0 (the default):
+ * no size rule; negative: the default.  The result never changes.  Returns
+ * MORPH_OK.
+ */
+int morph_set_batch_alone(long long min_pixels);
+
 #ifdef __cplusplus
 }
 #endif

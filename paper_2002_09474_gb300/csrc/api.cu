@@ -136,7 +136,11 @@ struct Scratch {
 bool use_colv(const FusedLaunch& L) {
   const int m = tuning().colv_mode;
   if (m == 0) return false;
-  return (m >= 1 || L.vhgw_col) && colv_fits(L);
+  // in auto mode only on sources TMA can describe: its plain loads are
+  // latency-bound at its occupancy (GB300, 1 x 101 at 4096^2, u8: 10.6 us
+  // aligned, 138 us from an unaligned base, where the column kernel takes
+  // 20.7 us)
+  return (m >= 1 || (L.vhgw_col && tma_loadable(L.src, L.sp))) && colv_fits(L);
 }
 bool use_rowv(const FusedLaunch& L) {
   const int m = tuning().rowv_mode;
@@ -451,6 +455,38 @@ struct BatchPlan {
   cudaGraphExec_t exec = nullptr;
 };
 
+namespace {
+
+// Takes out of a planned batch `in` the images that run as their own single
+// call (batch_runs_alone, or at least the tuned number of pixels); their
+// descriptor indices go to `alone`, and `in` keeps the rest, in order, for
+// the batched launches.
+void split_alone(const morph_desc* d, std::vector<BatchImageIn>* in, std::vector<int>* alone) {
+  const long long lim = tuning().batch_alone;
+  size_t k = 0;
+  for (size_t i = 0; i < in->size(); ++i) {
+    if ((lim > 0 && static_cast<long long>(d[i].width) * d[i].height >= lim) || batch_runs_alone((*in)[i].L)) {
+      alone->push_back(static_cast<int>(i));
+    } else {
+      (*in)[k++] = (*in)[i];
+    }
+  }
+  in->resize(k);
+}
+
+// The single calls of the images split off above, on `st`.
+int run_alone(const morph_desc* d, const std::vector<int>& alone, cudaStream_t st) {
+  for (int i : alone) {
+    const morph_desc& e = d[i];
+    const int rc = run_single(e.src, static_cast<size_t>(e.src_pitch), e.dst, static_cast<size_t>(e.dst_pitch),
+                              e.width, e.height, e.dtype, e.op, e.wx, e.wy, e.anchor_x, e.anchor_y, st);
+    if (rc != MORPH_OK) return rc;
+  }
+  return MORPH_OK;
+}
+
+}  // namespace
+
 }  // namespace morph
 
 // ---------------------------------------------------------------------------
@@ -588,22 +624,27 @@ int morph_batch(const morph_desc* descs_host, int n, void* stream) {
   std::vector<BatchImageIn> in;
   int rc = plan_batch(descs_host, n, &in);
   if (rc != MORPH_OK) return rc;
-  BatchHost h;
-  if (batch_prepare(in.data(), n, &h) != 0) return MORPH_ERR_WINDOW;
-  if (batch_configure(&h) != cudaSuccess) return MORPH_ERR_CUDA;
-  const BatchDev L = batch_dev_layout(h);
+  std::vector<int> alone;
+  split_alone(descs_host, &in, &alone);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // Stream-ordered scratch from the library's pool (records, then the 2-D
-  // images' intermediates): allocated and freed in the stream's order, so
-  // concurrent batches on different streams never share it.
-  void* dmem = nullptr;
-  if (scratch_malloc(&dmem, L.bytes, st) != cudaSuccess) return MORPH_ERR_NOMEM;
-  uint8_t* base = static_cast<uint8_t*>(dmem);
-  batch_bind_intermediates(base + L.inter_off, &h);
-  cudaError_t e = upload_batch(h, L, base, st);
-  if (e == cudaSuccess) e = batch_enqueue(h, base, L, st);
-  cudaFreeAsync(dmem, st);
-  return e == cudaSuccess ? MORPH_OK : MORPH_ERR_CUDA;
+  if (!in.empty()) {
+    BatchHost h;
+    if (batch_prepare(in.data(), static_cast<int>(in.size()), &h) != 0) return MORPH_ERR_WINDOW;
+    if (batch_configure(&h) != cudaSuccess) return MORPH_ERR_CUDA;
+    const BatchDev L = batch_dev_layout(h);
+    // Stream-ordered scratch from the library's pool (records, then the 2-D
+    // images' intermediates): allocated and freed in the stream's order, so
+    // concurrent batches on different streams never share it.
+    void* dmem = nullptr;
+    if (scratch_malloc(&dmem, L.bytes, st) != cudaSuccess) return MORPH_ERR_NOMEM;
+    uint8_t* base = static_cast<uint8_t*>(dmem);
+    batch_bind_intermediates(base + L.inter_off, &h);
+    cudaError_t e = upload_batch(h, L, base, st);
+    if (e == cudaSuccess) e = batch_enqueue(h, base, L, st);
+    cudaFreeAsync(dmem, st);
+    if (e != cudaSuccess) return MORPH_ERR_CUDA;
+  }
+  return run_alone(descs_host, alone, st);
 }
 
 int morph_batch_plan_create(const morph_desc* descs_host, int n, void** plan) {
@@ -612,9 +653,11 @@ int morph_batch_plan_create(const morph_desc* descs_host, int n, void** plan) {
   std::vector<BatchImageIn> in;
   int rc = plan_batch(descs_host, n, &in);
   if (rc != MORPH_OK) return rc;
+  std::vector<int> alone;
+  split_alone(descs_host, &in, &alone);
   BatchPlan* p = new BatchPlan();
   cudaGetDevice(&p->device);
-  if (batch_prepare(in.data(), n, &p->host) != 0) {
+  if (batch_prepare(in.data(), static_cast<int>(in.size()), &p->host) != 0) {
     delete p;
     return MORPH_ERR_WINDOW;
   }
@@ -636,9 +679,14 @@ int morph_batch_plan_create(const morph_desc* descs_host, int n, void** plan) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
+    // the large images' single calls join the graph (their scratch images
+    // become allocation nodes of it)
     cudaError_t le = batch_enqueue(p->host, base, L, cs);
+    int arc = MORPH_OK;
+    if (le == cudaSuccess) arc = run_alone(descs_host, alone, cs);
     e = cudaStreamEndCapture(cs, &p->graph);
     if (le != cudaSuccess) e = le;
+    else if (arc != MORPH_OK && e == cudaSuccess) e = cudaErrorUnknown;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
   if (cs) cudaStreamDestroy(cs);
@@ -696,6 +744,11 @@ int morph_set_pdl(int on) {
 int morph_set_split(int mode) {
   if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
   tuning().split_mode = mode;
+  return MORPH_OK;
+}
+
+int morph_set_batch_alone(long long min_pixels) {
+  tuning().batch_alone = min_pixels < 0 ? kBatchAlonePixels : min_pixels;
   return MORPH_OK;
 }
 

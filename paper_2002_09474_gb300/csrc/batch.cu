@@ -168,15 +168,31 @@ int esz_code(int dtype) { return dtype == MORPH_U8 ? 1 : dtype == MORPH_U16 ? 2 
 
 // ---- host side -----------------------------------------------------------------
 
-// Arguments of the pass along x in a batch: kBatchRR rows per warp task and
-// whole rows per segment (the batch supplies the parallelism); false where
-// the kernel does not take the launch (9 <= wx <= 256, wy = 1, rows aligned
-// to 8 bytes per pixel byte).
-bool rowv_batch_args(const FusedLaunch& L, RowvArgs* a) {
+// SMs of the current device (looked up once per device).
+static int batch_sms() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!sms[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    sms[dev] = n;
+  }
+  return sms[dev];
+}
+
+// Arguments of the pass along x in a batch: kBatchRR rows per warp task,
+// whole rows per task, or, with fill_gpu (a batch with too few tasks to fill
+// the GPU), segments as a single call of the image would take them on the
+// batched kernel's residency (4 warps a CTA, 8 CTAs an SM); false where the
+// kernel does not take the launch (9 <= wx <= 256, wy = 1, rows aligned to
+// 8 bytes per pixel byte).
+bool rowv_batch_args(const FusedLaunch& L, RowvArgs* a, bool fill_gpu) {
   const int al = 8 * L.esz;
   if (L.wx < 9 || L.wx > 256 || L.wy != 1) return false;
   if (reinterpret_cast<uintptr_t>(L.src) % al || L.sp % al) return false;
-  const RowvPlan p = rowv_plan(L.W, L.H, kBatchRR, 1, 1, L.W);
+  const RowvPlan p = fill_gpu ? rowv_plan(L.W, L.H, kBatchRR, batch_sms(), kBatchRowvWps, 0)
+                              : rowv_plan(L.W, L.H, kBatchRR, 1, 1, L.W);
   if (!p.ok) return false;
   memset(a, 0, sizeof(*a));
   a->src = static_cast<const uint8_t*>(L.src);
@@ -195,10 +211,15 @@ bool rowv_batch_args(const FusedLaunch& L, RowvArgs* a) {
 }
 
 // Arguments of the pass along y in a batch: one warp per CTA, 4 bytes per
-// lane, the built-in tile height; false where its warp tile does not fit.
-bool colv_batch_args(const FusedLaunch& L, ColvArgs* a, CUtensorMap* map) {
+// lane, the built-in tile height (with fill_gpu, shorter where the image has
+// too few tiles to fill the GPU, as a single call's); false where its warp
+// tile does not fit or its source is not one TMA can load (base and pitch
+// multiples of 16 bytes: the kernel's plain loads are latency-bound at its
+// one-warp-per-CTA occupancy).
+bool colv_batch_args(const FusedLaunch& L, ColvArgs* a, CUtensorMap* map, bool fill_gpu) {
   if (L.wy < 2 || L.wx != 1) return false;
-  const ColvPlan p = colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, 0, 4, 0);
+  if (!tma_loadable(L.src, L.sp)) return false;
+  const ColvPlan p = colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, 0, 4, fill_gpu ? batch_sms() : 0);
   if (!p.ok || p.nbox > kCvMaxBox) return false;
   memset(a, 0, sizeof(*a));
   a->src = static_cast<const uint8_t*>(L.src);
@@ -354,6 +375,21 @@ int batch_form(const FusedLaunch& L) {
   return kFormFused;
 }
 
+}  // namespace
+
+bool batch_runs_alone(const FusedLaunch& L) {
+  // a pass that takes van Herk/Gil-Werman whose source the batched
+  // single-pass kernels cannot load fast: its single call has kernels that
+  // can (the row and column kernels), where the fused kernel's tile would
+  // carry the window's whole halo
+  const bool vx = L.wx > 1 && L.vhgw_row, vy = L.wy > 1 && L.vhgw_col;
+  if (!vx && !vy) return false;
+  if (L.wx > 1 && L.wy > 1 && (!vx || !vy)) return false;  // a direct pass: the fused kernel
+  return batch_form(L) == kFormFused;
+}
+
+namespace {
+
 int colv_class(int nbox) {
   for (int c = 0; c < kColvClasses; ++c)
     if (nbox <= kColvClassBoxes[c]) return c;
@@ -364,6 +400,25 @@ int colv_class(int nbox) {
 
 int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
   *out = BatchHost();
+  // Forms, and the warp tasks of the single-pass groups in their long-task
+  // shapes (whole rows; the built-in tile height): a group whose tasks do
+  // not fill the GPU takes the shorter tasks a single call would.
+  std::vector<int> forms(n);
+  long long tx = 0, ty = 0, ty_slots = 0;
+  for (int i = 0; i < n; ++i) {
+    const FusedLaunch& L = in[i].L;
+    forms[i] = batch_form(L);
+    if (forms[i] == kFormFused) continue;
+    if (forms[i] != kFormY) tx += (L.H + kBatchRR - 1) / kBatchRR;
+    if (forms[i] != kFormX) {
+      const ColvPlan p = colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, 0, 4, 0);
+      if (!p.ok) return -1;
+      ty += static_cast<long long>(cdiv(L.W * L.esz, colv_strip_bytes(4))) * cdiv(L.H, p.L);
+      ty_slots = std::max<long long>(ty_slots, static_cast<long long>(batch_sms()) * p.wps);
+    }
+  }
+  const bool fill_x = tx < static_cast<long long>(batch_sms()) * kBatchRowvWps;
+  const bool fill_y = 5 * ty < 3 * ty_slots;
   std::vector<const FusedLaunch*> fused;
   std::vector<BatchColv> cols_by_class[kColvClasses];
   std::vector<CUtensorMap> maps_by_class[kColvClasses];
@@ -371,7 +426,7 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
   size_t inter = 0;
   for (int i = 0; i < n; ++i) {
     const FusedLaunch& L = in[i].L;
-    const int form = batch_form(L);
+    const int form = forms[i];
     if (form == kFormFused) {
       fused.push_back(&L);
       continue;
@@ -384,7 +439,7 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
         A.dst = reinterpret_cast<void*>(static_cast<uintptr_t>(256));
         A.dp = static_cast<long long>(inter_pitch(L));
       }
-      if (!rowv_batch_args(A, &r.a)) return -1;
+      if (!rowv_batch_args(A, &r.a, fill_x)) return -1;
       r.esz = L.esz;
       r.op = L.op;
       r.task0 = out->row_tasks;
@@ -401,7 +456,7 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
         B.src = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
         B.sp = static_cast<long long>(inter_pitch(L));
       }
-      if (!colv_batch_args(B, &c.a, &m)) return -1;
+      if (!colv_batch_args(B, &c.a, &m, fill_y)) return -1;
       c.esz = L.esz;
       c.op = L.op;
       const int k = colv_class(c.a.nbox);

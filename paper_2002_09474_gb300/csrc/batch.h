@@ -40,8 +40,10 @@ struct BatchColv {
 // memory sized for the class's largest warp tile.
 constexpr int kColvClasses = 4;
 constexpr int kColvClassBoxes[kColvClasses] = {2, 4, 8, kCvMaxBox};
-// Rows per warp of the pass-along-x group.
+// Rows per warp of the pass-along-x group, and its resident warps per SM
+// (4 warps a CTA, 8 CTAs an SM).
 constexpr int kBatchRR = 2;
+constexpr int kBatchRowvWps = 32;
 
 // Host-side layout of a batch.  Images are split into three groups by the
 // form a single call would take: windows whose passes take the direct method
@@ -126,8 +128,22 @@ cudaError_t batch_fused_grid(int cfg, int smem, int ntiles, int* grid, int** err
 void fill_img_args(const FusedLaunch& L, const Geom& g, int TX, int TY, ImgArgs* a, CUtensorMap* tin,
                    CUtensorMap* tout);
 
-// Shared with the single-pass launchers: the arguments of one launch.
-bool rowv_batch_args(const FusedLaunch& L, RowvArgs* a);
-bool colv_batch_args(const FusedLaunch& L, ColvArgs* a, CUtensorMap* map);
+// The arguments of one image's pass in the batched single-pass kernels;
+// fill_gpu: shorter tasks, for a group too small to fill the GPU.
+bool rowv_batch_args(const FusedLaunch& L, RowvArgs* a, bool fill_gpu = false);
+bool colv_batch_args(const FusedLaunch& L, ColvArgs* a, CUtensorMap* map, bool fill_gpu = false);
+
+// Whether a planned image runs as its own single call instead of in the
+// batched launches: a pass by van Herk/Gil-Werman whose source the batched
+// single-pass kernels cannot load fast (rows not aligned for the
+// pass-along-x kernel's vector loads, or not describable by TMA for the
+// pass along y).
+bool batch_runs_alone(const FusedLaunch& L);
+
+// Whether TMA can describe an image at src with rows of pitch bytes: base
+// and pitch multiples of 16 bytes.
+inline bool tma_loadable(const void* src, long long pitch) {
+  return reinterpret_cast<uintptr_t>(src) % 16 == 0 && pitch % 16 == 0;
+}
 
 }  // namespace morph

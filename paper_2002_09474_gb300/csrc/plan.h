@@ -27,6 +27,7 @@ struct Tuning {
   int rowv_rr[2];                 // [esz-1]: rows per warp of the pass along x (0: built-in, 2)
   int fused_cfg_tuned[2][4];      // [esz-1][window class]: measured tile shape of the fused kernel, -1 none
   int colv_fam_tuned[2][5];       // [esz-1][window class]: measured tile-height choice of the pass along y, -1 none
+  long long batch_alone;          // batch images of at least this many pixels run as their single call (0: none)
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 
@@ -40,6 +41,12 @@ int colv_tune_class(int wy);
 // built-in rule, 1..3 that many windows, 4..6 64, 128 or 256 rows.
 constexpr int kColvFamilies = 7;
 int colv_family_rows(int fam, int wy);
+
+// Default of the size above which images of a batch run as their own
+// single call: none (0).  Measured on the GB300 with 2000 images of 64 to
+// 2048 pixels a side (128-byte pitched rows): every image in the batched
+// launches 376 Gpixel/s, images of at least 2^20 pixels as single calls 253.
+constexpr long long kBatchAlonePixels = 0;
 
 Tuning& tuning();
 void reset_tuning_defaults();

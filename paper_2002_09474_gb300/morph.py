@@ -95,6 +95,7 @@ _SIGS = {
     "morph_set_colv": [_i32, _i32, _i32],
     "morph_set_rowv": [_i32, _i32],
     "morph_set_xpass": [_i32, _i32],
+    "morph_set_batch_alone": [ctypes.c_longlong],
     "morph_device_error": [],
     "morph_launch_count": [],
 }
@@ -259,6 +260,10 @@ def morph_set_rowv(mode, seg=0):
 
 def morph_set_xpass(dtype, mode):
     return _lib.morph_set_xpass(dtype, mode)
+
+
+def morph_set_batch_alone(min_pixels):
+    return _lib.morph_set_batch_alone(min_pixels)
 
 
 def morph_reset_tuning():

@@ -39,7 +39,10 @@ def test_batch_every_form(env):
     windows, small images), the pass along x alone (wx x 1), the pass along y
     alone (1 x wy), and both through an intermediate (2-D windows above the
     crossovers) -- u8 and u16, tight and padded pitches, anchor extremes --
-    each compared with the oracle, through morph_batch and the graph plan."""
+    each compared with the oracle, through morph_batch and the graph plan.
+    Sources and destinations start at offsets of 0-2 pixels from an aligned
+    address, with pitches aligned or not: a 2-D window whose source rows the
+    pass-along-x kernel cannot load runs its pass along y first."""
     torch, morph = env
     g = synth.rng(71)
     cases = []
@@ -50,18 +53,19 @@ def test_batch_every_form(env):
                 ax, ay = [int(g.integers(0, k)) for k in (wx, wy)]
                 op = int(g.integers(0, 2))
                 pad = (16 - (w * esz) % 16) % 16 if (w + wx) % 2 else 3 * esz
-                cases.append((dt, w, h, wx, wy, ax, ay, op, pad))
+                so, do = [esz * int(g.integers(0, 3)) for _ in range(2)]
+                cases.append((dt, w, h, wx, wy, ax, ay, op, pad, so, do))
     imgs, srcs, outs = [], [], []
     arr = (morph.MorphDesc * len(cases))()
-    for d, (dt, w, h, wx, wy, ax, ay, op, pad) in zip(arr, cases):
+    for d, (dt, w, h, wx, wy, ax, ay, op, pad, so, do) in zip(arr, cases):
         esz = np.dtype(dt).itemsize
         img = synth.uniform_image(w, h, dt, gen=g)
         pitch = w * esz + pad
         src = torch.zeros(h * pitch + 64, dtype=torch.uint8, device="cuda")
-        view = src[:h * pitch].view(h, pitch)[:, :w * esz]
+        view = src[so:so + h * pitch].view(h, pitch)[:, :w * esz]
         view.copy_(torch.from_numpy(img.view(np.uint8).reshape(h, w * esz)).cuda())
         out = torch.full((h * pitch + 64,), 0x5A, dtype=torch.uint8, device="cuda")
-        d.src, d.dst, d.width, d.height = src.data_ptr(), out.data_ptr(), w, h
+        d.src, d.dst, d.width, d.height = src.data_ptr() + so, out.data_ptr() + do, w, h
         d.src_pitch = d.dst_pitch = pitch
         d.wx, d.wy, d.anchor_x, d.anchor_y, d.op = wx, wy, ax, ay, op
         d.dtype = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
@@ -72,15 +76,16 @@ def test_batch_every_form(env):
     def check():
         torch.cuda.synchronize()
         assert morph.morph_device_error() == 0
-        for (dt, w, h, wx, wy, ax, ay, op, pad), img, out in zip(cases, imgs, outs):
+        for (dt, w, h, wx, wy, ax, ay, op, pad, so, do), img, out in zip(cases, imgs, outs):
             esz = np.dtype(dt).itemsize
             pitch = w * esz + pad
             host = out.cpu().numpy()
-            got = host[:h * pitch].reshape(h, pitch)[:, :w * esz].copy().view(dt)
+            got = host[do:do + h * pitch].reshape(h, pitch)[:, :w * esz].copy().view(dt)
             want = oracle.morph(img, wx, wy, ax, ay, OPS[op])
-            assert np.array_equal(got, want), (dt.__name__, w, h, wx, wy, ax, ay, op, pad)
-            rest = host[:h * pitch].reshape(h, pitch)[:, w * esz:]
-            assert (rest == 0x5A).all() and (host[h * pitch:] == 0x5A).all(), "wrote outside the image"
+            assert np.array_equal(got, want), (dt.__name__, w, h, wx, wy, ax, ay, op, pad, so, do)
+            rest = host[do:do + h * pitch].reshape(h, pitch)[:, w * esz:]
+            assert (rest == 0x5A).all() and (host[do + h * pitch:] == 0x5A).all() and (host[:do] == 0x5A).all(), \
+                "wrote outside the image"
             out.fill_(0x5A)
 
     assert morph.morph_batch(arr, len(cases), 0) == 0
@@ -94,6 +99,49 @@ def test_batch_every_form(env):
             check()
     finally:
         assert morph.morph_batch_plan_destroy(plan) == 0
+
+
+def test_batch_two_pass_forms_on_large_images(env):
+    """2-D windows above the crossovers on images of 2 Mpixels: with source
+    rows the batched pass-along-x kernel can load, the image takes the
+    batched two-pass form; otherwise (unaligned base or pitch) it runs as
+    its single call.  Either way a single-image batch is two launches,
+    equals the single call, and matches the oracle (the separable checker in
+    full, the brute force at sample points)."""
+    torch, morph = env
+    g = synth.rng(72)
+    cases = [(np.uint8, 1536, 1400, 21, 51, 0, 0), (np.uint8, 1537, 1400, 21, 51, 1, 3),
+             (np.uint16, 1500, 1450, 99, 37, 0, 0), (np.uint16, 1501, 1450, 99, 37, 2, 6)]
+    _two_pass_cases(torch, morph, g, cases)
+
+
+def _two_pass_cases(torch, morph, g, cases):
+    for k, (dt, w, h, wx, wy, so, do) in enumerate(cases):
+        esz = np.dtype(dt).itemsize
+        img = synth.uniform_image(w, h, dt, gen=g)
+        pitch = w * esz
+        src = torch.zeros(h * pitch + 64, dtype=torch.uint8, device="cuda")
+        src[so:so + h * pitch].copy_(torch.from_numpy(img.view(np.uint8).reshape(-1)).cuda())
+        outs = [torch.full((h * pitch + 64,), 0x5A, dtype=torch.uint8, device="cuda") for _ in range(2)]
+        ax, ay, op = wx // 3, wy - 1, k % 2
+        dtype = morph.MORPH_U8 if dt == np.uint8 else morph.MORPH_U16
+        d = morph.MorphDesc()
+        d.src, d.dst, d.width, d.height = src.data_ptr() + so, outs[0].data_ptr() + do, w, h
+        d.src_pitch = d.dst_pitch = pitch
+        d.wx, d.wy, d.anchor_x, d.anchor_y, d.op, d.dtype = wx, wy, ax, ay, op, dtype
+        torch.cuda.synchronize()
+        n0 = morph.morph_launch_count()
+        assert morph.morph_batch((morph.MorphDesc * 1)(d), 1, 0) == 0
+        assert morph.morph_launch_count() - n0 == 2, "not the two-pass form"
+        assert morph.morph_apply(src.data_ptr() + so, pitch, outs[1].data_ptr() + do, pitch, w, h, dtype, op,
+                                 wx, wy, ax, ay, 0) == 0
+        torch.cuda.synchronize()
+        assert morph.morph_device_error() == 0
+        assert torch.equal(outs[0], outs[1])
+        host = outs[0].cpu().numpy()
+        assert (host[:do] == 0x5A).all() and (host[do + h * pitch:] == 0x5A).all()
+        got = host[do:do + h * pitch].copy().view(dt).reshape(h, w)
+        check_sample(img, got, wx, wy, ax, ay, op, seed=720 + k)
 
 
 def test_batch_2000_images_graph_plan(env):
