@@ -53,6 +53,8 @@ class ServeRequest:
     admitted_s: float = -1.0
     done_s: float = -1.0
     out: object = None
+    charge_bytes: int = -1        # budget charge (computed once, at arrival)
+    batch_bytes: int = -1         # bytes it adds to a micro-batch
 
     @property
     def nbytes(self) -> int:
@@ -148,7 +150,9 @@ class Server:
                 raise TimeoutError("serving loop did not drain within %.0f s" % timeout_s)
             while pending and pending[0].arrival_s <= now:
                 r = pending.popleft()
-                if self.charge(r) > self.budget.limit:  # can never fit: reject now
+                r.charge_bytes = self.charge(r)
+                r.batch_bytes = self.batch_bytes(r)
+                if r.charge_bytes > self.budget.limit:  # can never fit: reject now
                     st.rejected += 1
                     continue
                 waiting.append(r)
@@ -162,7 +166,7 @@ class Server:
                         st.latencies_ms.append((tdone - r.arrival_s) * 1e3)
                         st.completed += 1
                         st.pixels += r.width * r.height
-                        self.budget.give(self.charge(r))
+                        self.budget.give(r.charge_bytes)
                         self.ex.finish(r)
                 else:
                     still.append((token, reqs))
@@ -174,9 +178,9 @@ class Server:
             if len(in_flight) < self.max_in_flight:
                 while (waiting and len(batch) < self.max_batch
                        and (not batch or self.batch_cap is None
-                            or bbytes + self.batch_bytes(waiting[0]) <= self.batch_cap)
-                       and self.budget.try_take(self.charge(waiting[0]))):
-                    bbytes += self.batch_bytes(waiting[0])
+                            or bbytes + waiting[0].batch_bytes <= self.batch_cap)
+                       and self.budget.try_take(waiting[0].charge_bytes)):
+                    bbytes += waiting[0].batch_bytes
                     r = waiting.popleft()
                     r.admitted_s = now
                     r.out = self.ex.alloc_out(r)
@@ -292,14 +296,14 @@ class GpuExecutor:
 
 class HostCopyExecutor(GpuExecutor):
     """GpuExecutor for requests whose ``src`` is a pinned HOST image (a dense
-    2-D CPU tensor).  A micro-batch takes one device block for its inputs,
-    one for its outputs and one pinned host block for the results, each
-    request at a 256-byte aligned offset, from torch's caching allocators
+    2-D CPU tensor).  A micro-batch takes one device block for its inputs
+    and outputs and one pinned host block for the results, each request at
+    a 256-byte aligned offset, from torch's caching allocators
     (device blocks on the current stream, freed only after the micro-batch's
     completion event, so their use on another stream is safe; pinned blocks
     from the host cache, warmed at construction for the block sizes a
     micro-batch of at most ``max_batch_bytes`` needs), so a warm server does
-    not allocate.
+    not allocate; completion events are reused.
     ``launch`` queues on the micro-batch's stream the copies in (one
     morph_copy_batch call for all requests), the batch (morph_batch), one
     copy of the whole output block back to the host block, and the
@@ -310,8 +314,9 @@ class HostCopyExecutor(GpuExecutor):
                  max_batch_bytes: int = 256 << 20):
         super().__init__(device=device, n_streams=n_streams, pool_cap=pool_cap)
         self.max_batch_bytes = max_batch_bytes
-        self.blocks = {}  # batch id -> [tensors, requests not finished]
+        self.blocks = {}  # batch id -> [(device block, host block, event), requests not finished]
         self.next_batch = 0
+        self.events = []  # completion events free for reuse
         torch = self.torch
         # the host cache keeps freed pinned blocks by power-of-two size:
         # allocate (and free) a few of every size a micro-batch may take
@@ -344,6 +349,7 @@ class HostCopyExecutor(GpuExecutor):
         blk = self.blocks[bid]
         blk[1] -= 1
         if blk[1] == 0:
+            self.events.append(blk[0][2])  # completed: its event may be recorded again
             del self.blocks[bid]
         r.out = None
 
@@ -354,29 +360,29 @@ class HostCopyExecutor(GpuExecutor):
         offs, total = [], 0
         for r in reqs:
             offs.append(total)
-            total += self._padded(r)
-        # allocated on the current stream, used on s: safe because the
-        # blocks are freed only after the batch's completion event
-        din = torch.empty(total, dtype=torch.uint8, device=self.device)
-        dout = torch.empty(total, dtype=torch.uint8, device=self.device)
+            total += r.batch_bytes
+        # one device block (inputs, then outputs), allocated on the current
+        # stream and used on s: safe because it is freed only after the
+        # batch's completion event
+        dblk = torch.empty(2 * total, dtype=torch.uint8, device=self.device)
         hout = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+        ev = self.events.pop() if self.events else torch.cuda.Event()
         bid = self.next_batch
         self.next_batch += 1
-        self.blocks[bid] = [(din, dout, hout), len(reqs)]
+        self.blocks[bid] = [(dblk, hout, ev), len(reqs)]
         n = len(reqs)
         copies = (m.MorphCopyDesc * n)()
         descs = (m.MorphDesc * n)()
-        di, do = din.data_ptr(), dout.data_ptr()
-        code = {1: m.MORPH_U8, 2: m.MORPH_U16}
+        di = dblk.data_ptr()
+        do = di + total
+        u16 = m.MORPH_U16
         for c, d, r, off in zip(copies, descs, reqs, offs):
             row = r.width * r.dtype_size
             c.dst, c.src, c.bytes = di + off, r.src.data_ptr(), row * r.height
-            d.src, d.dst = di + off, do + off
-            d.width, d.height = r.width, r.height
-            d.src_pitch = d.dst_pitch = row
-            d.wx, d.wy, d.anchor_x, d.anchor_y = r.wx, r.wy, r.ax, r.ay
-            d.op = r.op
-            d.dtype = code[r.dtype_size]
+            d.src, d.dst, d.width, d.height, d.src_pitch, d.dst_pitch = di + off, do + off, r.width, r.height, row, row
+            d.wx, d.wy, d.anchor_x, d.anchor_y, d.op = r.wx, r.wy, r.ax, r.ay, r.op
+            if r.dtype_size == 2:
+                d.dtype = u16
         rc = m.morph_copy_batch(copies, n, sh)
         if rc != 0:
             raise m.MorphError("morph_copy_batch", rc)
@@ -386,12 +392,14 @@ class HostCopyExecutor(GpuExecutor):
         rc = m.morph_copy_2d(hout.data_ptr(), total, do, total, total, 1, sh)
         if rc != 0:
             raise m.MorphError("morph_copy_2d", rc)
+        h16 = None
         for r, off in zip(reqs, offs):
-            v = hout[off:off + r.width * r.height * r.dtype_size]
             if r.dtype_size == 2:
-                v = v.view(torch.uint16)
-            r.out = (v.view(r.height, r.width), bid)
-        ev = torch.cuda.Event()
+                if h16 is None:
+                    h16 = hout.view(torch.uint16)
+                r.out = (h16.as_strided((r.height, r.width), (r.width, 1), off // 2), bid)
+            else:
+                r.out = (hout.as_strided((r.height, r.width), (r.width, 1), off), bid)
         ev.record(s)
         return ev
 
