@@ -102,18 +102,22 @@ def load_peaks():
 
 
 def load_traffic(kernel_class: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    """DRAM bytes per call of a class (all its launches) from the committed
+    ncu summary, if it was taken on the current kernel sources: (back to
+    back, the way the step runs the calls; each launch after a cache flush),
+    or (None, None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
     except (OSError, ValueError):
-        return None
+        return None, None
     if t.get("kernel_hash") != kernel_hash():
-        return None
+        return None, None
     v = t.get("classes", {}).get(kernel_class)
-    return None if v is None else float(v)
+    if not isinstance(v, dict):
+        return None, None
+    return v.get("back_to_back"), v.get("cache_flushed")
 
 
 # ---------------------------------------------------------------------------
@@ -775,6 +779,7 @@ def run_gpu(args):
                                                         duration_s=args.serving_seconds, host_copies=True)
 
     if rank == 0:
+        traffic_b2b, traffic_cold = load_traffic(dom[0])
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
@@ -784,7 +789,10 @@ def run_gpu(args):
                 "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": round(dom[1], 1),
                              "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                              "frac": round(dom[1] / peak, 4),
-                             "traffic": load_traffic(dom[0])},
+                             "traffic": traffic_b2b, "traffic_cache_flushed": traffic_cold,
+                             "traffic_note": "DRAM read+write bytes per call of the class (both launches), "
+                                             "ncu: back to back as the step runs them (--cache-control "
+                                             "none), and with caches flushed before each launch"},
                 "e2e": {"value": round(e2e_px / e2e_s / 1e9, 3), "unit": UNIT,
                         "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
                         "api": "morph_apply_host_batch (the step's 32 images, copies overlapped "

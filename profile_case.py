@@ -2,7 +2,7 @@
 profiler captures of a single kernel, e.g.
 
   python profile_case.py --dtype u8 --wx 1 --wy 101 --op erode --reps 3
-  ncu --clock-control none -k regex:ystream -s 2 -c 1 --set full -o prof \
+  ncu --clock-control none -k regex:colv_kernel -s 2 -c 1 --set full -o prof \
       python profile_case.py --dtype u8 --wx 1 --wy 101 --reps 3
 
 Inputs are seeded uniform images; nothing is checked or printed except a
@@ -38,7 +38,7 @@ def main(argv=None):
     ap.add_argument("--rowv", type=int, default=-1,
                     help="force the register-blocked pass along x with this segment (0: model)")
     ap.add_argument("--colv-lanes", type=int, default=0,
-                    help="bytes per lane of the warp-tiled pass along y (0: built-in rule; 2, 4, 8)")
+                    help="bytes per lane of the warp-tiled pass along y (0: built-in rule; 4 or 8)")
     args = ap.parse_args(argv)
 
     import torch
