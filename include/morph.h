@@ -128,12 +128,17 @@ int morph_apply(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
  *   MORPH_GRADIENT  dilate(S) - erode(S), both by the same element and
  *                   anchor (never negative)
  * Arguments as in morph_apply (kind replaces op; the anchor is the first
- * step's).  The library allocates one scratch image of width x height pixels
- * (pitch rounded to 16 bytes) from the library's stream-ordered pool on the
- * stream and frees it there, so the intermediate stays in L2 where it fits;
- * the call is safe to capture in a CUDA graph.  The gradient's subtraction is an elementwise
- * pass after the dilation.  Errors as morph_apply; MORPH_ERR_ARG for another kind,
- * MORPH_ERR_NOMEM when the scratch cannot be allocated.
+ * step's).  Windows of at most 9 x 9 pixels (on an image at least as large
+ * as the window) run as one kernel that keeps both steps in shared memory
+ * and allocates nothing: each pixel is read once and written once
+ * (morph_set_composite_kernel).  Larger windows run as two ordinary calls
+ * through one scratch image of width x height pixels (pitch rounded to 16
+ * bytes) from the library's stream-ordered pool, allocated and freed on the
+ * stream, so the intermediate stays in L2 where it fits; the gradient's
+ * subtraction is then an elementwise pass after the dilation.  Either form
+ * is safe to capture in a CUDA graph.  Errors as morph_apply;
+ * MORPH_ERR_ARG for another kind, MORPH_ERR_NOMEM when the scratch cannot be
+ * allocated.
  */
 enum { MORPH_OPEN = 0, MORPH_CLOSE = 1, MORPH_GRADIENT = 2 };
 

@@ -507,6 +507,13 @@ int morph_composite(const void* src, size_t src_pitch, void* dst, size_t dst_pit
   if (rc != MORPH_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int esz = esz_of(dtype);
+  // windows of at most 9 x 9: one pass over the image, both steps in shared
+  // memory (no intermediate image)
+  if (tuning().comp_mode != 0 && comp_fits(width, height, wx, wy))
+    return comp_launch(src, static_cast<long long>(src_pitch), dst, static_cast<long long>(dst_pitch), width, height,
+                       esz, kind, wx, wy, anchor_x, anchor_y, tuning().pdl_mode == 1, st) == cudaSuccess
+               ? MORPH_OK
+               : MORPH_ERR_CUDA;
   // the intermediate (opening, closing) or the erosion (gradient), ordered
   // on the caller's stream and freed there
   Scratch t;
@@ -744,6 +751,12 @@ int morph_set_pdl(int on) {
 int morph_set_split(int mode) {
   if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
   tuning().split_mode = mode;
+  return MORPH_OK;
+}
+
+int morph_set_composite_kernel(int mode) {
+  if (mode < -1 || mode > 1) return MORPH_ERR_ARG;
+  tuning().comp_mode = mode;
   return MORPH_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "morph_common.cuh"
+#include "morph_comp.cuh"
 #include "morph_internal.h"
 
 namespace morph {
@@ -54,7 +55,47 @@ __global__ void __launch_bounds__(kSubThreads) sub_kernel(uint8_t* dst, long lon
   }
 }
 
+// One CTA per output tile of the one-pass composite (morph_comp.cuh).
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kCompThreads) comp_kernel(const CompArgs a) {
+  __shared__ uint32_t smem[kCompSmemWords];
+  pdl_wait();
+  comp_tile<T, KIND>(a, blockIdx.x, threadIdx.x, smem);
+  pdl_launch_dependents();
+}
+
+template <typename T>
+void (*comp_kernel_for(int kind))(const CompArgs) {
+  return kind == kCompOpen ? comp_kernel<T, kCompOpen> : kind == kCompClose ? comp_kernel<T, kCompClose>
+                                                                            : comp_kernel<T, kCompGradient>;
+}
+
 }  // namespace
+
+bool comp_fits(int W, int H, int wx, int wy) {
+  return wx >= 1 && wy >= 1 && wx <= kCompMaxW && wy <= kCompMaxW && W >= wx && H >= wy;
+}
+
+cudaError_t comp_launch(const void* src, long long sp, void* dst, long long dp, int W, int H, int esz, int kind,
+                        int wx, int wy, int ax, int ay, bool pdl, cudaStream_t stream) {
+  if (!comp_fits(W, H, wx, wy) || kind < kCompOpen || kind > kCompGradient) return cudaErrorInvalidValue;
+  CompArgs a;
+  a.src = static_cast<const uint8_t*>(src);
+  a.dst = static_cast<uint8_t*>(dst);
+  a.sp = sp;
+  a.dp = dp;
+  a.W = W;
+  a.H = H;
+  a.wx = wx;
+  a.wy = wy;
+  a.ax = ax;
+  a.ay = ay;
+  a.tiles_x = (W + kCompTX - 1) / kCompTX;
+  const long long tiles = static_cast<long long>(a.tiles_x) * ((H + kCompTY - 1) / kCompTY);
+  if (tiles > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  auto k = esz == 1 ? comp_kernel_for<uint8_t>(kind) : comp_kernel_for<uint16_t>(kind);
+  return launch_pdl(pdl, k, dim3(static_cast<unsigned>(tiles)), dim3(kCompThreads), 0, stream, a);
+}
 
 cudaError_t sub_launch(void* dst, long long dp, const void* sub, long long sp, int row_bytes, int H, int esz,
                        cudaStream_t stream) {

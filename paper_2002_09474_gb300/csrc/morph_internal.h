@@ -116,6 +116,14 @@ cudaError_t colv_launch(const FusedLaunch& L, cudaStream_t stream);
 cudaError_t sub_launch(void* dst, long long dp, const void* sub, long long sp, int row_bytes, int H, int esz,
                        cudaStream_t stream);
 
+// The one-pass opening (kind 0), closing (1) or gradient (2) for windows of
+// at most 9 pixels a side on images at least as large as the window
+// (comp_fits; morph_comp.cuh).  The anchor is the first step's; the second
+// step of an opening or closing takes the reflected element.
+bool comp_fits(int W, int H, int wx, int wy);
+cudaError_t comp_launch(const void* src, long long sp, void* dst, long long dp, int W, int H, int esz, int kind,
+                        int wx, int wy, int ax, int ay, bool pdl, cudaStream_t stream);
+
 // One warp waits, bounded, on an mbarrier phase nothing completes, and
 // records kDevErrTmaTimeout when the wait gives up (selftest.cu).
 cudaError_t selftest_wait_timeout(cudaStream_t stream);

@@ -89,6 +89,7 @@ void reset_tuning_defaults() {
   }
   g_tuning.split_mode = -1;
   g_tuning.batch_alone = kBatchAlonePixels;
+  g_tuning.comp_mode = -1;
   g_tuning.split_order = 1;
   g_tuning.pdl_mode = 1;
   g_tuning.pipe_mode = -1;

@@ -28,6 +28,7 @@ struct Tuning {
   int fused_cfg_tuned[2][4];      // [esz-1][window class]: measured tile shape of the fused kernel, -1 none
   int colv_fam_tuned[2][5];       // [esz-1][window class]: measured tile-height choice of the pass along y, -1 none
   long long batch_alone;          // batch images of at least this many pixels run as their single call (0: none)
+  int comp_mode;                  // composites by the one-pass kernel where it fits: -1 auto, 0 never, 1 always
   int from_autotune;              // 1 once measured or loaded from a cache
 };
 

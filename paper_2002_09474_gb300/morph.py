@@ -96,6 +96,7 @@ _SIGS = {
     "morph_set_rowv": [_i32, _i32],
     "morph_set_xpass": [_i32, _i32],
     "morph_set_batch_alone": [ctypes.c_longlong],
+    "morph_set_composite_kernel": [_i32],
     "morph_device_error": [],
     "morph_launch_count": [],
 }
@@ -264,6 +265,10 @@ def morph_set_xpass(dtype, mode):
 
 def morph_set_batch_alone(min_pixels):
     return _lib.morph_set_batch_alone(min_pixels)
+
+
+def morph_set_composite_kernel(mode):
+    return _lib.morph_set_composite_kernel(mode)
 
 
 def morph_reset_tuning():

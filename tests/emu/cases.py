@@ -7,7 +7,8 @@ every 1 x wy case (wy > 1) also through the column kernel (kern 2), every
 wx x 1 case (wx > 1) also through the row kernel (kern 3), and every 1 x wy
 case also through the warp-tiled van Herk/Gil-Werman kernel of the pass
 along y (kern 4, its strip width varying with the seed); kern 5 is the
-register-blocked pass along x.  --only K keeps the cases of kernel K."""
+register-blocked pass along x; kern 6 the one-pass composite (op is then
+the kind: opening, closing, gradient).  --only K keeps the cases of kernel K."""
 import itertools
 import sys
 
@@ -137,6 +138,32 @@ def cases(full=True):
                         seed += 1
     for c in rowv:
         both.append(c + (5,))
+    # the one-pass composite (op: 0 opening, 1 closing, 2 gradient): windows
+    # up to 9 x 9, every anchor of some windows, ragged and tiny images
+    # (never smaller than the window), unaligned pitches and offsets
+    comp = []
+    for esz in (1, 2):
+        for (w, h) in ((128, 32), (129, 33), (300, 70), (9, 9), (17, 5), (5, 40), (257, 95), (64, 31)):
+            for (wx, wy) in ((1, 1), (3, 3), (2, 5), (9, 9), (1, 9), (9, 1), (4, 8), (7, 6)):
+                if wx > w or wy > h:
+                    continue
+                for kind in (0, 1, 2):
+                    n = len(comp)
+                    ax, ay = [(0, wx // 2, wx - 1)[n % 3], (wy - 1, 0, wy // 2)[n % 3]]
+                    if n % 3 == 0:
+                        pad, off, dpad, doff = aligned_pad(w, esz), 0, aligned_pad(w, esz), 0
+                    elif n % 3 == 1:
+                        pad, off, dpad, doff = 0, 0, 0, 0
+                    else:
+                        pad, off, dpad, doff = 3 * esz, esz, 5 * esz, 2 * esz
+                    comp.append((esz, kind, w, h, pad, off, dpad, doff, wx, wy, ax, ay, -1, -1, -1, seed))
+                    seed += 1
+        for (wx, wy) in ((4, 3), (5, 5)):
+            for ax, ay in itertools.product(range(wx), range(wy)):
+                comp.append((esz, (ax + ay) % 3, 70, 45, 0, 0, 0, 0, wx, wy, ax, ay, -1, -1, -1, seed))
+                seed += 1
+    for c in comp:
+        both.append(c + (6,))
     return both
 
 

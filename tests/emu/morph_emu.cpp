@@ -24,7 +24,8 @@
 // Herk/Gil-Werman kernel of the pass along x for wx x 1 windows, when the
 // source rows allow it, its segment planned for 152 SMs on odd seeds and 3
 // SMs on even ones; the warp-tiled kernel's strip width varies with the
-// seed: 4 or 8 bytes per lane).
+// seed: 4 or 8 bytes per lane; 6 = the one-pass composite, op then being
+// the kind: 0 opening, 1 closing, 2 gradient).
 // Output: one line per case, "OK ..." or "FAIL ...".
 #define MORPH_HOST_EMU 1
 
@@ -119,6 +120,12 @@ static inline unsigned int __vmaxu2(unsigned int a, unsigned int b) {
   const unsigned hi = (a >> 16) > (b >> 16) ? (a >> 16) : (b >> 16);
   return lo | (hi << 16);
 }
+// Per-lane subtraction of two 16-bit lanes, modulo 2^16 in each lane.
+static inline unsigned int __vsub2(unsigned int a, unsigned int b) {
+  const unsigned lo = ((a & 0xFFFFu) - (b & 0xFFFFu)) & 0xFFFFu;
+  const unsigned hi = ((a >> 16) - (b >> 16)) & 0xFFFFu;
+  return lo | (hi << 16);
+}
 // Byte selection from the 8-byte value {y, x}: result byte i is byte
 // (s >> 4i) & 7 (bit 3 of each selector nibble replicates that byte's sign).
 static inline unsigned int __byte_perm(unsigned int x, unsigned int y, unsigned int s) {
@@ -147,6 +154,7 @@ static inline unsigned int __funnelshift_r(unsigned int lo, unsigned int hi, uns
 #include "morph_row.cuh"
 #include "morph_colv.cuh"
 #include "morph_rowv.cuh"
+#include "morph_comp.cuh"
 
 // ---- TMA / mbarrier model ------------------------------------------------------
 struct EmuMap {
@@ -672,7 +680,45 @@ int main() {
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
     }
-    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv ? 0 : ncta); ++c) {
+    const bool use_comp = kern == 6;
+    if (use_comp) {
+      CompArgs ca{};
+      ca.src = src;
+      ca.dst = dst;
+      ca.sp = sp;
+      ca.dp = dp;
+      ca.W = W;
+      ca.H = H;
+      ca.wx = wx;
+      ca.wy = wy;
+      ca.ax = ax;
+      ca.ay = ay;
+      ca.tiles_x = cdiv(W, kCompTX);
+      const int ntile = ca.tiles_x * cdiv(H, kCompTY);
+      using CompFn = void (*)(const CompArgs&, int, int, uint32_t*);
+      CompFn cf = esz == 1 ? (op == 0 ? comp_tile<uint8_t, 0> : op == 1 ? comp_tile<uint8_t, 1> : comp_tile<uint8_t, 2>)
+                           : (op == 0 ? comp_tile<uint16_t, 0> : op == 1 ? comp_tile<uint16_t, 1> : comp_tile<uint16_t, 2>);
+      for (int tile = 0; tile < ntile; ++tile) {
+        EmuCta cta;
+        std::barrier<> bar(kCompThreads);
+        cta.bar = &bar;
+        const size_t smb = sizeof(uint32_t) * kCompSmemWords;
+        uint32_t* sm = static_cast<uint32_t*>(aligned_alloc(128, smb));
+        cta.smem = reinterpret_cast<const uint8_t*>(sm);
+        cta.smem_size = smb;
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              cf(ca, tile, tid, sm);
+            },
+            kCompThreads);
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+    }
+    for (int c = 0; c < (use_col || use_row || use_colv || use_rowv || use_comp ? 0 : ncta); ++c) {
       const int bx = c % gx, by = c / gx;
       EmuCta cta;
       std::barrier<> bar(kThreads);
@@ -705,7 +751,31 @@ int main() {
     }
     // compare with the oracle, and check the bytes between rows are untouched
     std::vector<uint8_t> want(static_cast<size_t>(W) * H * esz);
-    oracle_morph(src, esz, W, H, sp, wx, wy, ax, ay, op, want.data(), static_cast<long long>(W) * esz);
+    if (use_comp) {
+      // the composite from the oracle's erosion and dilation (section 2)
+      const long long wp = static_cast<long long>(W) * esz;
+      std::vector<uint8_t> mid(want.size()), other(want.size());
+      if (op == 2) {
+        oracle_morph(src, esz, W, H, sp, wx, wy, ax, ay, 1, want.data(), wp);
+        oracle_morph(src, esz, W, H, sp, wx, wy, ax, ay, 0, other.data(), wp);
+        for (size_t i = 0; i < want.size(); i += esz) {
+          if (esz == 1) {
+            want[i] = static_cast<uint8_t>(want[i] - other[i]);
+          } else {
+            uint16_t d, e;
+            memcpy(&d, &want[i], 2);
+            memcpy(&e, &other[i], 2);
+            d = static_cast<uint16_t>(d - e);
+            memcpy(&want[i], &d, 2);
+          }
+        }
+      } else {
+        oracle_morph(src, esz, W, H, sp, wx, wy, ax, ay, op == 0 ? 0 : 1, mid.data(), wp);
+        oracle_morph(mid.data(), esz, W, H, wp, wx, wy, wx - 1 - ax, wy - 1 - ay, op == 0 ? 1 : 0, want.data(), wp);
+      }
+    } else {
+      oracle_morph(src, esz, W, H, sp, wx, wy, ax, ay, op, want.data(), static_cast<long long>(W) * esz);
+    }
     long long bad = 0, guard = 0;
     for (int y = 0; y < H; ++y) {
       if (memcmp(dst + y * dp, want.data() + static_cast<size_t>(y) * W * esz, static_cast<size_t>(W) * esz)) ++bad;
@@ -720,7 +790,7 @@ int main() {
     printf("%s case %d esz %d op %d %dx%d win %dx%d a %d,%d cfg %d tile %dx%d blk %d,%d tma %d,%d kern %d "
            "col_ty %d partial_st %d rows_bad %lld guard %lld dev_err %d %s\n",
            ok ? "OK" : "FAIL", cases, esz, op, W, H, wx, wy, ax, ay, L.cfg, TX, TY, a.blk_x, a.blk_y, a.tma_ld,
-           a.tma_st, use_rowv ? 5 : use_colv ? kern : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
+           a.tma_st, use_comp ? 6 : use_rowv ? 5 : use_colv ? kern : use_row ? 3 : use_col ? 2 : use_pipe ? 1 : 0, col_ty, partial, bad, guard, errword, first.c_str());
     fflush(stdout);
     free(sbuf);
     free(dbuf);

@@ -118,6 +118,8 @@ def test_tuning_arguments():
     assert m.morph_set_xpass(5, 0) == -9 and m.morph_set_xpass(0, 2) == -10 and m.morph_set_xpass(1, -1) == -10
     assert m.morph_set_xpass(0, 1) == 0 and m.morph_set_xpass(0, 0) == 0
     assert m.morph_set_batch_alone(0) == 0 and m.morph_set_batch_alone(-1) == 0
+    assert m.morph_set_composite_kernel(2) == -10 and m.morph_set_composite_kernel(-2) == -10
+    assert m.morph_set_composite_kernel(0) == 0 and m.morph_set_composite_kernel(-1) == 0
     assert m.morph_set_column_kernel(3) == -10 and m.morph_set_column_kernel(-1) == 0
     assert m.morph_set_row_kernel(-3) == -10 and m.morph_set_row_kernel(-1) == 0
     assert m.morph_set_colv(2, 0, 0) == -10 and m.morph_set_colv(-2, 0, 0) == -10

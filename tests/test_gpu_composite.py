@@ -101,3 +101,47 @@ def test_composite_in_a_cuda_graph_and_errors(lib):
     assert lib.morph_composite(p, 640, o.data_ptr(), 640, 640, 480, lib.MORPH_U8, 0, 0, 3, 0, 1, 0) == -3
     assert lib.morph_composite(p, 640, p, 640, 640, 480, lib.MORPH_U8, 1, 3, 3, 1, 1, 0) == -6
     lib.check_device_error()
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+def test_one_pass_composite_small_windows(lib, dtype):
+    """Windows of at most 9 x 9 take the one-pass kernel: one launch per
+    call, every pixel equal to the oracle's composite and to the two-call
+    form's, over ragged sizes (tile edges inside and beyond the image),
+    anchor extremes, offsets and unaligned pitches."""
+    torch = need_cuda()
+    g = synth.rng(952)
+    esz = np.dtype(dtype).itemsize
+    code = lib.MORPH_U8 if dtype == np.uint8 else lib.MORPH_U16
+    kinds = (lib.MORPH_OPEN, lib.MORPH_CLOSE, lib.MORPH_GRADIENT)
+    n = 0
+    try:
+        for (h, w) in ((9, 9), (33, 129), (95, 300), (1500, 700)):
+            img = synth.uniform_image(w, h, dtype, gen=g)
+            for (wx, wy) in ((1, 9), (9, 1), (2, 2), (3, 5), (8, 9), (9, 9)):
+                for kind in kinds:
+                    n += 1
+                    ax, ay = (0, wx // 2, wx - 1)[n % 3], (wy - 1, 0, wy // 2)[n % 3]
+                    spad = (16 - (w * esz) % 16) % 16 if n % 2 else 3 * esz
+                    src = DeviceImage(torch, h, w, dtype, pad=spad, offset=esz * (n % 3 == 0), fill=img)
+                    outs = []
+                    for mode in (1, 0):
+                        assert lib.morph_set_composite_kernel(mode) == 0
+                        dst = DeviceImage(torch, h, w, dtype, pad=esz * (n % 4))
+                        torch.cuda.synchronize()
+                        n0 = lib.morph_launch_count()
+                        rc = lib.morph_composite(src.ptr, src.pitch, dst.ptr, dst.pitch, w, h, code, kind, wx, wy,
+                                                 ax, ay, 0)
+                        assert rc == 0, lib.status_string(rc)
+                        torch.cuda.synchronize()
+                        if mode == 1:
+                            assert lib.morph_launch_count() - n0 == 1, "not the one-pass kernel"
+                        assert dst.untouched_outside()
+                        outs.append(dst.read())
+                    want = want_of(kind, img, wx, wy, ax, ay, lib)
+                    err = str((h, w, wx, wy, ax, ay, kind))
+                    np.testing.assert_array_equal(outs[0], want, err_msg=err)
+                    np.testing.assert_array_equal(outs[1], want, err_msg=err)
+    finally:
+        lib.morph_set_composite_kernel(-1)
+    assert lib.morph_device_error() == 0
