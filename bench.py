@@ -324,13 +324,15 @@ def measure_small_images(torch, morph, reps: int = 7) -> dict:
     return out
 
 
-def measure_composite(torch, morph, reps: int = 7) -> dict:
-    """Opening, closing and gradient of a 4096 x 4096 image (u8 and u16,
-    21 x 51 and 127 x 127) as one morph_composite call, against the same
-    steps as separate morph_apply calls into a caller buffer (opening and
-    closing: two calls; gradient: two calls, without the subtraction).  Both
-    are timed as CUDA-graph replays of 8 calls; the results are checked
-    identical first.  Algorithmic bytes: read and write the image once."""
+def measure_composite(torch, morph, reps: int = 7, peak: float = 6800.0) -> dict:
+    """Opening, closing and gradient of a 4096 x 4096 image (u8 and u16;
+    3 x 3 and 9 x 9, which take the one-pass kernel, 21 x 51 and 127 x 127,
+    which take two calls through an intermediate) as one morph_composite
+    call, against the same steps as separate calls into a caller buffer
+    (opening and closing: two morph_apply calls; gradient: two calls and a
+    torch subtraction).  Both are timed as CUDA-graph replays of 8 calls;
+    the results are checked identical first.  Algorithmic bytes: read and
+    write the image once (frac_of_hbm against the measured copy peak)."""
     out = {}
     for dt, tdt, code, name in ((np.uint8, torch.uint8, morph.MORPH_U8, "u8"),
                                 (np.uint16, torch.uint16, morph.MORPH_U16, "u16")):
@@ -340,7 +342,7 @@ def measure_composite(torch, morph, reps: int = 7) -> dict:
         dsts = [torch.empty_like(srcs[0]) for _ in range(4)]
         tmp = torch.empty_like(srcs[0])
         pitch = SIDE * esz
-        for (wx, wy) in ((21, 51), (127, 127)):
+        for (wx, wy) in ((3, 3), (9, 9), (21, 51), (127, 127)):
             ax, ay = wx // 2, wy // 2
             rx, ry = wx - 1 - ax, wy - 1 - ay
             for kind, kname in ((morph.MORPH_OPEN, "open"), (morph.MORPH_CLOSE, "close"),
@@ -364,16 +366,20 @@ def measure_composite(torch, morph, reps: int = 7) -> dict:
                         rc = morph.morph_apply(sp_, pitch, dp_, pitch, SIDE, SIDE, code, op, wx, wy, x_, y_, sh)
                         if rc != 0:
                             raise morph.MorphError("morph_apply", rc)
+                    if kind == morph.MORPH_GRADIENT:
+                        # dilation minus erosion on the current stream (u16 through
+                        # int16 views: the same bits, and dilate >= erode)
+                        dv, tv = (d, tmp) if d.dtype == torch.uint8 else (d.view(torch.int16), tmp.view(torch.int16))
+                        torch.sub(dv, tv, out=dv)
 
                 st = torch.cuda.current_stream()
                 one(0, st.cuda_stream)
                 torch.cuda.synchronize()
                 ref = dsts[0].clone()
-                if kind != morph.MORPH_GRADIENT:
-                    sep(0, st.cuda_stream)
-                    torch.cuda.synchronize()
-                    if not torch.equal(ref, dsts[0]):
-                        raise RuntimeError("composite differs from separate calls")
+                sep(0, st.cuda_stream)
+                torch.cuda.synchronize()
+                if not torch.equal(ref, dsts[0]):
+                    raise RuntimeError("composite differs from separate calls")
                 times = {}
                 for label, fn in (("composite", one), ("separate", sep)):
                     g = torch.cuda.CUDAGraph()
@@ -394,7 +400,8 @@ def measure_composite(torch, morph, reps: int = 7) -> dict:
                     times[label] = round(sorted(ts)[len(ts) // 2], 2)
                 out["%s_%s_%dx%d" % (name, kname, wx, wy)] = {
                     "us_per_call": times["composite"], "separate_calls_us": times["separate"],
-                    "gpix_s": round(SIDE * SIDE / times["composite"] / 1e3, 1)}
+                    "gpix_s": round(SIDE * SIDE / times["composite"] / 1e3, 1),
+                    "frac_of_hbm": round(2 * esz * SIDE * SIDE / (times["composite"] * 1e3) / peak, 3)}
         del srcs, dsts, tmp
     return out
 
@@ -771,7 +778,7 @@ def run_gpu(args):
     if not args.no_extras:
         extras["transposes"] = measure_transposes(torch, morph, peak, peak_kind)
         extras["batched"] = measure_batched(torch, morph)
-        extras["composite"] = measure_composite(torch, morph)
+        extras["composite"] = measure_composite(torch, morph, peak=peak)
         extras["small_images"] = measure_small_images(torch, morph)
         extras["serving"] = measure_serving(torch, rates=args.serving_rates,
                                             duration_s=args.serving_seconds)

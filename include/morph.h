@@ -128,10 +128,11 @@ int morph_apply(const void *src, size_t src_pitch, void *dst, size_t dst_pitch,
  *   MORPH_GRADIENT  dilate(S) - erode(S), both by the same element and
  *                   anchor (never negative)
  * Arguments as in morph_apply (kind replaces op; the anchor is the first
- * step's).  Windows of at most 9 x 9 pixels (on an image at least as large
- * as the window) run as one kernel that keeps both steps in shared memory
- * and allocates nothing: each pixel is read once and written once
- * (morph_set_composite_kernel).  Larger windows run as two ordinary calls
+ * step's).  The gradient of windows up to 5 x 5 (on an image at least as
+ * large as the window) runs as one kernel that keeps both steps in shared
+ * memory and allocates nothing: each pixel is read once and written once
+ * (morph_set_composite_kernel extends that form to every window up to
+ * 9 x 9 and every kind).  Otherwise the call runs two ordinary calls
  * through one scratch image of width x height pixels (pitch rounded to 16
  * bytes) from the library's stream-ordered pool, allocated and freed on the
  * stream, so the intermediate stays in L2 where it fits; the gradient's

@@ -154,14 +154,16 @@ int morph_set_xpass(int dtype, int mode);
 int morph_set_batch_alone(long long min_pixels);
 
 /*
- * Form of morph_composite for windows of at most 9 x 9 pixels (on images at
- * least as large as the window): -1 (auto, the default) and 1: one kernel
- * that loads each output tile with the halo of both steps and runs all of
- * their 1-D passes (the gradient's min and max side by side) in shared
- * memory, so each pixel crosses HBM once in and once out; 0: the two
- * ordinary calls through an intermediate image (and the subtraction pass).
- * Larger windows always take the latter.  The result never changes.
- * MORPH_ERR_ARG for another value.
+ * Form of morph_composite.  The one-pass kernel (windows of at most 9 x 9
+ * pixels, on images at least as large as the window) loads each output tile
+ * with the halo of both steps and runs all of their 1-D passes (the
+ * gradient's min and max side by side) in shared memory, so each pixel
+ * crosses HBM once in and once out; the other form is two ordinary calls
+ * through an intermediate image (and, for the gradient, a subtraction pass).
+ * -1 (auto, the default): the one-pass kernel for the gradient of windows up
+ * to 5 x 5, where it measured faster; 1: the one-pass kernel wherever it
+ * fits; 0: never.  The result never changes.  MORPH_ERR_ARG for another
+ * value.
  */
 int morph_set_composite_kernel(int mode);
 

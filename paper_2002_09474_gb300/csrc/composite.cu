@@ -55,19 +55,28 @@ __global__ void __launch_bounds__(kSubThreads) sub_kernel(uint8_t* dst, long lon
   }
 }
 
-// One CTA per output tile of the one-pass composite (morph_comp.cuh).
-template <typename T, int KIND>
+// One CTA per output tile of the one-pass composite (morph_comp.cuh); HB
+// bounds both halos (2, 4 or 8).
+template <typename T, int KIND, int HB>
 __global__ void __launch_bounds__(kCompThreads) comp_kernel(const CompArgs a) {
   __shared__ uint32_t smem[kCompSmemWords];
   pdl_wait();
-  comp_tile<T, KIND>(a, blockIdx.x, threadIdx.x, smem);
+  comp_tile<T, KIND, HB>(a, blockIdx.x, threadIdx.x, smem);
   pdl_launch_dependents();
 }
 
+using CompFn = void (*)(const CompArgs);
+
+template <typename T, int HB>
+CompFn comp_kernel_for(int kind) {
+  return kind == kCompOpen    ? comp_kernel<T, kCompOpen, HB>
+         : kind == kCompClose ? comp_kernel<T, kCompClose, HB>
+                              : comp_kernel<T, kCompGradient, HB>;
+}
+
 template <typename T>
-void (*comp_kernel_for(int kind))(const CompArgs) {
-  return kind == kCompOpen ? comp_kernel<T, kCompOpen> : kind == kCompClose ? comp_kernel<T, kCompClose>
-                                                                            : comp_kernel<T, kCompGradient>;
+CompFn comp_kernel_for(int kind, int halo) {
+  return halo <= 2 ? comp_kernel_for<T, 2>(kind) : halo <= 4 ? comp_kernel_for<T, 4>(kind) : comp_kernel_for<T, 8>(kind);
 }
 
 }  // namespace
@@ -93,7 +102,8 @@ cudaError_t comp_launch(const void* src, long long sp, void* dst, long long dp, 
   a.tiles_x = (W + kCompTX - 1) / kCompTX;
   const long long tiles = static_cast<long long>(a.tiles_x) * ((H + kCompTY - 1) / kCompTY);
   if (tiles > 0x7FFFFFFFll) return cudaErrorInvalidValue;
-  auto k = esz == 1 ? comp_kernel_for<uint8_t>(kind) : comp_kernel_for<uint16_t>(kind);
+  const int halo = (wx > wy ? wx : wy) - 1;
+  CompFn k = esz == 1 ? comp_kernel_for<uint8_t>(kind, halo) : comp_kernel_for<uint16_t>(kind, halo);
   return launch_pdl(pdl, k, dim3(static_cast<unsigned>(tiles)), dim3(kCompThreads), 0, stream, a);
 }
 

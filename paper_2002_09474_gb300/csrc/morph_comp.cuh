@@ -50,42 +50,73 @@ template <int OP> __device__ __forceinline__ uint32_t comp_op(uint32_t a, uint32
 }
 
 // Region rows [ry, ry + nrows), pixels [rx, rx + 2 nw) into buf, each pixel
-// the image's at the clamped coordinates.
+// the image's at the clamped coordinates.  Warp w takes rows w, w + 8, ...;
+// every load of a thread is issued before its first store, so that they are
+// all in flight together (a store between them would order each load after
+// it).
 template <typename T>
 __device__ __forceinline__ void comp_load(const CompArgs& a, int rx, int ry, int nw, int nrows, uint32_t* buf,
                                           int tid) {
+  constexpr int RPW = (kCompInRows + kCompThreads / 32 - 1) / (kCompThreads / 32);  // rows per warp
+  constexpr int KPL = (kCompRowW + 31) / 32;                                       // words per lane and row
   const int warp = tid >> 5, lane = tid & 31;
-  for (int r = warp; r < nrows; r += kCompThreads / 32) {
+  const bool inside = rx >= 0 && rx + 2 * nw <= a.W;  // no column clamping in this region
+  uint32_t v[RPW][KPL];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = warp + i * (kCompThreads / 32);
+    if (r >= nrows) continue;
     int gy = ry + r;
     gy = gy < 0 ? 0 : (gy >= a.H ? a.H - 1 : gy);
     const T* row = reinterpret_cast<const T*>(a.src + static_cast<long long>(gy) * a.sp);
-    for (int k = lane; k < nw; k += 32) {
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+      const int k = lane + 32 * j;
+      if (k >= nw) continue;
       int g0 = rx + 2 * k, g1 = g0 + 1;
-      g0 = g0 < 0 ? 0 : (g0 >= a.W ? a.W - 1 : g0);
-      g1 = g1 < 0 ? 0 : (g1 >= a.W ? a.W - 1 : g1);
-      buf[r * kCompRowW + k] = static_cast<uint32_t>(row[g0]) | (static_cast<uint32_t>(row[g1]) << 16);
+      if (!inside) {
+        g0 = g0 < 0 ? 0 : (g0 >= a.W ? a.W - 1 : g0);
+        g1 = g1 < 0 ? 0 : (g1 >= a.W ? a.W - 1 : g1);
+      }
+      v[i][j] = static_cast<uint32_t>(row[g0]) | (static_cast<uint32_t>(row[g1]) << 16);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = warp + i * (kCompThreads / 32);
+    if (r >= nrows) continue;
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+      const int k = lane + 32 * j;
+      if (k < nw) buf[r * kCompRowW + k] = v[i][j];
     }
   }
 }
 
+// The loops over a window below run to HB, a compile-time bound on the
+// halo (2, 4 or 8): the compiler unrolls them, and a step beyond the actual
+// halo h is a predicated instruction that still issues, so the bound is
+// kept close to h.
+
 // Pass along y: out[r][k] = op(in[r .. r + h][k]), rows r in [0, nout),
-// words k in [0, nw).  A thread makes 8 consecutive rows of one word from
+// every word of the row (those past the region's compute unused values
+// inside the buffer).  A thread makes 8 consecutive rows of one word from
 // 8 + h loaded rows.  Reads rows up to 8 ceil(nout / 8) + h - 1 of `in`.
-template <int OP>
-__device__ __forceinline__ void comp_ypass(const uint32_t* in, uint32_t* out, int nout, int nw, int h, int tid) {
+template <int OP, int HB>
+__device__ __forceinline__ void comp_ypass(const uint32_t* in, uint32_t* out, int nout, int h, int tid) {
   constexpr int R = 8;
-  const int items = (nout + R - 1) / R * nw;
+  const int items = (nout + R - 1) / R * kCompRowW;
   for (int i = tid; i < items; i += kCompThreads) {
-    const int g = i / nw, k = i - g * nw, r0 = g * R;
-    uint32_t v[R + kCompHalo];
+    const int g = i / kCompRowW, k = i - g * kCompRowW, r0 = g * R;
+    uint32_t v[R + HB];
 #pragma unroll
-    for (int j = 0; j < R + kCompHalo; ++j)
+    for (int j = 0; j < R + HB; ++j)
       if (j < R + h) v[j] = in[(r0 + j) * kCompRowW + k];
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
       uint32_t acc = v[rr];
 #pragma unroll
-      for (int d = 1; d <= kCompHalo; ++d)
+      for (int d = 1; d <= HB; ++d)
         if (d <= h) acc = comp_op<OP>(acc, v[rr + d]);
       if (r0 + rr < nout) out[(r0 + rr) * kCompRowW + k] = acc;
     }
@@ -94,21 +125,22 @@ __device__ __forceinline__ void comp_ypass(const uint32_t* in, uint32_t* out, in
 
 // The gradient's pass along y: the min of the same rows into lo, the max
 // into hi.
-__device__ __forceinline__ void comp_ypass_minmax(const uint32_t* in, uint32_t* lo, uint32_t* hi, int nout, int nw,
-                                                  int h, int tid) {
+template <int HB>
+__device__ __forceinline__ void comp_ypass_minmax(const uint32_t* in, uint32_t* lo, uint32_t* hi, int nout, int h,
+                                                  int tid) {
   constexpr int R = 8;
-  const int items = (nout + R - 1) / R * nw;
+  const int items = (nout + R - 1) / R * kCompRowW;
   for (int i = tid; i < items; i += kCompThreads) {
-    const int g = i / nw, k = i - g * nw, r0 = g * R;
-    uint32_t v[R + kCompHalo];
+    const int g = i / kCompRowW, k = i - g * kCompRowW, r0 = g * R;
+    uint32_t v[R + HB];
 #pragma unroll
-    for (int j = 0; j < R + kCompHalo; ++j)
+    for (int j = 0; j < R + HB; ++j)
       if (j < R + h) v[j] = in[(r0 + j) * kCompRowW + k];
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
       uint32_t mn = v[rr], mx = v[rr];
 #pragma unroll
-      for (int d = 1; d <= kCompHalo; ++d)
+      for (int d = 1; d <= HB; ++d)
         if (d <= h) {
           mn = __vminu2(mn, v[rr + d]);
           mx = __vmaxu2(mx, v[rr + d]);
@@ -123,15 +155,15 @@ __device__ __forceinline__ void comp_ypass_minmax(const uint32_t* in, uint32_t* 
 
 // Pass along x of one word: pixels (2k, 2k+1) of a region row folded over
 // pixels (2k + d, 2k + 1 + d), d in [0, h]; reads words k .. k + (h+1)/2.
-template <int OP>
+template <int OP, int HB>
 __device__ __forceinline__ uint32_t comp_xword(const uint32_t* row, int h) {
-  uint32_t w[kCompHalo / 2 + 1];
+  uint32_t w[HB / 2 + 1];
 #pragma unroll
-  for (int j = 0; j <= kCompHalo / 2; ++j)
+  for (int j = 0; j <= HB / 2; ++j)
     if (2 * j <= h + 1) w[j] = row[j];
   uint32_t acc = w[0];
 #pragma unroll
-  for (int d = 1; d <= kCompHalo; ++d)
+  for (int d = 1; d <= HB; ++d)
     if (d <= h) acc = comp_op<OP>(acc, (d & 1) ? __byte_perm(w[d >> 1], w[(d >> 1) + 1], 0x5432) : w[d >> 1]);
   return acc;
 }
@@ -139,18 +171,21 @@ __device__ __forceinline__ uint32_t comp_xword(const uint32_t* row, int h) {
 // The first step's pass along x into the intermediate region (nrows rows,
 // nwo words), whose pixel (row r, pixel i) is the image's (xb + i, yb + r):
 // positions outside the image get the identity of the second step (OP2).
-template <int OP1, int OP2>
+template <int OP1, int OP2, int HB>
 __device__ __forceinline__ void comp_xpass_mid(const CompArgs& a, const uint32_t* in, uint32_t* out, int nrows,
                                                int nwo, int h, int xb, int yb, int tid) {
   const int warp = tid >> 5, lane = tid & 31;
   const uint32_t id2 = ident_word<OP2>();
+  // the whole region inside the image (most tiles): nothing to mask
+  const bool all_in = xb >= 0 && xb + 2 * nwo <= a.W && yb >= 0 && yb + nrows <= a.H;
   for (int r = warp; r < nrows; r += kCompThreads / 32) {
     const int gy = yb + r;
     const bool row_in = gy >= 0 && gy < a.H;
     for (int k = lane; k < nwo; k += 32) {
-      uint32_t v = comp_xword<OP1>(in + r * kCompRowW + k, h);
+      uint32_t v = comp_xword<OP1, HB>(in + r * kCompRowW + k, h);
       const int gx = xb + 2 * k;
-      if (!row_in) {
+      if (all_in) {
+      } else if (!row_in) {
         v = id2;
       } else {
         if (gx < 0 || gx >= a.W) v = (v & 0xFFFF0000u) | (id2 & 0x0000FFFFu);
@@ -161,21 +196,35 @@ __device__ __forceinline__ void comp_xpass_mid(const CompArgs& a, const uint32_t
   }
 }
 
-// Writes one result word (pixels x, x + 1 of image row y) where inside.
+// Writes result word v (pixels x, x + 1) into image row `row` where inside
+// (x is even; pair: the row's pixel pairs start at even addresses of their
+// size, so a u8 pair is one 16-bit store and a u16 pair one 32-bit store).
 template <typename T>
-__device__ __forceinline__ void comp_store(const CompArgs& a, int x, int y, uint32_t v) {
-  if (y >= a.H || x >= a.W) return;
-  T* row = reinterpret_cast<T*>(a.dst + static_cast<long long>(y) * a.dp);
-  if (sizeof(T) == 1 && x + 1 < a.W && !(reinterpret_cast<uintptr_t>(row + x) & 1)) {
-    *reinterpret_cast<uint16_t*>(row + x) = static_cast<uint16_t>((v & 0xFFu) | ((v >> 8) & 0xFF00u));
+__device__ __forceinline__ void comp_store(const CompArgs& a, T* row, bool pair, int x, uint32_t v) {
+  if (x >= a.W) return;
+  if (pair && x + 1 < a.W) {
+    if (sizeof(T) == 1)
+      *reinterpret_cast<uint16_t*>(row + x) = static_cast<uint16_t>((v & 0xFFu) | ((v >> 8) & 0xFF00u));
+    else
+      *reinterpret_cast<uint32_t*>(row + x) = v;
     return;
   }
   row[x] = static_cast<T>(v & 0xFFFFu);
   if (x + 1 < a.W) row[x + 1] = static_cast<T>(v >> 16);
 }
 
-// One output tile.  smem: kCompSmemWords words.
-template <typename T, int KIND>
+// Row y of the output (nullptr when below the image) and whether its pixel
+// pairs are aligned for one store each.
+template <typename T>
+__device__ __forceinline__ T* comp_row(const CompArgs& a, int y, bool* pair) {
+  if (y >= a.H) return nullptr;
+  T* row = reinterpret_cast<T*>(a.dst + static_cast<long long>(y) * a.dp);
+  *pair = !(reinterpret_cast<uintptr_t>(row) & (2 * sizeof(T) - 1));
+  return row;
+}
+
+// One output tile.  smem: kCompSmemWords words.  HB >= both halos.
+template <typename T, int KIND, int HB>
 __device__ __forceinline__ void comp_tile(const CompArgs& a, int tile, int tid, uint32_t* smem) {
   uint32_t* s_in = smem;
   uint32_t* s_mid = smem + kCompRowW * kCompInRows;
@@ -188,14 +237,19 @@ __device__ __forceinline__ void comp_tile(const CompArgs& a, int tile, int tid, 
     // both results from one region: rows y0 - ay .., pixels x0 - ax ..
     comp_load<T>(a, x0 - a.ax, y0 - a.ay, (kCompTX + hx + 1) / 2, kCompTY + hy, s_in, tid);
     __syncthreads();
-    comp_ypass_minmax(s_in, s_mid, s_out, kCompTY, (kCompTX + hx + 1) / 2, hy, tid);
+    comp_ypass_minmax<HB>(s_in, s_mid, s_out, kCompTY, hy, tid);
     __syncthreads();
-    for (int r = warp; r < kCompTY; r += kCompThreads / 32)
+    for (int r = warp; r < kCompTY; r += kCompThreads / 32) {
+      bool pair = false;
+      T* row = comp_row<T>(a, y0 + r, &pair);
+      if (!row) continue;
+#pragma unroll
       for (int k = lane; k < kOutW; k += 32) {
-        const uint32_t mn = comp_xword<0>(s_mid + r * kCompRowW + k, hx);
-        const uint32_t mx = comp_xword<1>(s_out + r * kCompRowW + k, hx);
-        comp_store<T>(a, x0 + 2 * k, y0 + r, __vsub2(mx, mn));  // mx >= mn in both lanes
+        const uint32_t mn = comp_xword<0, HB>(s_mid + r * kCompRowW + k, hx);
+        const uint32_t mx = comp_xword<1, HB>(s_out + r * kCompRowW + k, hx);
+        comp_store<T>(a, row, pair, x0 + 2 * k, __vsub2(mx, mn));  // mx >= mn in both lanes
       }
+    }
     return;
   }
   constexpr int OP1 = KIND == kCompOpen ? 0 : 1, OP2 = 1 - OP1;
@@ -205,14 +259,20 @@ __device__ __forceinline__ void comp_tile(const CompArgs& a, int tile, int tid, 
   const int nw_in = (kCompTX + 2 * hx + 1) / 2, nw_mid = (kCompTX + hx + 1) / 2;
   comp_load<T>(a, x0 - hx, y0 - hy, nw_in, kCompTY + 2 * hy, s_in, tid);
   __syncthreads();
-  comp_ypass<OP1>(s_in, s_mid, kCompTY + hy, nw_in, hy, tid);
+  comp_ypass<OP1, HB>(s_in, s_mid, kCompTY + hy, hy, tid);
   __syncthreads();
-  comp_xpass_mid<OP1, OP2>(a, s_mid, s_in, kCompTY + hy, nw_mid, hx, x0 - hx + a.ax, y0 - hy + a.ay, tid);
+  comp_xpass_mid<OP1, OP2, HB>(a, s_mid, s_in, kCompTY + hy, nw_mid, hx, x0 - hx + a.ax, y0 - hy + a.ay, tid);
   __syncthreads();
-  comp_ypass<OP2>(s_in, s_out, kCompTY, nw_mid, hy, tid);
+  comp_ypass<OP2, HB>(s_in, s_out, kCompTY, hy, tid);
   __syncthreads();
-  for (int r = warp; r < kCompTY; r += kCompThreads / 32)
-    for (int k = lane; k < kOutW; k += 32) comp_store<T>(a, x0 + 2 * k, y0 + r, comp_xword<OP2>(s_out + r * kCompRowW + k, hx));
+  for (int r = warp; r < kCompTY; r += kCompThreads / 32) {
+    bool pair = false;
+    T* row = comp_row<T>(a, y0 + r, &pair);
+    if (!row) continue;
+#pragma unroll
+    for (int k = lane; k < kOutW; k += 32)
+      comp_store<T>(a, row, pair, x0 + 2 * k, comp_xword<OP2, HB>(s_out + r * kCompRowW + k, hx));
+  }
 }
 
 }  // namespace morph

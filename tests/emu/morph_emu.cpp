@@ -696,8 +696,15 @@ int main() {
       ca.tiles_x = cdiv(W, kCompTX);
       const int ntile = ca.tiles_x * cdiv(H, kCompTY);
       using CompFn = void (*)(const CompArgs&, int, int, uint32_t*);
-      CompFn cf = esz == 1 ? (op == 0 ? comp_tile<uint8_t, 0> : op == 1 ? comp_tile<uint8_t, 1> : comp_tile<uint8_t, 2>)
-                           : (op == 0 ? comp_tile<uint16_t, 0> : op == 1 ? comp_tile<uint16_t, 1> : comp_tile<uint16_t, 2>);
+      // the halo class the launcher picks (2, 4 or 8), and on odd seeds the
+      // widest one (8), which every window fits
+      const int halo = (wx > wy ? wx : wy) - 1;
+      const int hb = (seed & 1) ? 8 : halo <= 2 ? 2 : halo <= 4 ? 4 : 8;
+#define MORPH_COMP_PICK(HB)                                                                                    \
+  (esz == 1 ? (op == 0 ? comp_tile<uint8_t, 0, HB> : op == 1 ? comp_tile<uint8_t, 1, HB> : comp_tile<uint8_t, 2, HB>) \
+            : (op == 0 ? comp_tile<uint16_t, 0, HB> : op == 1 ? comp_tile<uint16_t, 1, HB> : comp_tile<uint16_t, 2, HB>))
+      CompFn cf = hb == 2 ? MORPH_COMP_PICK(2) : hb == 4 ? MORPH_COMP_PICK(4) : MORPH_COMP_PICK(8);
+#undef MORPH_COMP_PICK
       for (int tile = 0; tile < ntile; ++tile) {
         EmuCta cta;
         std::barrier<> bar(kCompThreads);

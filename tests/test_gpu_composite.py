@@ -105,10 +105,11 @@ def test_composite_in_a_cuda_graph_and_errors(lib):
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
 def test_one_pass_composite_small_windows(lib, dtype):
-    """Windows of at most 9 x 9 take the one-pass kernel: one launch per
-    call, every pixel equal to the oracle's composite and to the two-call
-    form's, over ragged sizes (tile edges inside and beyond the image),
-    anchor extremes, offsets and unaligned pitches."""
+    """Windows of at most 9 x 9 through the one-pass kernel (forced for every
+    kind): one launch per call, every pixel equal to the oracle's composite
+    and to the two-call form's, over ragged sizes (tile edges inside and
+    beyond the image), anchor extremes, offsets and unaligned pitches; by
+    default the gradient of windows up to 5 x 5 takes it."""
     torch = need_cuda()
     g = synth.rng(952)
     esz = np.dtype(dtype).itemsize
@@ -144,4 +145,15 @@ def test_one_pass_composite_small_windows(lib, dtype):
                     np.testing.assert_array_equal(outs[1], want, err_msg=err)
     finally:
         lib.morph_set_composite_kernel(-1)
+    # the default form: one launch for a 5 x 5 gradient, more for an opening
+    img = synth.uniform_image(300, 200, dtype, gen=g)
+    src = DeviceImage(torch, 200, 300, dtype, fill=img)
+    for kind, one in ((lib.MORPH_GRADIENT, True), (lib.MORPH_OPEN, False)):
+        dst = DeviceImage(torch, 200, 300, dtype)
+        torch.cuda.synchronize()
+        n0 = lib.morph_launch_count()
+        assert lib.morph_composite(src.ptr, src.pitch, dst.ptr, dst.pitch, 300, 200, code, kind, 5, 5, 2, 2, 0) == 0
+        torch.cuda.synchronize()
+        assert (lib.morph_launch_count() - n0 == 1) == one
+        np.testing.assert_array_equal(dst.read(), want_of(kind, img, 5, 5, 2, 2, lib))
     assert lib.morph_device_error() == 0
