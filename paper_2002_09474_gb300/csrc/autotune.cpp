@@ -35,7 +35,7 @@ std::string device_key() {
   int drv = 0;
   cudaDriverGetVersion(&drv);
   char buf[512];
-  snprintf(buf, sizeof(buf), "%s|sm%d%d|%dSM|drv%d|v5", p.name, p.major, p.minor, p.multiProcessorCount, drv);
+  snprintf(buf, sizeof(buf), "%s|sm%d%d|%dSM|drv%d|v6", p.name, p.major, p.minor, p.multiProcessorCount, drv);
   return buf;
 }
 
@@ -111,11 +111,13 @@ bool load_cache(const char* path, const std::string& key, Tuning* t) {
   if (r && sscanf(r, "\"rowv_rows\": [%d, %d]", &rr[0], &rr[1]) == 2)
     for (int i = 0; i < 2; ++i)
       if (rr[i] == 2 || rr[i] == 4 || rr[i] == 8) t->rowv_rr[i] = rr[i];
-  int fc[8];
+  int fc[16];
   const char* f1 = strstr(buf, "\"fused_cfg\": [");
-  if (f1 && sscanf(f1, "\"fused_cfg\": [%d, %d, %d, %d, %d, %d, %d, %d]", &fc[0], &fc[1], &fc[2], &fc[3], &fc[4],
-                   &fc[5], &fc[6], &fc[7]) == 8)
-    for (int i = 0; i < 8; ++i) t->fused_cfg_tuned[i / 4][i % 4] = fc[i] >= 0 && fc[i] < kNumTileCfg ? fc[i] : -1;
+  if (f1 && sscanf(f1, "\"fused_cfg\": [%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d]", &fc[0],
+                   &fc[1], &fc[2], &fc[3], &fc[4], &fc[5], &fc[6], &fc[7], &fc[8], &fc[9], &fc[10], &fc[11], &fc[12],
+                   &fc[13], &fc[14], &fc[15]) == 16)
+    for (int i = 0; i < 16; ++i)
+      t->fused_cfg_tuned[i / 8][(i / 2) % 4][i % 2] = fc[i] >= 0 && fc[i] < kNumTileCfg ? fc[i] : -1;
   int cf[10];
   const char* f2 = strstr(buf, "\"colv_family\": [");
   if (f2 && sscanf(f2, "\"colv_family\": [%d, %d, %d, %d, %d, %d, %d, %d, %d, %d]", &cf[0], &cf[1], &cf[2], &cf[3],
@@ -130,15 +132,19 @@ bool save_cache(const char* path, const std::string& key, const Tuning& t) {
   fprintf(f,
           "{\"device\": \"%s\", \"cross\": [%d, %d, %d, %d], \"order\": \"u8 x, u8 y, u16 x, u16 y\", "
           "\"xpass\": [%d, %d], \"rowv_rows\": [%d, %d], "
-          "\"fused_cfg\": [%d, %d, %d, %d, %d, %d, %d, %d], "
-          "\"fused_cfg_order\": \"u8 windows <=3 <=5 <=7 <=9, u16 the same; tile configuration or -1\", "
+          "\"fused_cfg\": [%d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d, %d], "
+          "\"fused_cfg_order\": \"u8 windows <=3 <=5 <=7 <=9, each for images below 8 Mpixels and larger; "
+          "u16 the same; tile configuration or -1\", "
           "\"colv_family\": [%d, %d, %d, %d, %d, %d, %d, %d, %d, %d], "
           "\"colv_family_order\": \"u8 windows <=24 <=40 <=76 <=114 above, u16 the same; 0 rule, 1-3 multiples of "
           "the window, 4-6 64/128/256 rows\"}\n",
           key.c_str(), t.cross_row[0], t.cross_col[0], t.cross_row[1], t.cross_col[1], t.xpass_transpose[0],
-          t.xpass_transpose[1], t.rowv_rr[0], t.rowv_rr[1], t.fused_cfg_tuned[0][0], t.fused_cfg_tuned[0][1],
-          t.fused_cfg_tuned[0][2], t.fused_cfg_tuned[0][3], t.fused_cfg_tuned[1][0], t.fused_cfg_tuned[1][1],
-          t.fused_cfg_tuned[1][2], t.fused_cfg_tuned[1][3], t.colv_fam_tuned[0][0], t.colv_fam_tuned[0][1],
+          t.xpass_transpose[1], t.rowv_rr[0], t.rowv_rr[1], t.fused_cfg_tuned[0][0][0], t.fused_cfg_tuned[0][0][1],
+          t.fused_cfg_tuned[0][1][0], t.fused_cfg_tuned[0][1][1], t.fused_cfg_tuned[0][2][0],
+          t.fused_cfg_tuned[0][2][1], t.fused_cfg_tuned[0][3][0], t.fused_cfg_tuned[0][3][1],
+          t.fused_cfg_tuned[1][0][0], t.fused_cfg_tuned[1][0][1], t.fused_cfg_tuned[1][1][0],
+          t.fused_cfg_tuned[1][1][1], t.fused_cfg_tuned[1][2][0], t.fused_cfg_tuned[1][2][1],
+          t.fused_cfg_tuned[1][3][0], t.fused_cfg_tuned[1][3][1], t.colv_fam_tuned[0][0], t.colv_fam_tuned[0][1],
           t.colv_fam_tuned[0][2], t.colv_fam_tuned[0][3], t.colv_fam_tuned[0][4], t.colv_fam_tuned[1][0],
           t.colv_fam_tuned[1][1], t.colv_fam_tuned[1][2], t.colv_fam_tuned[1][3], t.colv_fam_tuned[1][4]);
   return fclose(f) == 0;
@@ -315,52 +321,56 @@ extern "C" int morph_autotune(const char* cache_path) {
       t.colv_fam_tuned[e][c] = best_f;
     }
   }
+  // Tile shape of the fused kernel per direct-method window class (square
+  // windows 3, 5, 7, 9) and size class: every shape that fits, the fastest
+  // kept; first on this 4096 x 4096 image, then on a 2048 x 2048 one.
+  const int fused_windows[4] = {3, 5, 7, 9};
+  auto tune_shapes = [&](int sc, int W, int H, long long sp) {
+    for (int e = 0; e < 2 && rc == MORPH_OK; ++e) {
+      for (int c = 0; c < 4 && rc == MORPH_OK; ++c) {
+        FusedLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.esz = e + 1;
+        L.src = src;
+        L.dst = dst;
+        L.sp = L.dp = sp;
+        L.W = W;
+        L.H = H;
+        L.wx = L.wy = fused_windows[c];
+        L.ax = L.ay = L.wx / 2;
+        FusedLaunch P = L;
+        if (!plan_single(&P) || P.vhgw_col || P.vhgw_row) {
+          t.fused_cfg_tuned[e][c][sc] = -1;  // not a direct-method window at the crossovers found
+          continue;
+        }
+        float best = 1e30f;
+        int best_c = -1;
+        for (int cfg = 0; cfg < kNumTileCfg && rc == MORPH_OK; ++cfg) {
+          FusedLaunch Q = P;
+          Q.cfg = cfg;
+          const int b = fused_smem_bytes(Q);
+          if (b <= 0 || b > kMaxSmemBytes) continue;
+          t.fused_cfg_tuned[e][c][sc] = cfg;
+          const float ms = time_planned(L, st, e0, e1);
+          if (ms >= 1e29f) rc = MORPH_ERR_CUDA;
+          if (ms < best) {
+            best = ms;
+            best_c = cfg;
+          }
+        }
+        t.fused_cfg_tuned[e][c][sc] = best_c;
+      }
+    }
+  };
+  if (rc == MORPH_OK) tune_shapes(1, kShapeW, kBigH, static_cast<long long>(spitch));
   cudaFree(src);
   cudaFree(dst);
   src = dst = nullptr;
-  // Tile shape of the fused kernel per direct-method window class, on a
-  // 2048 x 2048 image (square windows 3, 5, 7, 9): every shape that fits,
-  // the fastest kept.
   if (rc == MORPH_OK && (cudaMalloc(&src, pitch * kTuneH) != cudaSuccess ||
                          cudaMalloc(&dst, pitch * kTuneH) != cudaSuccess))
     rc = MORPH_ERR_NOMEM;
   if (rc == MORPH_OK) cudaMemset(src, 0x66, pitch * kTuneH);
-  const int fused_windows[4] = {3, 5, 7, 9};
-  for (int e = 0; e < 2 && rc == MORPH_OK; ++e) {
-    for (int c = 0; c < 4 && rc == MORPH_OK; ++c) {
-      FusedLaunch L;
-      memset(&L, 0, sizeof(L));
-      L.esz = e + 1;
-      L.src = src;
-      L.dst = dst;
-      L.sp = L.dp = static_cast<long long>(pitch);
-      L.W = kTuneW;
-      L.H = kTuneH;
-      L.wx = L.wy = fused_windows[c];
-      L.ax = L.ay = L.wx / 2;
-      FusedLaunch P = L;
-      if (!plan_single(&P) || P.vhgw_col || P.vhgw_row) {
-        t.fused_cfg_tuned[e][c] = -1;  // not a direct-method window at the crossovers found
-        continue;
-      }
-      float best = 1e30f;
-      int best_c = -1;
-      for (int cfg = 0; cfg < kNumTileCfg && rc == MORPH_OK; ++cfg) {
-        FusedLaunch Q = P;
-        Q.cfg = cfg;
-        const int b = fused_smem_bytes(Q);
-        if (b <= 0 || b > kMaxSmemBytes) continue;
-        t.fused_cfg_tuned[e][c] = cfg;
-        const float ms = time_planned(L, st, e0, e1);
-        if (ms >= 1e29f) rc = MORPH_ERR_CUDA;
-        if (ms < best) {
-          best = ms;
-          best_c = cfg;
-        }
-      }
-      t.fused_cfg_tuned[e][c] = best_c;
-    }
-  }
+  if (rc == MORPH_OK) tune_shapes(0, kTuneW, kTuneH, static_cast<long long>(pitch));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(st);

@@ -102,7 +102,7 @@ void reset_tuning_defaults() {
   g_tuning.rowv_seg = 0;
   g_tuning.rowv_rr[0] = g_tuning.rowv_rr[1] = 0;
   for (int e = 0; e < 2; ++e) {
-    for (int c = 0; c < 4; ++c) g_tuning.fused_cfg_tuned[e][c] = -1;
+    for (int c = 0; c < 4; ++c) g_tuning.fused_cfg_tuned[e][c][0] = g_tuning.fused_cfg_tuned[e][c][1] = -1;
     for (int c = 0; c < 5; ++c) g_tuning.colv_fam_tuned[e][c] = -1;
   }
   g_tuning.from_autotune = 0;
@@ -168,12 +168,14 @@ bool plan_single(FusedLaunch* L) {
       return true;
     }
   }
-  // the tile shape the autotuner measured for this pixel type and window
-  // class (direct-method windows on images of at least 1 Mpixel)
+  // the tile shape the autotuner measured for this pixel type, window
+  // class and size class (direct-method windows on images of at least
+  // 1 Mpixel)
   const int fc = fused_tune_class(L->wx, L->wy);
-  if (fc >= 0 && !L->vhgw_col && !L->vhgw_row && static_cast<long long>(L->W) * L->H >= (1ll << 20) &&
-      t.fused_cfg_tuned[e][fc] >= 0) {
-    L->cfg = t.fused_cfg_tuned[e][fc];
+  const long long px = static_cast<long long>(L->W) * L->H;
+  const int sc = fused_size_class(px);
+  if (fc >= 0 && !L->vhgw_col && !L->vhgw_row && px >= (1ll << 20) && t.fused_cfg_tuned[e][fc][sc] >= 0) {
+    L->cfg = t.fused_cfg_tuned[e][fc][sc];
     const int b = fused_smem_bytes(*L);
     if (b > 0 && b <= kMaxSmemBytes) {
       set_pipe(L);

@@ -25,7 +25,7 @@ struct Tuning {
   int rowv_mode;                  // wx x 1 passes by the register-blocked vHGW kernel: -1 auto, 0 never, 1 always
   int rowv_seg;                   // its output columns per warp segment (0: launch-shape model)
   int rowv_rr[2];                 // [esz-1]: rows per warp of the pass along x (0: built-in, 2)
-  int fused_cfg_tuned[2][4];      // [esz-1][window class]: measured tile shape of the fused kernel, -1 none
+  int fused_cfg_tuned[2][4][2];   // [esz-1][window class][size class]: measured tile shape of the fused kernel, -1 none
   int colv_fam_tuned[2][5];       // [esz-1][window class]: measured tile-height choice of the pass along y, -1 none
   long long batch_alone;          // batch images of at least this many pixels run as their single call (0: none)
   int comp_mode;                  // composites by the one-pass kernel where it fits: -1 auto, 0 never, 1 always
@@ -35,6 +35,9 @@ struct Tuning {
 // Window classes of the measured fused tile shapes: the larger window side
 // up to 3, 5, 7 or 9 (direct-method windows; -1 outside).
 int fused_tune_class(int wx, int wy);
+// Size classes of the measured fused tile shapes: images of 1 to 8 Mpixels
+// (measured on 2048 x 2048), larger (measured on 4096 x 4096).
+inline int fused_size_class(long long pixels) { return pixels >= (8ll << 20) ? 1 : 0; }
 // Window classes of the measured tile heights of the pass along y: wy up to
 // 24, 40, 76, 114, above (representatives 15, 31, 51, 101, 127).
 int colv_tune_class(int wy);
