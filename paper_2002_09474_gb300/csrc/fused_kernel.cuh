@@ -7,8 +7,12 @@
 
 namespace morph {
 
+// At least 5 resident CTAs per SM for 8-bit pixels (registers capped at 96,
+// a few bytes spilled: measured 5-8% faster at 3 x 3 to 7 x 7 on 4096^2
+// than 4 CTAs at 120 registers), 4 for 16-bit pixels (5 measured 2-4%
+// slower there).
 template <typename T, int OP, int TX, int TY>
-__global__ void __launch_bounds__(kThreads, 4) fused_kernel(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 5 : 4) fused_kernel(const __grid_constant__ CUtensorMap tin,
                                                             const __grid_constant__ CUtensorMap tout,
                                                             const ImgArgs a, const Geom g) {
   __shared__ __align__(8) uint64_t bar;
