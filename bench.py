@@ -16,8 +16,10 @@ Reported (one JSON line on rank 0):
   e2e          the same step through morph_apply_host_batch with pinned host buffers
                (host->device and device->host copies inside the timed region)
   cpu_baseline the brute-force CPU oracle on a bounded sample of the step,
-               and (separable) the oracle's separable van Herk/Gil-Werman
-               checker on the whole step, all cores and one core
+               (separable) the oracle's separable van Herk/Gil-Werman
+               checker on the whole step, all cores and one core, and
+               (paper_method) the paper's own NEON method against its scalar
+               form on the host's Arm cores, one thread
   breakdown    per (dtype, window) class: mean us per call, Gpixel/s, GB/s
   batched      2000 uneven u8 images (sides 64..2048, windows 1..63): images/s
                of the batch plan (one CUDA graph) vs the 2000 per-image calls
@@ -210,6 +212,59 @@ def oracle_sample(images, target_ops: float = 1.5e9, seed: int = 7):
 PAPER_ARM_CONTEXT = ("paper's own ratios, Samsung Exynos 5422 (ARM, one thread, gcc with NEON intrinsics), "
                      "context only: NEON erosion/dilation 3x its scalar van Herk/Gil-Werman; NEON 8x8 u16 "
                      "transpose 5.7x scalar (114 -> 20 ns), 16x16 u8 transpose 12x (565 -> 47 ns)")
+
+
+def paper_method_sample() -> dict:
+    """The paper's CPU method (cpu_method/) on the host's Arm cores, one
+    thread: its NEON form against its scalar form for 8-bit erosion of an
+    800 x 600 image (the paper's image size) at square windows 3, 15, 31 and
+    61, both passes by the direct method and both by van Herk/Gil-Werman; and
+    section 4's block transposes (ns per block, 100k blocks).  Every form's
+    output is checked against the oracle first.  The paper's own ratios are
+    quoted beside it as context."""
+    import cpu_method as cm
+    import oracle
+    if not cm.has_neon():
+        return {"unavailable": "the NEON form needs an aarch64 host"}
+
+    def per_call(fn, min_s=0.2):
+        fn()
+        n, t0 = 0, time.perf_counter()
+        while True:
+            fn()
+            n += 1
+            dt = time.perf_counter() - t0
+            if dt >= min_s:
+                return dt / n
+
+    img = synth.uniform_image(800, 600, np.uint8, seed=11)
+    out = {"image": "800x600 u8 uniform, erosion, one thread"}
+    for w in (3, 15, 31, 61):
+        want = oracle.morph(img, w, w, w // 2, w // 2, "erode")
+        row = {}
+        for method in ("direct", "vhgw"):
+            for vec in (False, True):
+                if not np.array_equal(cm.morph(img, w, w, op="erode", method=method, vector=vec), want):
+                    raise RuntimeError("paper CPU method differs from the oracle")
+                t = per_call(lambda: cm.morph(img, w, w, op="erode", method=method, vector=vec))
+                row["%s_%s_ms" % (method, "neon" if vec else "scalar")] = round(t * 1e3, 3)
+            row["%s_neon_over_scalar" % method] = round(row["%s_scalar_ms" % method] / row["%s_neon_ms" % method], 2)
+        out["%dx%d" % (w, w)] = row
+    g = synth.rng(12)
+    for kind, blocks in (("u8_16x16", g.integers(0, 256, (100000, 16, 16), dtype=np.uint8)),
+                         ("u16_8x8", g.integers(0, 65536, (100000, 8, 8), dtype=np.uint16))):
+        k = "u8" if kind.startswith("u8") else "u16"
+        ts = {}
+        for vec in (False, True):
+            if not np.array_equal(cm.transpose_blocks(k, blocks[:64], vec), blocks[:64].transpose(0, 2, 1)):
+                raise RuntimeError("paper CPU transpose differs")
+            ts[vec] = per_call(lambda: cm.transpose_blocks(k, blocks, vec)) / blocks.shape[0]
+        out["transpose_" + kind] = {"scalar_ns": round(ts[False] * 1e9, 1), "neon_ns": round(ts[True] * 1e9, 1),
+                                    "neon_over_scalar": round(ts[False] / ts[True], 2)}
+    out["paper_context"] = ("paper (Samsung Exynos 5422, one thread): NEON erosion/dilation about 3x its scalar "
+                            "van Herk/Gil-Werman; NEON 8x8 u16 transpose 5.7x scalar (114 -> 20 ns), 16x16 u8 "
+                            "transpose 12x (565 -> 47 ns)")
+    return out
 
 
 def separable_sample(images):
@@ -814,7 +869,8 @@ def run_gpu(args):
             v, cores, spent, desc = oracle_sample(host_imgs)
             line["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": cores,
                                     "kind": "oracle", "sample": desc, "seconds": round(spent, 1),
-                                    "separable": separable_sample(host_imgs)}
+                                    "separable": separable_sample(host_imgs),
+                                    "paper_method": paper_method_sample()}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
