@@ -212,10 +212,11 @@ typedef struct {
  * Runs all n images on `stream` in at most six launches: images whose
  * windows take the direct method (or too small for the single-pass kernels)
  * in one persistent launch of the fused kernel; the passes along x of 1-D
- * windows and of 2-D windows above the crossover in one batched launch of
- * the pass-along-x kernel (the 2-D ones into intermediate images); the
- * passes along y of 1-D windows and of those 2-D windows in batched
- * launches of the pass-along-y kernel (one per tile-size class).  An image
+ * windows and of 2-D windows whose pass along x is above the crossover in
+ * one batched launch of the pass-along-x kernel (the 2-D ones into
+ * intermediate images); the passes along y of 1-D windows and of those 2-D
+ * windows (direct-method ones included) in batched launches of the
+ * pass-along-y kernel (one per tile-size class).  An image
  * whose pass above the crossover reads a source those kernels cannot load
  * fast (rows not aligned to 8 pixels, base and pitch, for the pass along x;
  * base or pitch not a multiple of 16 bytes for the pass along y) runs as

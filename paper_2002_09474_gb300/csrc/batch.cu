@@ -361,7 +361,12 @@ int batch_form(const FusedLaunch& L) {
   ColvArgs ca;
   CUtensorMap m;
   if (L.wx > 1 && L.wy > 1) {
-    if (!vx || !vy) return kFormFused;
+    // two passes when the pass along x takes van Herk/Gil-Werman; a direct
+    // pass along y then runs on the pass-along-y kernel too (exact for any
+    // window), instead of a fused tile carrying the pass along x's halo
+    // (2000 uneven images: those images took half of the fused launch's
+    // time)
+    if (!vx) return kFormFused;
     FusedLaunch A = x_part(L), B = y_part(L);
     // the pass along y reads a 16-byte-pitched intermediate
     B.src = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));

@@ -71,10 +71,17 @@ bool plan_split(const FusedLaunch& L) {
   // x 3 to 9 x 9 at a crossover of 9) the fused kernel was 7-39% faster.  Below 2 Mpixels the second launch's
   // fixed cost is not repaid, and the fused kernel is kept.  Also whenever
   // the fused tile the planner picks (or every fused tile) would run fewer
-  // than 3 CTAs per SM.
+  // than 3 CTAs per SM.  A window with one pass by van Herk/Gil-Werman
+  // and the other direct splits from 4 Mpixels (the direct pass then runs
+  // on the row or column kernel): measured at 4096^2, u8 5 x 40 38.3 ->
+  // 22.6 us, 40 x 5 33.0 -> 24.0 us (u16 41.5 -> 37.9, 35.1 -> 28.3); at
+  // 2048^2 12.9 -> 9.7 and 11.4 -> 9.3 (u16 15.4 -> 15.0, 14.9 -> 11.9);
+  // at 1448^2 the fused kernel was still up to 30% faster.
   const int e = L.esz - 1;
   const bool vhgw_y = L.wy > t.cross_col[e] && L.wy >= 8, vhgw_x = L.wx > t.cross_row[e] && L.wx >= 8;
-  if (static_cast<long long>(L.W) * L.H >= (2ll << 20) && vhgw_x && vhgw_y) return true;
+  const long long px = static_cast<long long>(L.W) * L.H;
+  if (px >= (2ll << 20) && vhgw_x && vhgw_y) return true;
+  if (px >= (4ll << 20) && (vhgw_x || vhgw_y)) return true;
   FusedLaunch F = L;
   if (!plan_single(&F)) return true;
   return ctas_per_sm(fused_smem_bytes(F)) < 3;
