@@ -334,7 +334,7 @@ int batch_prepare_fused(const FusedLaunch* const* Ls, int n, int* cfg_out, int* 
 
 namespace {
 
-enum BatchForm { kFormFused = 0, kFormX = 1, kFormY = 2, kFormXY = 3 };
+enum BatchForm { kFormFused = 0, kFormX = 1, kFormY = 2, kFormXY = 3, kFormFY = 4 };
 
 // Pass-along-x launch of L (wy must be 1) in a batch.
 FusedLaunch x_part(const FusedLaunch& L) {
@@ -366,14 +366,18 @@ int batch_form(const FusedLaunch& L) {
     // window), instead of a fused tile carrying the pass along x's halo
     // (2000 uneven images: those images took half of the fused launch's
     // time)
-    if (!vx) return kFormFused;
     FusedLaunch A = x_part(L), B = y_part(L);
     // the pass along y reads a 16-byte-pitched intermediate
     B.src = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
     B.sp = static_cast<long long>(inter_pitch(L));
     A.dst = reinterpret_cast<void*>(static_cast<uintptr_t>(256));
     A.dp = B.sp;
-    return rowv_batch_args(A, &ra) && colv_batch_args(B, &ca, &m) ? kFormXY : kFormFused;
+    if (vx) return rowv_batch_args(A, &ra) && colv_batch_args(B, &ca, &m) ? kFormXY : kFormFused;
+    // a direct pass along x (the pass-along-x kernel needs 9 pixels) with a
+    // pass along y above the crossover: the pass along x as a 1-D record of
+    // the fused group, the pass along y on its kernel
+    if (vy) return colv_batch_args(B, &ca, &m) ? kFormFY : kFormFused;
+    return kFormFused;
   }
   if (L.wy == 1 && vx) return rowv_batch_args(L, &ra) ? kFormX : kFormFused;
   if (L.wx == 1 && vy) return colv_batch_args(L, &ca, &m) ? kFormY : kFormFused;
@@ -414,7 +418,7 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
     const FusedLaunch& L = in[i].L;
     forms[i] = batch_form(L);
     if (forms[i] == kFormFused) continue;
-    if (forms[i] != kFormY) tx += (L.H + kBatchRR - 1) / kBatchRR;
+    if (forms[i] == kFormX || forms[i] == kFormXY) tx += (L.H + kBatchRR - 1) / kBatchRR;
     if (forms[i] != kFormX) {
       const ColvPlan p = colv_plan(L.esz, L.W, L.H, L.wy, kMaxSmemBytes, 0, 4, 0);
       if (!p.ok) return -1;
@@ -425,6 +429,10 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
   const bool fill_x = tx < static_cast<long long>(batch_sms()) * kBatchRowvWps;
   const bool fill_y = 5 * ty < 3 * ty_slots;
   std::vector<const FusedLaunch*> fused;
+  // storage of the 1-D pass-along-x records of the fused group (reserved,
+  // so that pointers into it stay valid)
+  std::vector<FusedLaunch> xparts;
+  xparts.reserve(n);
   std::vector<BatchColv> cols_by_class[kColvClasses];
   std::vector<CUtensorMap> maps_by_class[kColvClasses];
   std::vector<int> inter_class;  // class of each intermediate's pass-along-y record (index in .col until sorted)
@@ -435,6 +443,16 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
     if (form == kFormFused) {
       fused.push_back(&L);
       continue;
+    }
+    int fused_x = -1;
+    if (form == kFormFY) {  // placeholder destination until bound
+      FusedLaunch A = x_part(L);
+      A.dst = reinterpret_cast<void*>(static_cast<uintptr_t>(256));
+      A.dp = static_cast<long long>(inter_pitch(L));
+      xparts.push_back(A);
+      fused_x = static_cast<int>(fused.size());
+      fused.push_back(&xparts.back());
+      out->fused_x.push_back(A);
     }
     if (form == kFormX || form == kFormXY) {
       BatchRowv r;
@@ -451,13 +469,14 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
       out->row_tasks += r.a.ntask;
       out->rows.push_back(r);
     }
-    if (form == kFormY || form == kFormXY) {
+    if (form == kFormY || form == kFormXY || form == kFormFY) {
+      const bool split = form != kFormY;
       BatchColv c;
       memset(&c, 0, sizeof(c));
       CUtensorMap m;
       memset(&m, 0, sizeof(m));
-      FusedLaunch B = form == kFormXY ? y_part(L) : L;
-      if (form == kFormXY) {
+      FusedLaunch B = split ? y_part(L) : L;
+      if (split) {
         B.src = reinterpret_cast<const void*>(static_cast<uintptr_t>(256));
         B.sp = static_cast<long long>(inter_pitch(L));
       }
@@ -466,9 +485,10 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
       c.op = L.op;
       const int k = colv_class(c.a.nbox);
       if (k < 0) return -1;
-      if (form == kFormXY) {
+      if (split) {
         BatchHost::Inter t;
-        t.row = static_cast<int>(out->rows.size()) - 1;
+        t.row = form == kFormXY ? static_cast<int>(out->rows.size()) - 1 : -1;
+        t.fused = fused_x;
         t.col = static_cast<int>(cols_by_class[k].size());
         t.off = inter;
         t.pitch = static_cast<long long>(inter_pitch(L));
@@ -510,11 +530,22 @@ int batch_prepare(const BatchImageIn* in, int n, BatchHost* out) {
 
 int batch_bind_intermediates(void* inter, BatchHost* h) {
   uint8_t* base = static_cast<uint8_t*>(inter);
+  size_t fx = 0;  // next of h->fused_x
   for (const BatchHost::Inter& t : h->inters) {
     uint8_t* p = base + t.off;
-    RowvArgs& ra = h->rows[t.row].a;
-    ra.dst = p;
-    ra.dp = t.pitch;
+    if (t.fused >= 0) {
+      // the fused record of the pass along x, filled again with its output
+      if (fx >= h->fused_x.size() || t.fused >= static_cast<int>(h->imgs.size())) return -1;
+      FusedLaunch A = h->fused_x[fx++];
+      A.dst = p;
+      A.dp = t.pitch;
+      BatchImage& b = h->imgs[t.fused];
+      fill_img_args(A, b.g, tile_tx(h->cfg), tile_ty(h->cfg), &b.a, &h->maps[2 * t.fused], &h->maps[2 * t.fused + 1]);
+    } else {
+      RowvArgs& ra = h->rows[t.row].a;
+      ra.dst = p;
+      ra.dp = t.pitch;
+    }
     BatchColv& c = h->cols[t.col];
     c.a.src = p;
     c.a.sp = t.pitch;

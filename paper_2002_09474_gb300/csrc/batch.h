@@ -48,10 +48,11 @@ constexpr int kBatchRowvWps = 32;
 // Host-side layout of a batch.  Images are split into three groups by the
 // form a single call would take: windows whose passes take the direct method
 // (and small images) run in the fused persistent kernel; a 2-D window whose
-// passes both take van Herk/Gil-Werman runs as a pass along x into an
-// intermediate image and a pass along y from it; 1-D windows run on the
-// kernel of their pass.  One launch per group (per tile class for the pass
-// along y), in the order fused, x, y.
+// pass along y takes van Herk/Gil-Werman runs as a pass along x into an
+// intermediate image (on the pass-along-x kernel where that pass takes van
+// Herk/Gil-Werman too, else as a 1-D record of the fused kernel) and a pass
+// along y from it; 1-D windows run on the kernel of their pass.  One launch
+// per group (per tile class for the pass along y), in the order fused, x, y.
 struct BatchHost {
   // fused group
   int cfg = -1, smem = 0, ntiles = 0, grid = 0;
@@ -68,12 +69,16 @@ struct BatchHost {
   // intermediate images of the 2-D images (bytes from the intermediate base)
   size_t inter_bytes = 0;
   struct Inter {
-    int row, col;     // its pass-along-x record and pass-along-y record
+    int row, col;     // its pass-along-x record (-1: a fused record) and pass-along-y record
+    int fused;        // the fused record of its pass along x (-1: a pass-along-x record)
     size_t off;       // bytes from the intermediate base
     long long pitch;  // bytes per row (16-byte multiple)
     int W, H, esz;
   };
   std::vector<Inter> inters;
+  // the passes along x that run in the fused group into an intermediate
+  // (their records are filled again once the intermediate is bound)
+  std::vector<FusedLaunch> fused_x;  // parallel to the inters with fused >= 0, in order
 };
 
 // One descriptor, validated and planned as a single call would be.

@@ -49,7 +49,8 @@ def test_batch_every_form(env):
     for dt in (np.uint8, np.uint16):
         esz = np.dtype(dt).itemsize
         for (w, h) in ((300, 200), (257, 129), (64, 40), (1000, 33), (130, 700), (5, 3)):
-            for (wx, wy) in ((3, 3), (1, 51), (51, 1), (21, 51), (127, 127), (9, 200), (40, 9), (17, 1)):
+            for (wx, wy) in ((3, 3), (1, 51), (51, 1), (21, 51), (127, 127), (9, 200), (40, 9), (17, 1), (5, 40),
+                             (3, 90)):
                 ax, ay = [int(g.integers(0, k)) for k in (wx, wy)]
                 op = int(g.integers(0, 2))
                 pad = (16 - (w * esz) % 16) % 16 if (w + wx) % 2 else 3 * esz
