@@ -214,9 +214,11 @@ typedef struct {
  * in one persistent launch of the fused kernel; the passes along x of 1-D
  * windows and of 2-D windows whose pass along x is above the crossover in
  * one batched launch of the pass-along-x kernel (the 2-D ones into
- * intermediate images); the passes along y of 1-D windows and of those 2-D
- * windows (direct-method ones included) in batched launches of the
- * pass-along-y kernel (one per tile-size class).  An image
+ * intermediate images; a direct pass along x of a 2-D window whose pass
+ * along y is above the crossover runs instead in the fused launch, as a
+ * 1-D pass into its intermediate); the passes along y of 1-D windows and of
+ * those 2-D windows (direct-method ones included) in batched launches of
+ * the pass-along-y kernel (one per tile-size class).  An image
  * whose pass above the crossover reads a source those kernels cannot load
  * fast (rows not aligned to 8 pixels, base and pitch, for the pass along x;
  * base or pitch not a multiple of 16 bytes for the pass along y) runs as
