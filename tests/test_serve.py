@@ -117,3 +117,50 @@ def test_max_batch_respected():
     assert max(len(ids) for _, _, ids in ex.launches) <= 16
     assert sorted(i for _, _, ids in ex.launches for i in ids) == list(range(100))
 
+
+
+class CappedExecutor(FakeExecutor):
+    """A FakeExecutor with a micro-batch byte cap and its own charge rule,
+    counting how often the server asks for each request's charge."""
+
+    def __init__(self, cap, **kw):
+        super().__init__(**kw)
+        self.max_batch_bytes = cap
+        self.charges = {}
+        self.batch_sizes = []
+
+    def charge(self, r):
+        self.charges[r.rid] = self.charges.get(r.rid, 0) + 1
+        return 3 * r.width * r.height
+
+    def batch_bytes(self, r):
+        return r.width * r.height
+
+    def launch(self, reqs, stream_index):
+        self.batch_sizes.append(sum(r.width * r.height for r in reqs))
+        return super().launch(reqs, stream_index)
+
+
+def test_micro_batch_byte_cap_and_charge_once():
+    """Micro-batches never exceed the executor's byte cap unless a single
+    request does; every request's charge is computed once."""
+    ex = CappedExecutor(cap=3 * 256 * 256, per_px=2e-8)
+    rs = reqs(40, 0.0, side=256, big=(7,))  # all at once: the server must split them
+    st = Server(ex, budget_bytes=1 << 30).run(rs, timeout_s=60)
+    assert st.completed == 40
+    for b in ex.batch_sizes:
+        assert b <= 3 * 256 * 256 or b == 4096 * 4096
+    assert max(ex.batch_sizes) == 4096 * 4096  # the oversized request alone
+    assert set(ex.charges.values()) == {1}
+
+
+@pytest.mark.parametrize("enabled", [True, False])
+def test_run_restores_the_collector_state(enabled):
+    import gc
+    was = gc.isenabled()
+    try:
+        (gc.enable if enabled else gc.disable)()
+        Server(FakeExecutor()).run(reqs(5, 0.0), timeout_s=30)
+        assert gc.isenabled() == enabled
+    finally:
+        (gc.enable if was else gc.disable)()
