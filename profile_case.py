@@ -37,6 +37,10 @@ def main(argv=None):
                     help="force the warp-tiled pass along y with this many rows per tile (0: model)")
     ap.add_argument("--rowv", type=int, default=-1,
                     help="force the register-blocked pass along x with this segment (0: model)")
+    ap.add_argument("--kind", choices=("open", "close", "gradient"), default=None,
+                    help="run morph_composite of this kind instead of one erosion or dilation")
+    ap.add_argument("--one-pass", action="store_true",
+                    help="with --kind: force the one-pass composite kernel (windows up to 9 x 9)")
     ap.add_argument("--colv-lanes", type=int, default=0,
                     help="bytes per lane of the warp-tiled pass along y (0: built-in rule; 4 or 8)")
     args = ap.parse_args(argv)
@@ -57,17 +61,23 @@ def main(argv=None):
     src = torch.from_numpy(img).cuda()
     dst = torch.empty_like(src)
     op = morph.MORPH_ERODE if args.op == "erode" else morph.MORPH_DILATE
+    kinds = {"open": morph.MORPH_OPEN, "close": morph.MORPH_CLOSE, "gradient": morph.MORPH_GRADIENT}
+    if args.one_pass:
+        morph.morph_set_composite_kernel(1)
     times = []
     for _ in range(args.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        morph.apply(src, dst, args.wx, args.wy, op=op)
+        if args.kind:
+            morph.composite(src, dst, kinds[args.kind], args.wx, args.wy)
+        else:
+            morph.apply(src, dst, args.wx, args.wy, op=op)
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     morph.check_device_error()
-    print("profile_case %s %dx%d %dx%d %s: %d launches, last %.1f us" % (
-        args.dtype, args.width, args.height, args.wx, args.wy, args.op, args.reps,
+    print("profile_case %s %dx%d %dx%d %s: %d calls, last %.1f us" % (
+        args.dtype, args.width, args.height, args.wx, args.wy, args.kind or args.op, args.reps,
         times[-1] * 1e3))
     return 0
 
