@@ -544,6 +544,54 @@ int main() {
       }
       a.tma_ld = c.tma_ld;
     }
+    if (use_row) {
+      // the row kernel, launched as row_launch does
+      const bool blk = L.vhgw_row && L.wx >= 9;
+      RowArgs ra{};
+      ra.src = src;
+      ra.dst = dst;
+      ra.sp = sp;
+      ra.dp = dp;
+      ra.W = W;
+      ra.H = H;
+      ra.w = L.wx;
+      ra.a = L.ax;
+      ra.ntx = cdiv(W, rg.txp);
+      ra.nty = cdiv(H, rg.ty);
+      ra.blocked = blk;
+      ra.ld_vec = a.ld_vec;
+      ra.st_vec = (reinterpret_cast<uintptr_t>(dst) % (8 * esz) == 0) && (dp % (8 * esz) == 0);
+      ra.err = &errword;
+      ra.tma_ld = tma_ok(src, sp, 128 / esz, rg.ty);
+      EmuMap mr{src, nullptr, esz, W, H, sp, 128 / esz, rg.ty};
+      CUtensorMap tr{};
+      memcpy(&tr, &mr, sizeof(mr));
+      RowFnE rf = esz == 1 ? (op == 0 ? pick_row<uint8_t, 0>(blk) : pick_row<uint8_t, 1>(blk))
+                           : (op == 0 ? pick_row<uint16_t, 0>(blk) : pick_row<uint16_t, 1>(blk));
+      for (int t = 0; t < ra.ntx * ra.nty; ++t) {
+        EmuCta cta;
+        std::barrier<> bar(kRowThreads);
+        cta.bar = &bar;
+        uint8_t* sm = static_cast<uint8_t*>(aligned_alloc(128, (rg.smem + 127) / 128 * 128));
+        cta.smem = sm;
+        cta.smem_size = rg.smem;
+        uint64_t mbar = 0;
+        pool_run(
+            [&](int tid) {
+              g_cta = &cta;
+              emu_threadIdx = make_uint3(tid, 0, 0);
+              uint32_t phase = 0;
+              if (tid == 0) mbar_init(&mbar, 1);
+              __syncthreads();
+              rf(ra, &tr, t, rg, sm, &mbar, phase);
+            },
+            kRowThreads);
+        free(sm);
+        errors += cta.errors.load();
+        if (cta.errors.load() && first.empty()) first = cta.first_error;
+      }
+      a.tma_ld = ra.tma_ld;
+    }
     const bool use_colv = kern == 4 && L.wx == 1 && L.wy > 1;
     if (use_colv) {
       // the warp-tiled pass along y, planned and launched as colv_launch does;
