@@ -7,6 +7,16 @@ profiler captures of a single kernel, e.g.
 
 Inputs are seeded uniform images; nothing is checked or printed except a
 one-line summary (launch count, mean event time of the launches).
+
+`--packed-minmax` instead times the packed min intrinsics on their own (8
+independent accumulators a thread, one intrinsic each per step): the 4-byte
+form `__vminu4` against the 2 x 16-bit form `__vminu2`, the choice between
+byte lanes and 16-bit lanes in every kernel.  Under ncu,
+`smsp__inst_executed.sum` of each launch divided by the warp-intrinsics it
+prints gives the instructions each form issues:
+
+  ncu --clock-control none --metrics smsp__inst_executed.sum -k regex:packed_minmax -c 2 \
+      python profile_case.py --packed-minmax --reps 1
 """
 from __future__ import annotations
 
@@ -19,6 +29,88 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+
+PACKED_MINMAX_SRC = r"""
+#include <cstdint>
+#include <cuda_runtime.h>
+
+template <int FORM>  // 0: __vminu4 (4 bytes), 1: __vminu2 (2 x 16 bits)
+__global__ void packed_minmax_kernel(const uint32_t* in, uint32_t* out, int iters) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = in[t] * (2654435761u + 2u * i);
+  for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t b = a[(i + 1) & 7];
+      a[i] = FORM == 0 ? __vminu4(a[i], b) : __vminu2(a[i], b);
+    }
+  }
+  uint32_t r = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r ^= a[i];
+  out[t] = r;
+}
+
+extern "C" int packed_minmax_launch(int form, const void* in, void* out, int iters, int blocks, int threads,
+                                    void* stream) {
+  const uint32_t* i = static_cast<const uint32_t*>(in);
+  uint32_t* o = static_cast<uint32_t*>(out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (form == 0)
+    packed_minmax_kernel<0><<<blocks, threads, 0, s>>>(i, o, iters);
+  else
+    packed_minmax_kernel<1><<<blocks, threads, 0, s>>>(i, o, iters);
+  return static_cast<int>(cudaGetLastError());
+}
+"""
+
+
+def packed_minmax(reps: int) -> int:
+    """Times __vminu4 against __vminu2 (one launch per form and repetition)."""
+    import ctypes
+    import subprocess
+
+    import torch
+
+    bdir = os.path.join(ROOT, "_build")
+    os.makedirs(bdir, exist_ok=True)
+    cu, so = os.path.join(bdir, "packed_minmax.cu"), os.path.join(bdir, "packed_minmax.so")
+    with open(cu, "w") as f:
+        f.write(PACKED_MINMAX_SRC)
+    subprocess.run(["nvcc", "-O3", "-shared", "-Xcompiler", "-fPIC", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-lineinfo", cu, "-o", so], check=True)
+    lib = ctypes.CDLL(so)
+    lib.packed_minmax_launch.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_void_p]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, threads, iters = sms * 8, 256, 2048
+    n = blocks * threads
+    src = torch.randint(0, 2**31 - 1, (n,), dtype=torch.int32, device="cuda")
+    dst = torch.empty_like(src)
+    stream = torch.cuda.current_stream()
+    warp_ops = (n // 32) * iters * 8
+    best = {}
+    for form, name in ((0, "__vminu4"), (1, "__vminu2")):
+        times = []
+        for r in range(3 + reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = lib.packed_minmax_launch(form, src.data_ptr(), dst.data_ptr(), iters, blocks, threads,
+                                          ctypes.c_void_p(stream.cuda_stream))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rc != 0:
+                raise RuntimeError("packed_minmax_launch: CUDA error %d" % rc)
+            if r >= 3:
+                times.append(e0.elapsed_time(e1) * 1e-3)
+        best[name] = min(times)
+        print("packed_minmax %s: %d warp-intrinsics a launch, best %.1f us, %.2f T thread-ops/s" % (
+            name, warp_ops, best[name] * 1e6, warp_ops * 32 / best[name] * 1e-12))
+    print("packed_minmax time ratio __vminu4 / __vminu2: %.2f" % (best["__vminu4"] / best["__vminu2"]))
+    return 0
 
 
 def main(argv=None):
@@ -43,7 +135,11 @@ def main(argv=None):
                     help="with --kind: force the one-pass composite kernel (windows up to 9 x 9)")
     ap.add_argument("--colv-lanes", type=int, default=0,
                     help="bytes per lane of the warp-tiled pass along y (0: built-in rule; 4 or 8)")
+    ap.add_argument("--packed-minmax", action="store_true",
+                    help="time __vminu4 against __vminu2 on their own instead of a filter call")
     args = ap.parse_args(argv)
+    if args.packed_minmax:
+        return packed_minmax(args.reps)
 
     import torch
     from paper_2002_09474_gb300 import build as libbuild, synth
