@@ -640,6 +640,49 @@ def measure_serving(torch, rates=(5000.0,), duration_s: float = 3.0, host_copies
     return out
 
 
+def measure_host_link(torch, step_px: int, io_bytes: int, nbytes: int = 256 << 20, reps: int = 5) -> dict:
+    """Pinned host <-> device copy rates in this run (CUDA events, median of
+    `reps` after 3 warm-ups): host to device alone, device to host alone, and
+    both at once on two streams.  They bound the end-to-end figure: a step
+    moves `io_bytes` each way, so it takes at least the longest of the three
+    copy times, whatever the kernels do."""
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_in = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    d_out = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(h2d: bool, d2h: bool) -> float:
+        times = []
+        for r in range(3 + reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            out_done = torch.cuda.Event()
+            torch.cuda.synchronize()
+            e0.record(s_in)
+            s_out.wait_event(e0)
+            if h2d:
+                with torch.cuda.stream(s_in):
+                    d_in.copy_(h_in, non_blocking=True)
+            if d2h:
+                with torch.cuda.stream(s_out):
+                    h_out.copy_(d_out, non_blocking=True)
+            out_done.record(s_out)
+            s_in.wait_event(out_done)
+            e1.record(s_in)
+            torch.cuda.synchronize()
+            if r >= 3:
+                times.append(e0.elapsed_time(e1) * 1e-3)
+        return float(np.median(times))
+
+    t_in, t_out, t_both = timed(True, False), timed(False, True), timed(True, True)
+    step_floor = max(io_bytes / (nbytes / t_in), io_bytes / (nbytes / t_out), 2 * io_bytes / (2 * nbytes / t_both))
+    return {"bytes": nbytes, "h2d_gbs": round(nbytes / t_in / 1e9, 1), "d2h_gbs": round(nbytes / t_out / 1e9, 1),
+            "both_gbs": round(2 * nbytes / t_both / 1e9, 1),
+            "ceiling": round(step_px / step_floor / 1e9, 1),
+            "note": "pinned copies of 256 MB timed with CUDA events; ceiling = the step's pixels over its "
+                    "copy time in and out at these rates (Gpixel/s)"}
+
+
 def reduce_over_ranks(torch, dist, value: float, op: str) -> float:
     """max or sum of a float over all ranks (identity without a process group)."""
     if dist is None or not dist.is_initialized():
@@ -828,6 +871,10 @@ def run_gpu(args):
     io_bytes = sum(SIDE * SIDE * np.dtype(dt).itemsize for dt, _, _, _ in runs)
     morph.morph_release_staging()
     morph.check_device_error()
+    try:
+        host_link = measure_host_link(torch, step_px, io_bytes)
+    except Exception as exc:  # a copy-rate probe must not cost the bench line
+        host_link = {"error": repr(exc)}
 
     extras = {}
     if not args.no_extras:
@@ -858,7 +905,8 @@ def run_gpu(args):
                 "e2e": {"value": round(e2e_px / e2e_s / 1e9, 3), "unit": UNIT,
                         "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
                         "api": "morph_apply_host_batch (the step's 32 images, copies overlapped "
-                               "with filtering), pinned host buffers"},
+                               "with filtering), pinned host buffers",
+                        "host_link": host_link},
                 "gpu_launches": launches_per_step * args.steps,
                 "timing": "the step's 32 calls captured once into a CUDA graph (on %d streams, one per "
                           "image kind) and replayed; per-class times from single-stream graphs" % STEP_STREAMS,
