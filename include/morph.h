@@ -24,9 +24,10 @@
  * (section 5.3) measured on this GPU.  Small windows (both passes direct) and
  * small images run both passes fused in one kernel; a 1-D window above the
  * crossover runs on the single-pass kernel of its axis; a 2-D window whose
- * passes both take van Herk/Gil-Werman, on images of at least 2 Mpixels,
- * runs as two launches, the pass along x into an intermediate image and the
- * pass along y from it (see morph_set_split).
+ * passes both take van Herk/Gil-Werman, on images of at least 2 Mpixels
+ * (4 Mpixels when only one pass takes it), runs as two launches, the pass
+ * along x into an intermediate image and the pass along y from it (see
+ * morph_set_split).
  *
  * Conventions for every entry point below
  *  - Image pointers are DEVICE pointers (cudaMalloc / torch CUDA memory)

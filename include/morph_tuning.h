@@ -27,11 +27,12 @@ extern "C" {
  * library allocates stream-ordered for images of at least 2 Mpixels when
  * both passes take the van Herk/Gil-Werman method (both window sides above
  * the crossovers of morph_set_tuning; there the single-pass kernels were
- * measured faster than the fused kernel on the GB300), or when the fused
- * tile is so large that fewer than 3 CTAs fit on an SM; otherwise both
- * passes fused in one kernel.  0: always fused; 1:
- * always two launches.  The result never
- * changes.
+ * measured faster than the fused kernel on the GB300), for images of at
+ * least 4 Mpixels when one pass takes that method and the other the direct
+ * one (the direct pass then runs on the row or column kernel), or when the
+ * fused tile is so large that fewer than 3 CTAs fit on an SM; otherwise
+ * both passes fused in one kernel.  0: always fused; 1: always two
+ * launches.  The result never changes.
  */
 int morph_set_split(int mode);
 
