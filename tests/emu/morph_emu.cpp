@@ -10,7 +10,12 @@
 // the run.  It also checks the rules the hardware does not check for us:
 // TMA coordinates 16-byte aligned, no store box starting outside the tensor,
 // boxes no larger than the tensor, transfer counts that match the expected
-// bytes.  Results are compared with the brute-force oracle.
+// bytes.  On half of the cases (by seed) a TMA load lands only when a thread
+// waits on its mbarrier for the phase it completes, so a missing or
+// wrong-phase wait reads stale shared memory, and loads still in flight when
+// a CTA ends are an error; on the other half loads land when issued, so a
+// buffer refilled before its last read shows up.  Results are compared with
+// the brute-force oracle.
 //
 // Input, one case per line on stdin:
 //   esz op W H spad soff dpad doff wx wy ax ay cfg cross_x cross_y seed kern
@@ -67,6 +72,15 @@ struct EmuCta {
   };
   std::mutex mu;
   std::map<const void*, Mbar> mbars;
+  // TMA loads not yet landed (deferred mode): each lands when a thread waits
+  // on its barrier for the phase it completes
+  struct PendingLoad {
+    void* dst;
+    CUtensorMap map;
+    int x, y;
+    uint64_t* bar;
+  };
+  std::vector<PendingLoad> pending;
   const uint8_t* smem = nullptr;
   size_t smem_size = 0;
   std::atomic<int> errors{0};
@@ -74,9 +88,23 @@ struct EmuCta {
   std::atomic<int> partial_stores{0};
 };
 thread_local EmuCta* g_cta = nullptr;
+// Deferred mode (chosen per case): a TMA load copies nothing when it is
+// issued, only when a thread waits on its mbarrier for the phase it
+// completes, so a read that does not wait, or waits for the wrong phase,
+// sees stale shared memory; and a CTA that ends with loads in flight is an
+// error.  Immediate mode copies at issue, so a buffer refilled before its
+// last read shows up instead.
+bool g_tma_deferred = false;
 
 static void emu_error(const char* what) {
   if (g_cta->errors.fetch_add(1) == 0) g_cta->first_error = what;
+}
+// Errors of a CTA that has ended, counting TMA loads still in flight.
+static int cta_end_errors(EmuCta& cta) {
+  if (!cta.pending.empty()) {
+    if (cta.errors.fetch_add(1) == 0) cta.first_error = "TMA loads still in flight when the CTA ended";
+  }
+  return cta.errors.load();
 }
 
 static inline void __syncthreads() { g_cta->bar->arrive_and_wait(); }
@@ -198,12 +226,20 @@ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   it->second.pending -= 1;
   mbar_check_complete(it->second);
 }
+static void land_tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y);  // holds g_cta->mu
 bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   std::lock_guard<std::mutex> l(g_cta->mu);
   auto it = g_cta->mbars.find(bar);
   if (it == g_cta->mbars.end()) {
     emu_error("wait on an uninitialised mbarrier");
     return true;
+  }
+  if (it->second.phase_bit == static_cast<int>(parity)) {  // the phase waited for: its loads land now
+    std::vector<EmuCta::PendingLoad> keep;
+    std::vector<EmuCta::PendingLoad> land;
+    for (auto& p : g_cta->pending) (p.bar == bar ? land : keep).push_back(p);
+    g_cta->pending.swap(keep);
+    for (auto& p : land) land_tma_load(p.dst, &p.map, p.bar, p.x, p.y);
   }
   return it->second.phase_bit != static_cast<int>(parity);
 }
@@ -226,6 +262,18 @@ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
   if (m->bw > m->W || m->bh > m->H) emu_error("TMA box larger than the tensor");
   const size_t row = static_cast<size_t>(m->bw) * m->esz;
   check_smem(dst, row * m->bh, 128, "TMA load box outside shared memory");
+  std::lock_guard<std::mutex> l(g_cta->mu);
+  if (g_tma_deferred) {
+    EmuCta::PendingLoad p{dst, {}, x, y, bar};
+    memcpy(&p.map, map, sizeof(CUtensorMap));
+    g_cta->pending.push_back(p);
+    return;
+  }
+  land_tma_load(dst, map, bar, x, y);
+}
+static void land_tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  const EmuMap* m = reinterpret_cast<const EmuMap*>(map);
+  const size_t row = static_cast<size_t>(m->bw) * m->esz;
   uint8_t* d = static_cast<uint8_t*>(dst);
   for (int r = 0; r < m->bh; ++r)
     for (int c = 0; c < m->bw; ++c) {
@@ -236,7 +284,6 @@ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
         d[r * row + c * m->esz + b] = v;
       }
     }
-  std::lock_guard<std::mutex> l(g_cta->mu);
   EmuCta::Mbar& mb = g_cta->mbars[bar];
   mb.tx -= static_cast<long long>(row) * m->bh;
   mbar_check_complete(mb);
@@ -407,6 +454,7 @@ int main() {
                &doff, &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed, &kern) == 17) {
     const int pipe = kern == 1;
     ++cases;
+    g_tma_deferred = (seed >> 2) & 1;
     const long long sp = static_cast<long long>(W) * esz + spad, dp = static_cast<long long>(W) * esz + dpad;
     // Exact-size buffers: ASan flags any byte outside [offset, last pixel].
     const size_t sbytes = soff + (H - 1) * sp + static_cast<size_t>(W) * esz;
@@ -539,7 +587,7 @@ int main() {
             },
             kColThreads);
         free(sm);
-        errors += cta.errors.load();
+        errors += cta_end_errors(cta);
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
       a.tma_ld = c.tma_ld;
@@ -587,7 +635,7 @@ int main() {
             },
             kRowThreads);
         free(sm);
-        errors += cta.errors.load();
+        errors += cta_end_errors(cta);
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
       a.tma_ld = ra.tma_ld;
@@ -668,7 +716,7 @@ int main() {
             nthr);
         for (int wi = 0; wi < c.wpc; ++wi) delete wbv[wi];
         free(sm);
-        errors += cta.errors.load();
+        errors += cta_end_errors(cta);
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
       a.tma_ld = c.tma_ld;
@@ -724,7 +772,7 @@ int main() {
             },
             32 * wpc);
         free(sm);
-        errors += cta.errors.load();
+        errors += cta_end_errors(cta);
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
     }
@@ -769,7 +817,7 @@ int main() {
             },
             kCompThreads);
         free(sm);
-        errors += cta.errors.load();
+        errors += cta_end_errors(cta);
         if (cta.errors.load() && first.empty()) first = cta.first_error;
       }
     }
@@ -800,7 +848,7 @@ int main() {
         }
       });
       free(smem);
-      errors += cta.errors.load();
+      errors += cta_end_errors(cta);
       partial += cta.partial_stores.load();
       if (cta.errors.load() && first.empty()) first = cta.first_error;
     }
