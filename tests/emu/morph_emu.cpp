@@ -445,13 +445,76 @@ static uint64_t splitmix(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
+// Planner queries (a line starting with "P"), answered with the default
+// tuning, one line each:
+//   P split esz W H wx wy      -> split 0|1           (plan_split)
+//   P single esz W H wx wy     -> single ok vhgw_col vhgw_row cfg ctas_per_sm
+//   P colvrows esz w           -> colvrows L          (built-in tile height)
+//   P colv esz W H w lb        -> colv ok L nbox wpc ntask wps   (152 SMs)
+//   P rowv W H rr wps          -> rowv ok seg nseg ntask         (152 SMs)
+//   P ctas smem_bytes          -> ctas n
+static void planner_query(const char* s) {
+  char what[32];
+  int n = 0;
+  if (sscanf(s, "%31s%n", what, &n) != 1) return;
+  s += n;
+  reset_tuning_defaults();
+  if (!strcmp(what, "split") || !strcmp(what, "single")) {
+    int esz = 1, W = 1, H = 1, wx = 1, wy = 1;
+    sscanf(s, "%d %d %d %d %d", &esz, &W, &H, &wx, &wy);
+    FusedLaunch L{};
+    L.esz = esz;
+    L.W = W;
+    L.H = H;
+    L.wx = wx;
+    L.wy = wy;
+    L.ax = wx / 2;
+    L.ay = wy / 2;
+    if (what[1] == 'p') {
+      printf("split %d\n", plan_split(L) ? 1 : 0);
+    } else {
+      const bool ok = plan_single(&L);
+      printf("single %d %d %d %d %d\n", ok ? 1 : 0, L.vhgw_col ? 1 : 0, L.vhgw_row ? 1 : 0, L.cfg,
+             ok ? ctas_per_sm(fused_smem_bytes(L)) : 0);
+    }
+  } else if (!strcmp(what, "colvrows")) {
+    int esz = 1, w = 2;
+    sscanf(s, "%d %d", &esz, &w);
+    printf("colvrows %d\n", colv_default_rows(esz, w));
+  } else if (!strcmp(what, "colv")) {
+    int esz = 1, W = 1, H = 1, w = 2, lb = 4;
+    sscanf(s, "%d %d %d %d %d", &esz, &W, &H, &w, &lb);
+    const ColvPlan p = colv_plan(esz, W, H, w, kMaxSmemBytes, 0, lb, 152);
+    printf("colv %d %d %d %d %d %d\n", p.ok ? 1 : 0, p.L, p.nbox, p.wpc, p.ntask, p.wps);
+  } else if (!strcmp(what, "rowv")) {
+    int W = 1, H = 1, rr = 2, wps = 32;
+    sscanf(s, "%d %d %d %d", &W, &H, &rr, &wps);
+    const RowvPlan p = rowv_plan(W, H, rr, 152, wps, 0);
+    printf("rowv %d %d %d %d\n", p.ok ? 1 : 0, p.seg, p.nseg, p.ntask);
+  } else if (!strcmp(what, "ctas")) {
+    int b = 0;
+    sscanf(s, "%d", &b);
+    printf("ctas %d\n", ctas_per_sm(b));
+  } else {
+    printf("unknown %s\n", what);
+  }
+  fflush(stdout);
+}
+
 int main() {
   int esz, op, W, H, spad, soff, dpad, doff, wx, wy, ax, ay, cfg, crx, cry, kern;
   unsigned long long seed;
   int failures = 0, cases = 0;
   pool_init();
-  while (scanf("%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %llu %d", &esz, &op, &W, &H, &spad, &soff, &dpad,
-               &doff, &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed, &kern) == 17) {
+  char line[512];
+  while (fgets(line, sizeof line, stdin)) {
+    if (line[0] == 'P') {
+      planner_query(line + 1);
+      continue;
+    }
+    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %llu %d", &esz, &op, &W, &H, &spad, &soff,
+               &dpad, &doff, &wx, &wy, &ax, &ay, &cfg, &crx, &cry, &seed, &kern) != 17)
+      break;
     const int pipe = kern == 1;
     ++cases;
     g_tma_deferred = (seed >> 2) & 1;
