@@ -11,7 +11,8 @@ one-line summary (launch count, mean event time of the launches).
 `--packed-minmax` instead times the packed min intrinsics on their own (8
 independent accumulators a thread, one intrinsic each per step): the 4-byte
 form `__vminu4` against the 2 x 16-bit form `__vminu2`, the choice between
-byte lanes and 16-bit lanes in every kernel.  Under ncu,
+byte lanes and 16-bit lanes in every kernel, and `__vminu2` against the PTX
+instruction `min.u16x2` written inline.  Under ncu,
 `smsp__inst_executed.sum` of each launch divided by the warp-intrinsics it
 prints gives the instructions each form issues:
 
@@ -35,7 +36,15 @@ PACKED_MINMAX_SRC = r"""
 #include <cstdint>
 #include <cuda_runtime.h>
 
-template <int FORM>  // 0: __vminu4 (4 bytes), 1: __vminu2 (2 x 16 bits)
+__device__ __forceinline__ uint32_t min_u16x2_ptx(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// 0: __vminu4 (4 bytes), 1: __vminu2 (2 x 16 bits), 2: the PTX instruction
+// min.u16x2 written inline (sm_90 and later)
+template <int FORM>
 __global__ void packed_minmax_kernel(const uint32_t* in, uint32_t* out, int iters) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t a[8];
@@ -45,7 +54,7 @@ __global__ void packed_minmax_kernel(const uint32_t* in, uint32_t* out, int iter
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const uint32_t b = a[(i + 1) & 7];
-      a[i] = FORM == 0 ? __vminu4(a[i], b) : __vminu2(a[i], b);
+      a[i] = FORM == 0 ? __vminu4(a[i], b) : FORM == 1 ? __vminu2(a[i], b) : min_u16x2_ptx(a[i], b);
     }
   }
   uint32_t r = 0;
@@ -61,8 +70,10 @@ extern "C" int packed_minmax_launch(int form, const void* in, void* out, int ite
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (form == 0)
     packed_minmax_kernel<0><<<blocks, threads, 0, s>>>(i, o, iters);
-  else
+  else if (form == 1)
     packed_minmax_kernel<1><<<blocks, threads, 0, s>>>(i, o, iters);
+  else
+    packed_minmax_kernel<2><<<blocks, threads, 0, s>>>(i, o, iters);
   return static_cast<int>(cudaGetLastError());
 }
 """
@@ -93,7 +104,7 @@ def packed_minmax(reps: int) -> int:
     stream = torch.cuda.current_stream()
     warp_ops = (n // 32) * iters * 8
     best = {}
-    for form, name in ((0, "__vminu4"), (1, "__vminu2")):
+    for form, name in ((0, "__vminu4"), (1, "__vminu2"), (2, "min.u16x2")):
         times = []
         for r in range(3 + reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -109,7 +120,8 @@ def packed_minmax(reps: int) -> int:
         best[name] = min(times)
         print("packed_minmax %s: %d warp-intrinsics a launch, best %.1f us, %.2f T thread-ops/s" % (
             name, warp_ops, best[name] * 1e6, warp_ops * 32 / best[name] * 1e-12))
-    print("packed_minmax time ratio __vminu4 / __vminu2: %.2f" % (best["__vminu4"] / best["__vminu2"]))
+    print("packed_minmax time ratio __vminu4 / __vminu2: %.2f, __vminu2 / min.u16x2: %.2f" % (
+        best["__vminu4"] / best["__vminu2"], best["__vminu2"] / best["min.u16x2"]))
     return 0
 
 
